@@ -1,0 +1,169 @@
+/*
+ * fda_bem.h - C ABI of the GB300 fast directional Burton-Miller BEM library.
+ *
+ * The library solves the exterior Helmholtz problem for a sound-hard body
+ * with the Burton-Miller boundary integral equation (Sec. 2, Eq. eq_bm),
+ * discretised by collocation at triangle centroids with piecewise-constant
+ * elements (Sec. 5), alpha = i/k.  Its matrix-vector product is the left-hand
+ * side sum of Eq. eq_sum, evaluated by the fast directional algorithm of
+ * Sec. 3 (algorithm summary, Steps 1-4) with the compressed translations of
+ * Sec. 4, inside a GMRES solve (Sec. 5).
+ *
+ * Conventions shared by every entry point:
+ *   - Mesh: vertices double[nv][3], triangles int32[nt][3] (0-based), oriented
+ *     so that (v1 - v0) x (v2 - v0) points out of the body into the acoustic
+ *     domain.  The library's normal n is the opposite unit vector (into the
+ *     body): the orientation under which Eq. cbie is Green's representation
+ *     with G = e^{ikr}/(4 pi r).
+ *   - Vectors: complex double, interleaved (re, im), one value per triangle in
+ *     the caller's triangle order; several right-hand sides are stored
+ *     column-major with leading dimension ld >= nt.
+ *   - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *     "host" pointers are ordinary host memory.  The library copies what it
+ *     keeps and owns all of its internal device memory.
+ *   - Calls are stream-ordered on the stream given in fda_config.cuda_stream
+ *     (NULL = legacy default stream).  Entry points that return results to
+ *     the host (fda_solve's info, fda_get_stats) synchronise that stream.
+ *   - Call order: fda_create -> fda_build_tree -> fda_precompute_translations
+ *     -> fda_apply / fda_rhs_plane_wave / fda_solve (any number of times)
+ *     -> fda_destroy.  Out-of-order calls return FDA_ERR_STATE.
+ *   - No C++ exception crosses this interface.  Every failing call returns a
+ *     status and leaves a message for fda_last_error.
+ */
+#ifndef FDA_BEM_H
+#define FDA_BEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } fda_c128;
+
+typedef enum {
+    FDA_OK = 0,
+    FDA_ERR_ARG = 1,            /* invalid argument (sizes, degenerate triangle, k <= 0, ...) */
+    FDA_ERR_STATE = 2,          /* call out of order */
+    FDA_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    FDA_ERR_OOM = 4,            /* device allocation failed */
+    FDA_ERR_NOT_CONVERGED = 5,  /* GMRES reached maxit above the tolerance */
+    FDA_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+    FDA_ERR_NUMERIC = 7         /* NaN/Inf met, or GMRES breakdown */
+} fda_status;
+
+typedef enum { FDA_PLAIN_FP64 = 0, FDA_CHOSEN_FP32 = 1 } fda_precision;
+typedef enum { FDA_MODE_FDA = 0, FDA_MODE_DENSE = 1 } fda_mode;
+
+typedef struct {
+    double eps;            /* SVD truncation threshold of Eq. epsg / epsk (default 1e-4) */
+    int p_lf;              /* low-frequency cube surfaces: points per edge (default 8) */
+    int p_hf;              /* high-frequency equivalent sphere: points per cube edge before projection (10) */
+    int hf_nr;             /* high-frequency cone sampling: radial shells (5) */
+    int hf_na;             /* high-frequency cone sampling: directions per shell (300) */
+    int leaf_max;          /* octree leaf capacity in elements, <= 64 (default 64) */
+    double hf_wavelengths; /* a cube is high-frequency iff its width >= hf_wavelengths * lambda (1.0) */
+    double rho_min;        /* high-frequency far field starts at max(rho_min, w/lambda) widths (2.2) */
+    int precision;         /* fda_precision: plain FP64 or chosen FP32 far field and near storage */
+    int mode;              /* fda_mode: FDA, or dense all-pairs direct sum (small meshes, testing) */
+    int restart;           /* GMRES restart length (default 100) */
+    int maxit;             /* GMRES iteration cap (default 1000) */
+    void *cuda_stream;     /* cudaStream_t, or NULL */
+} fda_config;
+
+typedef struct {
+    int iters;              /* GMRES iterations (inner iterations, summed over refinement passes) */
+    int refinements;        /* outer FP64 residual evaluations (chosen precision) */
+    double rel_resid_fp64;  /* ||b - A x|| / ||b|| with the plain FP64 FDA operator */
+    double setup_s;         /* wall time of build_tree + precompute_translations */
+    double solve_s;         /* wall time of this solve */
+    double matvec_s;        /* mean wall time of one operator application inside the solve */
+} fda_info;
+
+typedef struct {
+    int64_t n_elements, n_boxes, n_leaves, n_levels;
+    int64_t nnz_near;             /* near-field matrix entries (Step 4) */
+    int64_t n_m2l;                /* M2L (box, source) pairs over all levels */
+    int64_t n_m2l_ops;            /* distinct compressed M2L operators */
+    int64_t bytes_near;           /* bytes of the near-field matrix read per apply */
+    int64_t bytes_far;            /* bytes of far-field operators and densities read/written per apply */
+    int64_t flops_far;            /* real flops of the far-field passes per apply */
+    int64_t device_bytes;         /* device memory held by the handle */
+    int32_t level_regime[32];     /* per level: 0 = low frequency, 1 = high frequency, -1 = unused */
+    int32_t level_rank[32];       /* per level: retained SVD rank T */
+    int32_t level_boxes[32];
+    int32_t level_cones[32];
+    double precompute_s, tree_s, near_s;
+} fda_stats;
+
+typedef struct fda_handle fda_handle;
+
+/* Fill *cfg with the defaults listed above. */
+void fda_default_config(fda_config *cfg);
+
+/* Create a handle.  cfg (host) is copied.  Returns FDA_ERR_ARG for invalid
+ * settings (eps outside (0, 0.1], leaf_max outside [1, 64], ...). */
+fda_status fda_create(const fda_config *cfg, fda_handle **out);
+
+/* Sec. 3.3 Step 1 (setup, first part): copy the mesh (host pointers) to the
+ * device, compute centroids, normals, areas and quadrature points, sort the
+ * elements along a Morton curve, build the adaptive octree, split it into
+ * low- and high-frequency regimes for wavenumber k > 0, divide the
+ * high-frequency far fields into directional cones, and build the
+ * interaction and near-field lists.  All of this runs on the device.
+ * Returns FDA_ERR_ARG for nt < 1, indices out of range, a degenerate
+ * triangle or k <= 0. */
+fda_status fda_build_tree(fda_handle *h, const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                          double k);
+
+/* Sec. 3.3 Step 1 (setup, second part) and Sec. 4: equivalent and check
+ * points, truncated-SVD pseudo-inverses (Eq. svdg, epsg, invg), compressed
+ * S2M/M2M/M2L/L2L/L2T operators (Eq. cmpm2l and the compressed forms of
+ * Sec. 4.3), and the near-field matrix of Eq. eq_sum with its singular and
+ * near-singular element integrals, all in FP64 on the device. */
+fda_status fda_precompute_translations(fda_handle *h);
+
+/* y = A x (Sec. 3.3 Steps 2-4): x, y device pointers, nrhs columns with
+ * leading dimension ld (complex elements).  x and y must not overlap. */
+fda_status fda_apply(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, int64_t ld);
+
+/* Same as fda_apply with x and y in host memory: the copies to and from the
+ * device are part of the call (synchronises the stream). */
+fda_status fda_apply_host(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, int64_t ld);
+
+/* Right-hand side of Eq. eq_bm for a sound-hard body and plane waves
+ * u_inc = e^{ik d.x}: b = u_inc + alpha du_inc/dn at the centroids.
+ * dirs: host double[nrhs][3] unit vectors; b: device, ld = nt. */
+fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b);
+
+/* GMRES (Sec. 5): solve A x = b to ||b - A x|| / ||b|| <= tol for each of
+ * nrhs columns (device pointers, ld = nt; x holds the initial guess on
+ * entry, zero is fine).  Plain precision: GMRES(restart) on the FP64 FDA
+ * operator.  Chosen precision: GMRES on the FP32 operator inside an outer
+ * loop that evaluates the residual with the FP64 operator.  info (host, may
+ * be NULL) receives the last column's figures.  Returns
+ * FDA_ERR_NOT_CONVERGED when maxit is reached above tol. */
+fda_status fda_solve(fda_handle *h, const fda_c128 *b, fda_c128 *x, int nrhs, double tol, fda_info *info);
+
+/* Tree, list and operator statistics (host struct). */
+fda_status fda_get_stats(fda_handle *h, fda_stats *out);
+
+/* Per-pass device time of the most recent fda_apply, in milliseconds,
+ * measured with CUDA events on the library stream when timing is enabled:
+ * out[0] S2M, out[1] M2M, out[2] M2L, out[3] L2L, out[4] L2T, out[5] near
+ * field (S2T).  Returns FDA_ERR_STATE if timing is off. */
+fda_status fda_set_timing(fda_handle *h, int enable);
+fda_status fda_get_pass_times(fda_handle *h, float out[6]);
+
+/* Message of the last failing call on this handle (never NULL). */
+const char *fda_last_error(const fda_handle *h);
+
+/* Release every resource of the handle (NULL is ignored). */
+void fda_destroy(fda_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDA_BEM_H */

@@ -1,0 +1,166 @@
+"""ctypes binding of include/fda_bem.h: same names, argument marshalling only.
+
+Every computation happens inside libfdabem.so (CUDA kernels).  If the
+library has not been built, or no CUDA device is present, these calls fail
+with an exception: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfdabem.so")
+
+FDA_OK, FDA_ERR_ARG, FDA_ERR_STATE, FDA_ERR_CUDA, FDA_ERR_OOM = 0, 1, 2, 3, 4
+FDA_ERR_NOT_CONVERGED, FDA_ERR_TIMEOUT, FDA_ERR_NUMERIC = 5, 6, 7
+STATUS_NAMES = {0: "FDA_OK", 1: "FDA_ERR_ARG", 2: "FDA_ERR_STATE", 3: "FDA_ERR_CUDA", 4: "FDA_ERR_OOM",
+                5: "FDA_ERR_NOT_CONVERGED", 6: "FDA_ERR_TIMEOUT", 7: "FDA_ERR_NUMERIC"}
+FDA_PLAIN_FP64, FDA_CHOSEN_FP32 = 0, 1
+FDA_MODE_FDA, FDA_MODE_DENSE = 0, 1
+
+
+class fda_config(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("p_lf", ctypes.c_int), ("p_hf", ctypes.c_int), ("hf_nr", ctypes.c_int),
+                ("hf_na", ctypes.c_int), ("leaf_max", ctypes.c_int), ("hf_wavelengths", ctypes.c_double),
+                ("rho_min", ctypes.c_double), ("precision", ctypes.c_int), ("mode", ctypes.c_int),
+                ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class fda_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("rel_resid_fp64", ctypes.c_double),
+                ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double), ("matvec_s", ctypes.c_double)]
+
+
+class fda_stats(ctypes.Structure):
+    _fields_ = [("n_elements", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_levels", ctypes.c_int64), ("nnz_near", ctypes.c_int64), ("n_m2l", ctypes.c_int64),
+                ("n_m2l_ops", ctypes.c_int64), ("bytes_near", ctypes.c_int64), ("bytes_far", ctypes.c_int64),
+                ("flops_far", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("level_regime", ctypes.c_int32 * 32), ("level_rank", ctypes.c_int32 * 32),
+                ("level_boxes", ctypes.c_int32 * 32), ("level_cones", ctypes.c_int32 * 32),
+                ("precompute_s", ctypes.c_double), ("tree_s", ctypes.c_double), ("near_s", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfdabem.so (built by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libfdabem.so not built (run paper_1403_4747_gb300.build.build()); "
+                           "there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i64, dbl, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    H = ctypes.c_void_p
+    lib.fda_default_config.argtypes = [ctypes.POINTER(fda_config)]
+    lib.fda_default_config.restype = None
+    lib.fda_create.argtypes = [ctypes.POINTER(fda_config), ctypes.POINTER(H)]
+    lib.fda_build_tree.argtypes = [H, vp, i64, vp, i64, dbl]
+    lib.fda_precompute_translations.argtypes = [H]
+    lib.fda_apply.argtypes = [H, vp, vp, cint, i64]
+    lib.fda_apply_host.argtypes = [H, vp, vp, cint, i64]
+    lib.fda_rhs_plane_wave.argtypes = [H, vp, cint, vp]
+    lib.fda_solve.argtypes = [H, vp, vp, cint, dbl, ctypes.POINTER(fda_info)]
+    lib.fda_get_stats.argtypes = [H, ctypes.POINTER(fda_stats)]
+    lib.fda_set_timing.argtypes = [H, cint]
+    lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
+    lib.fda_last_error.argtypes = [H]
+    lib.fda_last_error.restype = ctypes.c_char_p
+    lib.fda_destroy.argtypes = [H]
+    lib.fda_destroy.restype = None
+    for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
+                 "fda_rhs_plane_wave", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times"):
+        getattr(lib, name).restype = cint
+    _lib = lib
+    return lib
+
+
+class FDAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _check(h, st):
+    if st != FDA_OK:
+        raise FDAError(st, load().fda_last_error(h).decode() if h else "")
+
+
+def fda_default_config(**overrides) -> fda_config:
+    c = fda_config()
+    load().fda_default_config(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def fda_create(cfg: fda_config | None = None):
+    h = ctypes.c_void_p()
+    st = load().fda_create(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h))
+    if st != FDA_OK:
+        raise FDAError(st, "fda_create failed")
+    return h
+
+
+def fda_build_tree(h, verts, tris, k):
+    """verts: float64 [V,3], tris: int32 [N,3] host arrays (numpy)."""
+    import numpy as np
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    _check(h, load().fda_build_tree(h, v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0], float(k)))
+
+
+def fda_precompute_translations(h):
+    _check(h, load().fda_precompute_translations(h))
+
+
+def fda_apply(h, x_ptr, y_ptr, nrhs, ld):
+    """x_ptr, y_ptr: device addresses (e.g. torch complex128 tensor.data_ptr())."""
+    _check(h, load().fda_apply(h, x_ptr, y_ptr, int(nrhs), int(ld)))
+
+
+def fda_apply_host(h, x_ptr, y_ptr, nrhs, ld):
+    _check(h, load().fda_apply_host(h, x_ptr, y_ptr, int(nrhs), int(ld)))
+
+
+def fda_rhs_plane_wave(h, dirs, b_ptr):
+    import numpy as np
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    _check(h, load().fda_rhs_plane_wave(h, d.ctypes.data, d.shape[0], b_ptr))
+
+
+def fda_solve(h, b_ptr, x_ptr, nrhs, tol, raise_on_not_converged=True):
+    info = fda_info()
+    st = load().fda_solve(h, b_ptr, x_ptr, int(nrhs), float(tol), ctypes.byref(info))
+    if st != FDA_OK and (raise_on_not_converged or st != FDA_ERR_NOT_CONVERGED):
+        _check(h, st)
+    return info, st
+
+
+def fda_get_stats(h) -> fda_stats:
+    s = fda_stats()
+    _check(h, load().fda_get_stats(h, ctypes.byref(s)))
+    return s
+
+
+def fda_set_timing(h, enable=True):
+    _check(h, load().fda_set_timing(h, 1 if enable else 0))
+
+
+def fda_get_pass_times(h):
+    arr = (ctypes.c_float * 6)()
+    _check(h, load().fda_get_pass_times(h, arr))
+    return list(arr)
+
+
+def fda_last_error(h) -> str:
+    return load().fda_last_error(h).decode()
+
+
+def fda_destroy(h):
+    if h:
+        load().fda_destroy(h)

@@ -1,0 +1,373 @@
+// C-ABI entry points (include/fda_bem.h).  Each call validates its
+// arguments, runs on the handle's stream and converts failures into a
+// status code plus a message; no exception leaves this file.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "fda_internal.cuh"
+
+void fda_alloc_densities(fda_handle *h, int want32);
+void fda_near_convert_f32(fda_handle *h);
+void fda_far_convert_f32(fda_handle *h);
+
+int fda_debug_sync()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FDA_DEBUG_SYNC");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v;
+}
+
+namespace {
+
+template <typename F>
+fda_status guarded(fda_handle *h, F &&f)
+{
+    try {
+        f();
+        return FDA_OK;
+    } catch (const fda_error &e) {
+        if (h) h->err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        if (h) h->err = "host allocation failed";
+        return FDA_ERR_OOM;
+    } catch (...) {
+        if (h) h->err = "unexpected internal error";
+        return FDA_ERR_CUDA;
+    }
+}
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t handle_bytes(const fda_handle *h)
+{
+    size_t s = 0;
+    const dbuf *bufs[] = {&h->perm, &h->iperm, &h->verts9, &h->cent, &h->nrm, &h->area, &h->h2, &h->qpt, &h->qw,
+                          &h->keys, &h->box_begin, &h->box_end, &h->box_key, &h->box_coord, &h->box_parent,
+                          &h->box_child0, &h->box_child1, &h->box_leaf, &h->box_level, &h->leaf_box,
+                          &h->leaf_of_box, &h->il_ptr, &h->il_src, &h->il_op, &h->il_cone, &h->nr_ptr,
+                          &h->nr_begin, &h->nr_end, &h->nf_colptr, &h->nf_cols, &h->nf_off, &h->leaf_op_off,
+                          &h->op64.St, &h->op64.Tt, &h->op64.near, &h->op32.St, &h->op32.Tt, &h->op32.near,
+                          &h->xs, &h->ys, &h->xs32};
+    for (const dbuf *b : bufs) s += b->bytes;
+    for (int l = 0; l < FDA_MAX_LEVELS; ++l) {
+        s += h->eq_up[l].bytes + h->chk_up[l].bytes + h->rot[l].bytes + h->Uup[l].bytes + h->Vup[l].bytes +
+             h->sig[l].bytes;
+        s += h->op64.Kt[l].bytes + h->op64.Mt[l].bytes + h->op64.Lt[l].bytes;
+        s += h->op32.Kt[l].bytes + h->op32.Mt[l].bytes + h->op32.Lt[l].bytes;
+        s += h->q64[l].bytes + h->p64[l].bytes + h->q32[l].bytes + h->p32[l].bytes;
+    }
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fda_default_config(fda_config *c)
+{
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->eps = 1e-4;
+    c->p_lf = 8;
+    c->p_hf = 10;
+    c->hf_nr = 5;
+    c->hf_na = 300;
+    c->leaf_max = 64;
+    c->hf_wavelengths = 1.0;
+    c->rho_min = 2.2;
+    c->precision = FDA_PLAIN_FP64;
+    c->mode = FDA_MODE_FDA;
+    c->restart = 100;
+    c->maxit = 1000;
+    c->cuda_stream = nullptr;
+}
+
+fda_status fda_create(const fda_config *cfg, fda_handle **out)
+{
+    if (!out) return FDA_ERR_ARG;
+    *out = nullptr;
+    fda_config c;
+    if (cfg) c = *cfg; else fda_default_config(&c);
+    if (!(c.eps > 0 && c.eps <= 0.1) || c.leaf_max < 1 || c.leaf_max > 64 || c.p_lf < 3 || c.p_lf > 16 ||
+        c.p_hf < 3 || c.p_hf > 16 || c.hf_nr < 1 || c.hf_na < 8 || !(c.hf_wavelengths > 0) || !(c.rho_min >= 2.0) ||
+        (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
+        (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.maxit < 1)
+        return FDA_ERR_ARG;
+    fda_handle *h = new (std::nothrow) fda_handle();
+    if (!h) return FDA_ERR_OOM;
+    h->cfg = c;
+    h->stream = (cudaStream_t)c.cuda_stream;
+    fda_status st = guarded(h, [&] {
+        for (int i = 0; i < 8; ++i) FDA_CUDA(cudaEventCreate(&h->ev[i]));
+    });
+    if (st != FDA_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return FDA_OK;
+}
+
+fda_status fda_build_tree(fda_handle *h, const double *verts, int64_t nv, const int32_t *tris, int64_t nt, double k)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state != 0) {
+        h->err = "fda_build_tree called twice on one handle";
+        return FDA_ERR_STATE;
+    }
+    if (!verts || !tris || nv < 3 || nt < 1 || nt > (int64_t)INT32_MAX / 2 || !(k > 0) || !std::isfinite(k) ||
+        (h->cfg.mode == FDA_MODE_DENSE && nt > 65535)) {
+        h->err = "invalid mesh or wavenumber";
+        return FDA_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        double t0 = now_s();
+        h->k = k;
+        fda_geometry_build(h, verts, nv, tris, nt);
+        fda_tree_build(h);
+        h->tree_s = now_s() - t0;
+        h->state = 1;
+    });
+}
+
+fda_status fda_precompute_translations(fda_handle *h)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state != 1) {
+        h->err = "fda_precompute_translations needs fda_build_tree first (and runs once)";
+        return FDA_ERR_STATE;
+    }
+    return guarded(h, [&] {
+        double t0 = now_s();
+        fda_near_build(h);
+        h->near_s = now_s() - t0;
+        fda_far_precompute(h);
+        int want32 = h->cfg.precision == FDA_CHOSEN_FP32;
+        if (want32) {
+            fda_near_convert_f32(h);
+            fda_far_convert_f32(h);
+            h->have32 = 1;
+        }
+        fda_alloc_densities(h, want32);
+        h->xs.alloc(sizeof(c64d) * h->N);
+        h->ys.alloc(sizeof(c64d) * h->N);
+        FDA_CUDA(cudaStreamSynchronize(h->stream));
+        h->precompute_s = now_s() - t0;
+        h->state = 2;
+    });
+}
+
+fda_status fda_apply(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, int64_t ld)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = "fda_apply before fda_precompute_translations";
+        return FDA_ERR_STATE;
+    }
+    if (!x || !y || nrhs < 1 || ld < h->N) {
+        h->err = "invalid apply arguments";
+        return FDA_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        for (int m = 0; m < nrhs; ++m) {
+            const c64d *xm = reinterpret_cast<const c64d *>(x) + (int64_t)m * ld;
+            c64d *ym = reinterpret_cast<c64d *>(y) + (int64_t)m * ld;
+            fda_gather_to_sorted(h, xm, h->xs.as<c64d>());
+            fda_apply_sorted(h, h->xs.as<c64d>(), h->ys.as<c64d>(), h->cfg.precision);
+            fda_scatter_from_sorted(h, h->ys.as<c64d>(), ym);
+        }
+    });
+}
+
+fda_status fda_apply_host(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, int64_t ld)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = "fda_apply_host before fda_precompute_translations";
+        return FDA_ERR_STATE;
+    }
+    if (!x || !y || nrhs < 1 || ld < h->N) {
+        h->err = "invalid apply arguments";
+        return FDA_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        dbuf dx, dy;
+        dx.alloc(sizeof(c64d) * h->N);
+        dy.alloc(sizeof(c64d) * h->N);
+        for (int m = 0; m < nrhs; ++m) {
+            FDA_CUDA(cudaMemcpyAsync(dx.p, x + (int64_t)m * ld, sizeof(c64d) * h->N, cudaMemcpyHostToDevice,
+                                     h->stream));
+            fda_gather_to_sorted(h, dx.as<c64d>(), h->xs.as<c64d>());
+            fda_apply_sorted(h, h->xs.as<c64d>(), h->ys.as<c64d>(), h->cfg.precision);
+            fda_scatter_from_sorted(h, h->ys.as<c64d>(), dy.as<c64d>());
+            FDA_CUDA(cudaMemcpyAsync(y + (int64_t)m * ld, dy.p, sizeof(c64d) * h->N, cudaMemcpyDeviceToHost,
+                                     h->stream));
+        }
+        FDA_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state < 1) {
+        h->err = "fda_rhs_plane_wave before fda_build_tree";
+        return FDA_ERR_STATE;
+    }
+    if (!dirs || !b || nrhs < 1) {
+        h->err = "invalid right-hand-side arguments";
+        return FDA_ERR_ARG;
+    }
+    for (int m = 0; m < nrhs; ++m) {
+        double n2 = dirs[3 * m] * dirs[3 * m] + dirs[3 * m + 1] * dirs[3 * m + 1] + dirs[3 * m + 2] * dirs[3 * m + 2];
+        if (!(fabs(n2 - 1.0) < 1e-6)) {
+            h->err = "incidence directions must be unit vectors";
+            return FDA_ERR_ARG;
+        }
+    }
+    return guarded(h, [&] {
+        dbuf dd, bs;
+        dd.alloc(sizeof(double) * 3 * nrhs);
+        bs.alloc(sizeof(c64d) * h->N * nrhs);
+        FDA_CUDA(cudaMemcpyAsync(dd.p, dirs, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, h->stream));
+        fda_rhs_sorted(h, dd.as<double>(), nrhs, bs.as<c64d>());
+        for (int m = 0; m < nrhs; ++m)
+            fda_scatter_from_sorted(h, bs.as<c64d>() + (int64_t)m * h->N, reinterpret_cast<c64d *>(b) + (int64_t)m * h->N);
+        FDA_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+fda_status fda_solve(fda_handle *h, const fda_c128 *b, fda_c128 *x, int nrhs, double tol, fda_info *info)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = "fda_solve before fda_precompute_translations";
+        return FDA_ERR_STATE;
+    }
+    if (!b || !x || nrhs < 1 || !(tol > 0) || !(tol < 1)) {
+        h->err = "invalid solve arguments";
+        return FDA_ERR_ARG;
+    }
+    fda_status last = FDA_OK;
+    fda_status st = guarded(h, [&] {
+        for (int m = 0; m < nrhs; ++m) {
+            fda_status s = fda_solve_impl(h, reinterpret_cast<const c64d *>(b) + (int64_t)m * h->N,
+                                          reinterpret_cast<c64d *>(x) + (int64_t)m * h->N, tol, info);
+            if (s != FDA_OK) last = s;
+        }
+    });
+    return st != FDA_OK ? st : last;
+}
+
+fda_status fda_get_stats(fda_handle *h, fda_stats *out)
+{
+    if (!h || !out) return FDA_ERR_ARG;
+    if (h->state < 1) {
+        h->err = "fda_get_stats before fda_build_tree";
+        return FDA_ERR_STATE;
+    }
+    memset(out, 0, sizeof(*out));
+    return guarded(h, [&] {
+        out->n_elements = h->N;
+        out->n_boxes = h->nbox_total;
+        out->n_leaves = h->nleaf;
+        out->n_levels = h->nlev;
+        out->nnz_near = h->nnz_near;
+        out->n_m2l = h->n_il_total;
+        int64_t ops = 0;
+        for (int l = 0; l < 32; ++l) {
+            out->level_regime[l] = l < h->nlev ? h->lev[l].hf : -1;
+            out->level_rank[l] = l < h->nlev ? h->lev[l].T : 0;
+            out->level_boxes[l] = l < h->nlev ? h->lev[l].nbox : 0;
+            out->level_cones[l] = l < h->nlev ? h->lev[l].ncones : 0;
+            if (l < h->nlev) ops += h->lev[l].n_ops;
+        }
+        out->n_m2l_ops = ops;
+        int rb = h->cfg.precision == FDA_CHOSEN_FP32 ? 8 : 16;
+        out->bytes_near = h->nnz_near * rb;
+        // far-field flop count (real flops, 8 per complex multiply-add)
+        if (h->state == 2 && h->lev_lo >= 0) {
+            std::vector<int32_t> leaf(h->nbox_total), c0(h->nbox_total), c1(h->nbox_total), beg(h->nbox_total),
+                end(h->nbox_total);
+            std::vector<int64_t> ilp(h->nbox_total + 1);
+            FDA_CUDA(cudaMemcpy(leaf.data(), h->box_leaf.p, 4 * leaf.size(), cudaMemcpyDeviceToHost));
+            FDA_CUDA(cudaMemcpy(c0.data(), h->box_child0.p, 4 * c0.size(), cudaMemcpyDeviceToHost));
+            FDA_CUDA(cudaMemcpy(c1.data(), h->box_child1.p, 4 * c1.size(), cudaMemcpyDeviceToHost));
+            FDA_CUDA(cudaMemcpy(beg.data(), h->box_begin.p, 4 * beg.size(), cudaMemcpyDeviceToHost));
+            FDA_CUDA(cudaMemcpy(end.data(), h->box_end.p, 4 * end.size(), cudaMemcpyDeviceToHost));
+            FDA_CUDA(cudaMemcpy(ilp.data(), h->il_ptr.p, 8 * ilp.size(), cudaMemcpyDeviceToHost));
+            double fl = 0, by = 0;
+            int cb = h->cfg.precision == FDA_CHOSEN_FP32 ? 8 : 16;
+            for (int l = h->lev_lo; l < h->nlev; ++l) {
+                const level_info &L = h->lev[l];
+                double T = L.T;
+                for (int b = L.box0; b < L.box0 + L.nbox; ++b) {
+                    double nB = end[b] - beg[b];
+                    if (leaf[b]) {
+                        fl += 2 * 8.0 * T * nB;  // S2M + L2T
+                        by += 2.0 * cb * 64 * T;
+                    } else if (l + 1 < h->nlev) {
+                        fl += 8.0 * T * h->lev[l + 1].T * (c1[b] - c0[b]) * L.ncones;  // M2M
+                    }
+                    if (l > h->lev_lo) fl += 8.0 * T * h->lev[l - 1].T * h->lev[l - 1].ncones;  // L2L (upper bound)
+                    fl += 8.0 * T * T * (double)(ilp[b + 1] - ilp[b]);                         // M2L
+                }
+                by += (double)cb * L.n_ops * T * T;                 // distinct K~
+                by += 2.0 * 2.0 * cb * L.nbox * L.ncones * T;       // q~ and p~ written and read
+            }
+            out->flops_far = (int64_t)fl;
+            out->bytes_far = (int64_t)by;
+        }
+        out->device_bytes = (int64_t)handle_bytes(h);
+        out->tree_s = h->tree_s;
+        out->near_s = h->near_s;
+        out->precompute_s = h->precompute_s;
+    });
+}
+
+fda_status fda_set_timing(fda_handle *h, int enable)
+{
+    if (!h) return FDA_ERR_ARG;
+    h->timing = enable ? 1 : 0;
+    return FDA_OK;
+}
+
+fda_status fda_get_pass_times(fda_handle *h, float out[6])
+{
+    if (!h || !out) return FDA_ERR_ARG;
+    if (!h->timing) {
+        h->err = "pass timing is off (fda_set_timing)";
+        return FDA_ERR_STATE;
+    }
+    for (int i = 0; i < 6; ++i) out[i] = h->pass_ms[i];
+    return FDA_OK;
+}
+
+const char *fda_last_error(const fda_handle *h)
+{
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+void fda_destroy(fda_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+    for (int i = 0; i < 8; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,356 @@
+// One FDA matrix-vector product (Sec. 3.3 Steps 2-4) on the device:
+//   near field (S2T, Step 4) -> y
+//   upward pass (Step 2): S2M at leaves, M2M bottom-up (per cone at
+//       high-frequency levels; a high-frequency parent takes each child's
+//       cone that contains its own cone, or the child's non-directional
+//       densities if the child is low-frequency)
+//   downward pass (Step 3): M2L at every level, then L2L top-down (a
+//       low-frequency child sums all of its high-frequency parent's cones)
+//   L2T at leaves -> y += ...
+// Densities are kept in the compressed coordinates of Sec. 4 (q~ of rank T
+// per box and cone; p~ = U_dn^H p).  Every pass is templated on the real
+// type: double (plain FP64 form) or float (chosen form: FP32 operators and
+// densities, FP32 accumulation, the result added into the FP64 output).
+#include "fda_internal.cuh"
+
+namespace {
+
+constexpr int AT = 256;    // threads per CTA
+constexpr int MAXR = 4;    // rows per thread (rank <= 1024)
+constexpr int MAXT = AT * MAXR;
+
+template <typename R>
+struct lvl_ptrs {
+    int box0[FDA_MAX_LEVELS], nbox[FDA_MAX_LEVELS], T[FDA_MAX_LEVELS], ncones[FDA_MAX_LEVELS];
+    int nc[FDA_MAX_LEVELS], hf[FDA_MAX_LEVELS];
+    cx<R> *q[FDA_MAX_LEVELS];
+    cx<R> *p[FDA_MAX_LEVELS];
+    const cx<R> *Kt[FDA_MAX_LEVELS];
+    const cx<R> *Mt[FDA_MAX_LEVELS];
+    const cx<R> *Lt[FDA_MAX_LEVELS];
+};
+
+template <typename R>
+__device__ inline int child_cone_dev(const lvl_ptrs<R> &P, int l, int u)
+{
+    int ncp = P.nc[l], ncc = P.nc[l + 1];
+    int face = u / (ncp * ncp), rem = u % (ncp * ncp);
+    int a = rem / ncp, b = rem % ncp;
+    int f = ncp / ncc;
+    return face * ncc * ncc + (a / f) * ncc + (b / f);
+}
+
+__device__ inline int octant_of(const int32_t *coord, int b)
+{
+    return ((coord[3 * b] & 1) << 2) | ((coord[3 * b + 1] & 1) << 1) | (coord[3 * b + 2] & 1);
+}
+
+template <typename R>
+__device__ inline cx<R> ldx(const void *x, int64_t i, int x64)
+{
+    if (x64) {
+        c64d v = ((const c64d *)x)[i];
+        return cx<R>((R)v.re, (R)v.im);
+    }
+    c32f v = ((const c32f *)x)[i];
+    return cx<R>((R)v.re, (R)v.im);
+}
+
+// ---- Step 4: near field, y = A_near x (overwrites y)
+template <typename R>
+__global__ void k_near_apply(const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend,
+                             const int64_t *colptr, const int64_t *rptr, const int32_t *rb, const int32_t *re,
+                             const int64_t *off, const cx<R> *A, const void *x, int x64, c64d *y)
+{
+    int li = blockIdx.x;
+    int B = leaf_box[li];
+    int i0 = bbeg[B], nB = bend[B] - i0;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int r = blockIdx.y * (AT / 32) + warp;
+    if (r >= nB) return;
+    int64_t nc = colptr[li + 1] - colptr[li];
+    const cx<R> *row = A + off[li] + (int64_t)r * nc;
+    cx<R> acc;
+    int64_t coff = 0;
+    for (int64_t g = rptr[li]; g < rptr[li + 1]; ++g) {
+        int b = rb[g], len = re[g] - b;
+        for (int c = lane; c < len; c += 32) cfma(acc, row[coff + c], ldx<R>(x, b + c, x64));
+        coff += len;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+        acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) y[i0 + r] = c64d((double)acc.re, (double)acc.im);
+}
+
+// ---- Step 2: S2M at leaves, q~ = S~ x_B
+template <typename R>
+__global__ void k_s2m(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *blev, const int32_t *bbeg,
+                      const int32_t *bend, const int64_t *loff, const cx<R> *St, const void *x, int x64)
+{
+    __shared__ cx<R> xs[64];
+    int li = blockIdx.x;
+    int B = leaf_box[li];
+    int l = blev[B];
+    int T = P.T[l];
+    if (T == 0) return;
+    int j0 = bbeg[B], nB = bend[B] - j0;
+    for (int j = threadIdx.x; j < nB; j += blockDim.x) xs[j] = ldx<R>(x, j0 + j, x64);
+    __syncthreads();
+    const cx<R> *S = St + loff[li];
+    cx<R> *q = P.q[l] + (int64_t)(B - P.box0[l]) * T;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        cx<R> acc;
+        for (int j = 0; j < nB; ++j) cfma(acc, S[(int64_t)j * T + t], xs[j]);
+        q[t] = acc;
+    }
+}
+
+// ---- Step 2: M2M into parent level l
+template <typename R>
+__global__ void k_m2m(lvl_ptrs<R> P, int l, const int32_t *bleaf, const int32_t *c0, const int32_t *c1,
+                      const int32_t *coord)
+{
+    __shared__ cx<R> qc[MAXT];
+    int b = P.box0[l] + blockIdx.x;
+    int u = blockIdx.y;
+    if (bleaf[b]) return;
+    const int Tp = P.T[l], Tc = P.T[l + 1], ncp = P.ncones[l], ncc = P.ncones[l + 1];
+    cx<R> acc[MAXR];
+    for (int c = c0[b]; c < c1[b]; ++c) {
+        int o = octant_of(coord, c);
+        int uc = P.hf[l + 1] ? child_cone_dev(P, l, u) : 0;
+        const cx<R> *src = P.q[l + 1] + ((int64_t)(c - P.box0[l + 1]) * ncc + uc) * Tc;
+        __syncthreads();
+        for (int j = threadIdx.x; j < Tc; j += blockDim.x) qc[j] = src[j];
+        __syncthreads();
+        const cx<R> *M = P.Mt[l] + (int64_t)(o * ncp + u) * Tp * Tc;
+        for (int r = 0; r < MAXR; ++r) {
+            int t = threadIdx.x + r * blockDim.x;
+            if (t >= Tp) break;
+            cx<R> a = acc[r];
+            for (int j = 0; j < Tc; ++j) cfma(a, M[(int64_t)j * Tp + t], qc[j]);
+            acc[r] = a;
+        }
+    }
+    cx<R> *dst = P.q[l] + ((int64_t)(b - P.box0[l]) * ncp + u) * Tp;
+    for (int r = 0; r < MAXR; ++r) {
+        int t = threadIdx.x + r * blockDim.x;
+        if (t < Tp) dst[t] = acc[r];
+    }
+}
+
+// ---- Step 3: M2L at level l (writes p~)
+template <typename R>
+__global__ void k_m2l(lvl_ptrs<R> P, int l, const int64_t *ilp, const int32_t *ils, const int32_t *ilo,
+                      const int32_t *ilc)
+{
+    __shared__ cx<R> qs[MAXT];
+    int b = P.box0[l] + blockIdx.x;
+    int u = blockIdx.y;
+    const int T = P.T[l], nc = P.ncones[l];
+    cx<R> acc[MAXR];
+    for (int64_t e = ilp[b]; e < ilp[b + 1]; ++e) {
+        int cw = ilc[e];
+        if ((cw & 0xffff) != u) continue;
+        int su = cw >> 16;
+        const cx<R> *src = P.q[l] + ((int64_t)(ils[e] - P.box0[l]) * nc + su) * T;
+        __syncthreads();
+        for (int j = threadIdx.x; j < T; j += blockDim.x) qs[j] = src[j];
+        __syncthreads();
+        const cx<R> *K = P.Kt[l] + (int64_t)ilo[e] * T * T;
+        for (int r = 0; r < MAXR; ++r) {
+            int t = threadIdx.x + r * blockDim.x;
+            if (t >= T) break;
+            cx<R> a = acc[r];
+            for (int j = 0; j < T; ++j) cfma(a, K[(int64_t)j * T + t], qs[j]);
+            acc[r] = a;
+        }
+    }
+    cx<R> *dst = P.p[l] + ((int64_t)(b - P.box0[l]) * nc + u) * T;
+    for (int r = 0; r < MAXR; ++r) {
+        int t = threadIdx.x + r * blockDim.x;
+        if (t < T) dst[t] = acc[r];
+    }
+}
+
+// ---- Step 3: L2L from parent level l into child level l+1 (adds to p~)
+template <typename R>
+__global__ void k_l2l(lvl_ptrs<R> P, int l, const int32_t *bpar, const int32_t *coord)
+{
+    __shared__ cx<R> pp[MAXT];
+    int c = P.box0[l + 1] + blockIdx.x;
+    int uc = blockIdx.y;
+    int par = bpar[c];
+    int o = octant_of(coord, c);
+    const int Tp = P.T[l], Tc = P.T[l + 1], ncp = P.ncones[l], ncc = P.ncones[l + 1];
+    cx<R> acc[MAXR];
+    for (int u = 0; u < ncp; ++u) {
+        if (P.hf[l + 1] && child_cone_dev(P, l, u) != uc) continue;
+        const cx<R> *src = P.p[l] + ((int64_t)(par - P.box0[l]) * ncp + u) * Tp;
+        __syncthreads();
+        for (int j = threadIdx.x; j < Tp; j += blockDim.x) pp[j] = src[j];
+        __syncthreads();
+        const cx<R> *Lm = P.Lt[l] + (int64_t)(o * ncp + u) * Tc * Tp;
+        for (int r = 0; r < MAXR; ++r) {
+            int t = threadIdx.x + r * blockDim.x;
+            if (t >= Tc) break;
+            cx<R> a = acc[r];
+            for (int j = 0; j < Tp; ++j) cfma(a, Lm[(int64_t)j * Tc + t], pp[j]);
+            acc[r] = a;
+        }
+    }
+    cx<R> *dst = P.p[l + 1] + ((int64_t)(c - P.box0[l + 1]) * ncc + uc) * Tc;
+    for (int r = 0; r < MAXR; ++r) {
+        int t = threadIdx.x + r * blockDim.x;
+        if (t < Tc) dst[t] = dst[t] + acc[r];
+    }
+}
+
+// ---- Step 3: L2T at leaves, y += T~ p~
+template <typename R>
+__global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *blev, const int32_t *bbeg,
+                      const int32_t *bend, const int64_t *loff, const cx<R> *Tt, c64d *y)
+{
+    __shared__ cx<R> pp[MAXT];
+    int li = blockIdx.x;
+    int B = leaf_box[li];
+    int l = blev[B];
+    int T = P.T[l];
+    if (T == 0) return;
+    int i0 = bbeg[B], nB = bend[B] - i0;
+    const cx<R> *src = P.p[l] + (int64_t)(B - P.box0[l]) * T;
+    for (int j = threadIdx.x; j < T; j += blockDim.x) pp[j] = src[j];
+    __syncthreads();
+    const cx<R> *Tm = Tt + loff[li];
+    for (int i = threadIdx.x; i < nB; i += blockDim.x) {
+        cx<R> acc;
+        for (int t = 0; t < T; ++t) cfma(acc, Tm[(int64_t)t * 64 + i], pp[t]);
+        c64d v = y[i0 + i];
+        y[i0 + i] = c64d(v.re + (double)acc.re, v.im + (double)acc.im);
+    }
+}
+
+__global__ void k_c64_to_c32(const c64d *a, c32f *b, int64_t n)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = c32f((float)a[t].re, (float)a[t].im);
+}
+
+template <typename R>
+lvl_ptrs<R> make_ptrs(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p)
+{
+    lvl_ptrs<R> P;
+    for (int l = 0; l < FDA_MAX_LEVELS; ++l) {
+        P.box0[l] = l < h->nlev ? h->lev[l].box0 : 0;
+        P.nbox[l] = l < h->nlev ? h->lev[l].nbox : 0;
+        P.T[l] = (l < h->nlev && h->lev[l].active) ? h->lev[l].T : 0;
+        P.ncones[l] = l < h->nlev ? h->lev[l].ncones : 1;
+        P.nc[l] = l < h->nlev ? h->lev[l].nc : 0;
+        P.hf[l] = l < h->nlev ? h->lev[l].hf : 0;
+        P.q[l] = q[l].as<cx<R>>();
+        P.p[l] = p[l].as<cx<R>>();
+        P.Kt[l] = ops.Kt[l].template as<cx<R>>();
+        P.Mt[l] = ops.Mt[l].template as<cx<R>>();
+        P.Lt[l] = ops.Lt[l].template as<cx<R>>();
+    }
+    return P;
+}
+
+template <typename R>
+void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x, int x64, c64d *y)
+{
+    cudaStream_t s = h->stream;
+    const int NL = h->nleaf;
+    auto mark = [&](int i) {
+        if (h->timing) FDA_CUDA(cudaEventRecord(h->ev[i], s));
+    };
+    mark(0);
+    const int max_rows = h->max_leaf_rows;
+    dim3 gn(NL, (max_rows + AT / 32 - 1) / (AT / 32));
+    k_near_apply<R><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+                                      h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
+                                      h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(), h->nr_end.as<int32_t>(),
+                                      h->nf_off.as<int64_t>(), ops.near.template as<cx<R>>(), x, x64, y);
+    FDA_CHECK_LAUNCH();
+    mark(1);
+    if (h->lev_lo < 0) {
+        for (int i = 2; i <= 6; ++i) mark(i);
+        return;
+    }
+    lvl_ptrs<R> P = make_ptrs<R>(h, ops, q, p);
+    k_s2m<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
+                               h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(),
+                               ops.St.template as<cx<R>>(), x, x64);
+    FDA_CHECK_LAUNCH();
+    mark(2);
+    for (int l = h->nlev - 2; l >= h->lev_lo; --l) {
+        dim3 g(h->lev[l].nbox, h->lev[l].ncones);
+        k_m2m<R><<<g, AT, 0, s>>>(P, l, h->box_leaf.as<int32_t>(), h->box_child0.as<int32_t>(),
+                                  h->box_child1.as<int32_t>(), h->box_coord.as<int32_t>());
+        FDA_CHECK_LAUNCH();
+    }
+    mark(3);
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        dim3 g(h->lev[l].nbox, h->lev[l].ncones);
+        k_m2l<R><<<g, AT, 0, s>>>(P, l, h->il_ptr.as<int64_t>(), h->il_src.as<int32_t>(), h->il_op.as<int32_t>(),
+                                  h->il_cone.as<int32_t>());
+        FDA_CHECK_LAUNCH();
+    }
+    mark(4);
+    for (int l = h->lev_lo; l + 1 < h->nlev; ++l) {
+        dim3 g(h->lev[l + 1].nbox, h->lev[l + 1].ncones);
+        k_l2l<R><<<g, AT, 0, s>>>(P, l, h->box_parent.as<int32_t>(), h->box_coord.as<int32_t>());
+        FDA_CHECK_LAUNCH();
+    }
+    mark(5);
+    k_l2t<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
+                               h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(), ops.Tt.template as<cx<R>>(),
+                               y);
+    FDA_CHECK_LAUNCH();
+    mark(6);
+}
+
+}  // namespace
+
+void fda_alloc_densities(fda_handle *h, int want32)
+{
+    for (int l = 0; l < h->nlev; ++l) {
+        const level_info &L = h->lev[l];
+        if (!L.active || L.T == 0) continue;
+        size_t n = (size_t)L.nbox * L.ncones * L.T;
+        h->q64[l].alloc(sizeof(c64d) * n);
+        h->p64[l].alloc(sizeof(c64d) * n);
+        if (want32) {
+            h->q32[l].alloc(sizeof(c32f) * n);
+            h->p32[l].alloc(sizeof(c32f) * n);
+        }
+    }
+}
+
+// ys = A xs, both complex double in Morton order
+void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision)
+{
+    if (precision == FDA_CHOSEN_FP32) {
+        if (!h->have32) fda_fail(FDA_ERR_STATE, "FP32 operators were not built (precision = plain)");
+        if (!h->xs32.p) h->xs32.alloc(sizeof(c32f) * h->N);
+        k_c64_to_c32<<<fda_blocks(h->N, 256), 256, 0, h->stream>>>(xs, h->xs32.as<c32f>(), h->N);
+        FDA_CHECK_LAUNCH();
+        apply_impl<float>(h, h->op32, h->q32, h->p32, h->xs32.p, 0, ys);
+    } else {
+        apply_impl<double>(h, h->op64, h->q64, h->p64, xs, 1, ys);
+    }
+    if (h->timing) {
+        FDA_CUDA(cudaEventSynchronize(h->ev[6]));
+        float t[6];
+        for (int i = 0; i < 6; ++i) FDA_CUDA(cudaEventElapsedTime(&t[i], h->ev[i], h->ev[i + 1]));
+        // events: near | S2M | M2M | M2L | L2L | L2T
+        h->pass_ms[5] = t[0];
+        h->pass_ms[0] = t[1];
+        h->pass_ms[1] = t[2];
+        h->pass_ms[2] = t[3];
+        h->pass_ms[3] = t[4];
+        h->pass_ms[4] = t[5];
+    }
+}

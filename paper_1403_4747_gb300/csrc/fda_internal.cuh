@@ -1,0 +1,244 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fda_bem.h"
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on interleaved (re, im) pairs
+// ---------------------------------------------------------------------------
+template <typename T>
+struct cx {
+    T re, im;
+    __host__ __device__ cx() : re(0), im(0) {}
+    __host__ __device__ cx(T r, T i) : re(r), im(i) {}
+};
+template <typename T> __host__ __device__ inline cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __host__ __device__ inline cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __host__ __device__ inline cx<T> operator*(cx<T> a, cx<T> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> __host__ __device__ inline cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __host__ __device__ inline cx<T> conjg(cx<T> a) { return {a.re, -a.im}; }
+// a += b * c
+template <typename T> __host__ __device__ inline void cfma(cx<T> &a, cx<T> b, cx<T> c)
+{
+    a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
+    a.im = fma(b.re, c.im, fma(b.im, c.re, a.im));
+}
+// a += conj(b) * c
+template <typename T> __host__ __device__ inline void cfma_conj(cx<T> &a, cx<T> b, cx<T> c)
+{
+    a.re = fma(b.re, c.re, fma(b.im, c.im, a.re));
+    a.im = fma(b.re, c.im, fma(-b.im, c.re, a.im));
+}
+
+typedef cx<double> c64d;  // complex double
+typedef cx<float> c32f;   // complex float
+
+#define FDA_PI 3.14159265358979323846
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+struct fda_error {
+    fda_status st;
+    std::string msg;
+};
+
+#define FDA_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw fda_error{e_ == cudaErrorMemoryAllocation ? FDA_ERR_OOM : FDA_ERR_CUDA,     \
+                            std::string(#call) + ": " + cudaGetErrorString(e_)};              \
+    } while (0)
+
+// FDA_DEBUG_SYNC=1 in the environment makes every launch check synchronous,
+// so that a failing kernel is reported at its own launch site.
+int fda_debug_sync();
+#define FDA_CHECK_LAUNCH()                                                                    \
+    do {                                                                                      \
+        FDA_CUDA(cudaGetLastError());                                                         \
+        if (fda_debug_sync()) {                                                               \
+            cudaError_t e2_ = cudaDeviceSynchronize();                                        \
+            if (e2_ != cudaSuccess)                                                           \
+                throw fda_error{FDA_ERR_CUDA, std::string(__FILE__) + ":" +                   \
+                                                  std::to_string(__LINE__) + ": " +           \
+                                                  cudaGetErrorString(e2_)};                   \
+        }                                                                                     \
+    } while (0)
+
+inline void fda_fail(fda_status st, const std::string &m) { throw fda_error{st, m}; }
+
+// ---------------------------------------------------------------------------
+// device buffer owned by the handle
+// ---------------------------------------------------------------------------
+struct dbuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    dbuf() {}
+    dbuf(const dbuf &) = delete;
+    dbuf &operator=(const dbuf &) = delete;
+    ~dbuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void alloc(size_t b)
+    {
+        release();
+        if (b == 0) b = 16;
+        FDA_CUDA(cudaMalloc(&p, b));
+        bytes = b;
+    }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// a small fixed-capacity array of buffers, one per octree level
+constexpr int FDA_MAX_LEVELS = 24;
+
+// ---------------------------------------------------------------------------
+// per-level description
+// ---------------------------------------------------------------------------
+struct level_info {
+    int nbox = 0;        // boxes at this level
+    int box0 = 0;        // offset of the level in the concatenated box arrays
+    int nleaf = 0;
+    double w = 0;        // box width
+    int hf = 0;          // high-frequency regime
+    int nc = 0;          // cells per cube-face edge (high frequency); cones = 6 nc^2
+    int ncones = 1;      // 1 for low frequency
+    double rho = 0;      // high-frequency far-field distance in widths
+    int T = 0;           // retained rank (0: level has no far-field operators)
+    int n_eq = 0, n_chk = 0;  // upward equivalent / check point counts
+    int active = 0;      // densities are needed at this level
+    int n_il = 0;        // interaction-list entries at this level
+    int n_ops = 0;       // distinct M2L operators at this level
+    int R_off = 0;       // offsets of the dense offset table lie in [-R_off, R_off]^3
+};
+
+template <typename T>
+struct far_ops {
+    // per level (index = level)
+    dbuf Kt[FDA_MAX_LEVELS];     // [n_ops][T][T] column-major (K[j*T + i] = K~_ij)
+    dbuf Mt[FDA_MAX_LEVELS];     // parent level: [8 * ncones][T_child][T] column-major
+    dbuf Lt[FDA_MAX_LEVELS];     // parent level: [8 * ncones][T][T_child] column-major (rows = child rank)
+    dbuf St;                     // per leaf: [n_B][T] (S~ transposed)
+    dbuf Tt;                     // per leaf: [T][n_B] (T~ column-major)
+    dbuf near;                   // near-field blocks, row-major per leaf
+};
+
+struct fda_handle {
+    fda_config cfg;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int state = 0;  // 0 created, 1 tree built, 2 precomputed
+
+    // problem
+    double k = 0, lambda = 0;
+    int64_t N = 0, NV = 0;
+    double root_lo[3] = {0, 0, 0};
+    double W = 0, diam = 0;
+
+    // geometry in Morton order (device)
+    dbuf perm;      // int32 [N]: sorted position -> caller index
+    dbuf iperm;     // int32 [N]: caller index -> sorted position
+    dbuf verts9;    // double [N][9] triangle vertices
+    dbuf cent;      // double [N][3]
+    dbuf nrm;       // double [N][3] normal into the body
+    dbuf area;      // double [N]
+    dbuf h2;        // double [N] squared longest edge
+    dbuf qpt;       // double [N][6][3] regular-rule quadrature points
+    dbuf qw;        // double [N][6] weights (area included)
+    dbuf keys;      // uint64 [N] sorted Morton keys
+
+    // tree (device, concatenated over levels)
+    int nlev = 0;
+    level_info lev[FDA_MAX_LEVELS];
+    int nbox_total = 0;
+    dbuf box_begin, box_end;   // int32 element ranges
+    dbuf box_key;              // uint64 Morton prefix at the box's level
+    dbuf box_coord;            // int32 [nbox][3]
+    dbuf box_parent;           // int32 global index (-1 root)
+    dbuf box_child0, box_child1;  // int32 global child range [c0, c1)
+    dbuf box_leaf;             // int32 flag
+    dbuf box_level;            // int32
+    int nleaf = 0;
+    int max_leaf_rows = 0;     // largest leaf (elements)
+    dbuf leaf_box;             // int32 [nleaf] global box index
+    std::vector<int> h_leaf_level;  // leaf index -> level (host)
+    dbuf leaf_of_box;          // int32 [nbox]: leaf index or -1
+
+    // interaction lists (CSR over global boxes): source box (global) and operator index
+    dbuf il_ptr, il_src, il_op, il_cone;  // il_cone: target cone (high frequency) or 0
+    int64_t n_il_total = 0;
+    // near-field lists (CSR over leaves): source element ranges
+    dbuf nr_ptr, nr_begin, nr_end;
+    dbuf nf_colptr;            // int64 [nleaf+1]: column offsets per leaf
+    dbuf nf_cols;              // int32 [total cols]: sorted source element of each column
+    dbuf nf_off;               // int64 [nleaf+1]: entry offsets per leaf block
+    int64_t nnz_near = 0, ncols_total = 0;
+
+    // canonical point sets per level (device, box-relative, scaled)
+    dbuf eq_up[FDA_MAX_LEVELS], chk_up[FDA_MAX_LEVELS];
+    dbuf rot[FDA_MAX_LEVELS];  // double [ncones][9] cone rotations (high frequency)
+    // truncated SVD of G_up per level (FP64)
+    dbuf Uup[FDA_MAX_LEVELS];  // [n_chk][T] column-major? stored as [T][n_chk] (column j contiguous)
+    dbuf Vup[FDA_MAX_LEVELS];  // [T][n_eq]
+    dbuf sig[FDA_MAX_LEVELS];  // [T]
+    std::vector<int> leaf_T_off;   // per leaf: offset into St / Tt (elements)
+    dbuf leaf_op_off;          // int64 [nleaf]
+
+    far_ops<double> op64;
+    far_ops<float> op32;
+    int have32 = 0;
+
+    // densities (per level, [nbox][ncones][T])
+    dbuf q64[FDA_MAX_LEVELS], p64[FDA_MAX_LEVELS];
+    dbuf q32[FDA_MAX_LEVELS], p32[FDA_MAX_LEVELS];
+    int lev_lo = -1;           // coarsest level with interaction-list entries
+    std::vector<int3> h_ops[FDA_MAX_LEVELS];  // per level: offset of each distinct M2L operator
+
+    // timing
+    int timing = 0;
+    cudaEvent_t ev[8] = {};
+    float pass_ms[6] = {0, 0, 0, 0, 0, 0};
+    double tree_s = 0, precompute_s = 0, near_s = 0;
+
+    // workspace
+    dbuf work64;               // general FP64 workspace (x staging etc.)
+    dbuf xs, ys;               // sorted-order staging vectors (complex double)
+    dbuf xs32;                 // sorted-order complex float staging
+    dbuf solve_ws;             // GMRES basis
+    dbuf red;                  // reduction scratch
+};
+
+// ---------------------------------------------------------------------------
+// entry points between translation units
+// ---------------------------------------------------------------------------
+void fda_geometry_build(fda_handle *h, const double *verts, int64_t nv, const int32_t *tris, int64_t nt);
+void fda_tree_build(fda_handle *h);
+void fda_near_build(fda_handle *h);
+void fda_far_precompute(fda_handle *h);
+void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision);
+void fda_rhs_sorted(fda_handle *h, const double *dirs_dev, int nrhs, c64d *b_sorted);
+void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
+void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
+fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda_info *info);
+
+// scans and sorts (sort.cu)
+void fda_exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, int32_t *total_host);
+void fda_exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s, int64_t *total_host);
+void fda_radix_sort_u64(uint64_t *keys, int32_t *vals, int64_t n, int key_bits, cudaStream_t s);
+
+// kernel launch helper
+inline unsigned fda_blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }

@@ -1,0 +1,63 @@
+"""Thin object wrapper over the C ABI: holds a handle and marshals torch
+CUDA tensors (complex128) to device pointers.  No arithmetic here."""
+from __future__ import annotations
+
+from . import _lib
+
+
+class FDAProblem:
+    def __init__(self, verts, tris, k, stream=None, **cfg):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("FDAProblem needs a CUDA device; there is no CPU path")
+        c = _lib.fda_default_config(**cfg)
+        if stream is not None:
+            c.cuda_stream = stream.cuda_stream
+        self.h = _lib.fda_create(c)
+        self.k = float(k)
+        self.n = int(len(tris))
+        _lib.fda_build_tree(self.h, verts, tris, k)
+        _lib.fda_precompute_translations(self.h)
+
+    def _c(self, t):
+        import torch
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("expected a contiguous complex128 CUDA tensor")
+        return t.data_ptr()
+
+    def apply(self, x, y=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        _lib.fda_apply(self.h, self._c(x), self._c(y), nrhs, self.n)
+        return y
+
+    def rhs_plane_wave(self, dirs):
+        import numpy as np
+        import torch
+        d = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        b = torch.empty((d.shape[0], self.n), dtype=torch.complex128, device="cuda")
+        _lib.fda_rhs_plane_wave(self.h, d, self._c(b))
+        return b[0] if np.ndim(dirs) == 1 else b
+
+    def solve(self, b, tol, x0=None, raise_on_not_converged=True):
+        import torch
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        info, st = _lib.fda_solve(self.h, self._c(b), self._c(x), nrhs, tol, raise_on_not_converged)
+        return x, info
+
+    def stats(self):
+        return _lib.fda_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            _lib.fda_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

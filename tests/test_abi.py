@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/fda_bem.h declares; argument validation that needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fda_bem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fda_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1403_4747_gb300 import build
+    build.build()
+    from paper_1403_4747_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_four_calls():
+    names = _declared()
+    for n in ("fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_solve"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_config(lib):
+    from paper_1403_4747_gb300 import fda_default_config
+    c = fda_default_config()
+    assert c.eps == 1e-4 and c.leaf_max == 64 and c.p_lf == 8 and c.restart == 100
+    assert c.precision == 0 and c.mode == 0
+
+
+@pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", 0.5), ("leaf_max", 0), ("leaf_max", 65),
+                                         ("p_lf", 2), ("precision", 3), ("mode", 7), ("restart", 0),
+                                         ("rho_min", 1.0)])
+def test_invalid_config_rejected_without_gpu(lib, field, value):
+    from paper_1403_4747_gb300 import fda_default_config, fda_create, FDAError, FDA_ERR_ARG
+    c = fda_default_config(**{field: value})
+    with pytest.raises(FDAError) as e:
+        fda_create(c)
+    assert e.value.status == FDA_ERR_ARG
+
+
+def test_null_handle_calls(lib):
+    assert lib.fda_apply(None, None, None, 1, 1) == 1
+    assert lib.fda_last_error(None) == b"null handle"
+    lib.fda_destroy(None)

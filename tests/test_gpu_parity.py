@@ -1,0 +1,152 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the dense mode evaluates exactly the oracle's operator in FP64
+(only the summation order differs): relative L2 error <= 1e-12.  The FDA
+matvec approximates it; the bar is a relative L2 error <= 1e-4 (plain FP64
+and chosen FP32 forms alike).  Solutions: GMRES to tol against dense LU.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from inputs import icosphere, ellipsoid_from_icosphere, complex_normal, fibonacci_directions
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_4747_gb300 import build
+    build.build()
+
+
+def _problem(v, f, k, **cfg):
+    from paper_1403_4747_gb300 import FDAProblem
+    return FDAProblem(v, f, k, **cfg)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def test_rhs_matches_oracle():
+    v, f = icosphere(3)
+    P = _problem(v, f, 5.0, mode=1)
+    d = fibonacci_directions(3)
+    b = P.rhs_plane_wave(d).cpu().numpy()
+    ref = oracle.rhs_plane_wave(v, f, 5.0, d)
+    assert _rel(b, ref) < 1e-13
+
+
+@pytest.mark.parametrize("level,k", [(2, 3.0), (3, 5.0), (3, 40.0)])
+def test_dense_mode_matches_oracle(level, k):
+    v, f = icosphere(level)
+    x = complex_normal(len(f), seed=11)
+    P = _problem(v, f, k, mode=1)
+    y = P.apply(_dev(x)).cpu().numpy()
+    ref = oracle.matvec(v, f, k, x)
+    assert _rel(y, ref) < 1e-12
+
+
+@pytest.mark.parametrize("level,k,precision", [(4, 5.0, 0), (4, 20.0, 0), (4, 20.0, 1), (4, 5.0, 1)])
+def test_fda_matvec_parity(level, k, precision):
+    v, f = icosphere(level)
+    x = complex_normal(len(f), seed=3)
+    P = _problem(v, f, k, precision=precision)
+    st = P.stats()
+    assert st.n_m2l > 0  # the far field is exercised
+    y = P.apply(_dev(x)).cpu().numpy()
+    ref = oracle.matvec(v, f, k, x)
+    assert _rel(y, ref) < 1e-4
+
+
+def test_fda_high_frequency_levels_present():
+    v, f = icosphere(4)
+    P = _problem(v, f, 20.0)
+    st = P.stats()
+    regimes = [st.level_regime[l] for l in range(st.n_levels)]
+    assert 1 in regimes and 0 in regimes
+
+
+def test_fda_ellipsoid_ragged_leaves():
+    v, f = ellipsoid_from_icosphere(4)
+    x = complex_normal(len(f), seed=5)
+    P = _problem(v, f, 15.0)
+    y = P.apply(_dev(x)).cpu().numpy()
+    ref = oracle.matvec(v, f, 15.0, x)
+    assert _rel(y, ref) < 1e-4
+
+
+def test_fda_sampled_rows_larger_mesh():
+    v, f = icosphere(6)
+    k = 25.0
+    x = complex_normal(len(f), seed=9)
+    P = _problem(v, f, k)
+    y = P.apply(_dev(x)).cpu().numpy()
+    rows = np.random.default_rng(7).choice(len(f), 192, replace=False)
+    ref = oracle.matvec(v, f, k, x, rows=rows)
+    assert _rel(y[rows], ref) < 1e-4
+
+
+def test_multi_rhs_columns():
+    v, f = icosphere(3)
+    x = complex_normal(len(f), seed=1, nrhs=2)
+    P = _problem(v, f, 8.0)
+    y2 = P.apply(_dev(x)).cpu().numpy()
+    y0 = P.apply(_dev(x[0])).cpu().numpy()
+    y1 = P.apply(_dev(x[1])).cpu().numpy()
+    assert np.array_equal(y2[0], y0) and np.array_equal(y2[1], y1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_dense_lu(precision):
+    v, f = icosphere(3)
+    k = 5.0
+    P = _problem(v, f, k, precision=precision)
+    b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+    x, info = P.solve(b, 1e-8)
+    a = oracle.assemble(v, f, k)
+    u = oracle.lu_solve(a, oracle.rhs_plane_wave(v, f, k, [[0, 0, 1.0]])[0])
+    assert info.rel_resid_fp64 <= 1e-8
+    # FDA operator differs from the dense one by <= ~1e-4 relative
+    assert _rel(x.cpu().numpy(), u) < 1e-3
+
+
+def test_tiny_mesh_and_small_k():
+    v, f = icosphere(0)  # 20 triangles: a single leaf, near field only
+    x = complex_normal(len(f), seed=2)
+    for k in (0.05, 3.0):
+        P = _problem(v, f, k)
+        y = P.apply(_dev(x)).cpu().numpy()
+        assert _rel(y, oracle.matvec(v, f, k, x)) < 1e-12
+
+
+def test_errors_are_reported():
+    from paper_1403_4747_gb300 import (fda_create, fda_default_config, fda_build_tree, fda_apply,
+                                       fda_precompute_translations, FDAError, FDA_ERR_ARG, FDA_ERR_STATE,
+                                       fda_destroy)
+    v, f = icosphere(1)
+    h = fda_create(fda_default_config())
+    with pytest.raises(FDAError) as e:
+        fda_precompute_translations(h)
+    assert e.value.status == FDA_ERR_STATE
+    with pytest.raises(FDAError) as e:
+        fda_build_tree(h, v, f, -1.0)
+    assert e.value.status == FDA_ERR_ARG
+    bad = f.copy(); bad[0, 0] = len(v) + 5
+    with pytest.raises(FDAError) as e:
+        fda_build_tree(h, v, bad, 1.0)
+    assert e.value.status == FDA_ERR_ARG
+    deg = f.copy(); deg[0, 1] = deg[0, 0]
+    with pytest.raises(FDAError) as e:
+        fda_build_tree(h, v, deg, 1.0)
+    assert e.value.status == FDA_ERR_ARG
+    fda_destroy(h)
