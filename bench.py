@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the fast directional Burton-Miller BEM on GB300.
+
+Workload: rigid unit sphere, icosphere level 7 (327,680 flat triangles,
+collocation at centroids), k = 50 (kD = 100), plane wave along +z, octree
+leaves <= 64 elements, SVD threshold eps = 1e-4, GMRES tolerance 1e-4.
+Synthetic input: the icosphere stands in for the paper's sphere meshes.
+
+A timed step is one FDA matrix-vector product (Steps 2-4 of the paper's
+algorithm: near field, S2M, M2M, M2L, L2L, L2T) through the C ABI on inputs
+resident in HBM.  `value` is FDA matvec/s of the chosen form (FP32 far field
+and FP32 near-field storage); the JSON line also carries the plain FP64
+matvec rate, the setup time (tree, lists, quadrature, SVD precompute) and
+GMRES solve seconds of both forms at 1e-4, with the FP64 residual.
+
+`--impl reference` times the FP64 CPU oracle (dense on-the-fly matvec) on a
+bounded sample of rows of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FDA matvec/s & GMRES solve s, kD=100 N=327,680, plain vs chosen form @1e-4"
+WORKLOAD = "rigid unit sphere, icosphere level 7 (327,680 triangles), k=50 (kD=100), plane wave +z, eps=1e-4"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        self.path = os.path.join("/tmp", "fda_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _cpu_oracle_rate(v, f, k, x, rows_n, seed=7):
+    import numpy as np
+    import oracle
+    rows = np.random.default_rng(seed).choice(len(f), rows_n, replace=False)
+    t0 = time.perf_counter()
+    oracle.matvec(v, f, k, x, rows=rows)
+    dt = time.perf_counter() - t0
+    return (rows_n / len(f)) / dt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from inputs import icosphere, complex_normal
+    v, f = icosphere(args.level)
+    n = len(f)
+    x = complex_normal(n, seed=1234)
+    rows_n = args.ref_rows
+    rows = np.random.default_rng(7).choice(n, rows_n, replace=False)
+    oracle.load()
+    for _ in range(args.warmup):
+        oracle.matvec(v, f, args.k, x, rows=rows[:max(1, rows_n // 8)])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r = np.random.default_rng(100 + s).choice(n, rows_n, replace=False)
+        oracle.matvec(v, f, args.k, x, rows=r)
+    dt = time.perf_counter() - t0
+    value = args.steps * (rows_n / n) / dt
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": n, "k": args.k},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "matvec/s", "cores": cores,
+                             "sample": "%d sampled rows of the dense FP64 oracle matvec per step (of %d)" % (rows_n, n)},
+            "e2e": {"value": value, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import icosphere, complex_normal
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def reduce_max(v):
+        if ws == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    v, f = icosphere(args.level)
+    n = len(f)
+    k = args.k
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    P = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    st = P.stats()
+    nlev = st.n_levels
+    active = [l for l in range(nlev) if st.level_rank[l] > 0]
+    lev_lo = min(active) if active else nlev
+    launches_per_apply = 2 + 1 + 1 + 1 + 1 + (nlev - lev_lo) + 2 * max(0, nlev - 1 - lev_lo)
+
+    x = torch.from_numpy(complex_normal(n, seed=1234)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        P.apply(x, y)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        P.apply(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = reduce_max(ms)
+    value = ws * 1e3 / ms
+
+    # per-pass device times (CUDA events recorded by the library on its stream)
+    def pass_times(reps):
+        F.fda_set_timing(P.h, True)
+        acc = np.zeros(6)
+        for _ in range(reps):
+            P.apply(x, y)
+            acc += np.array(F.fda_get_pass_times(P.h))
+        F.fda_set_timing(P.h, False)
+        return acc / reps
+
+    pt32 = pass_times(5)
+    F.fda_set_precision(P.h, F.FDA_PLAIN_FP64)
+    P.apply(x, y)
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    nplain = max(1, args.plain_steps)
+    for _ in range(nplain):
+        P.apply(x, y)
+    torch.cuda.synchronize()
+    plain_ms = (time.perf_counter() - tp) / nplain * 1e3
+    pt64 = pass_times(1)
+    F.fda_set_precision(P.h, F.FDA_CHOSEN_FP32)
+
+    # end to end through the C ABI with host buffers (pinned)
+    xh = torch.from_numpy(complex_normal(n, seed=99)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    F.fda_apply_host(P.h, xh.data_ptr(), yh.data_ptr(), 1, n)
+    te = time.perf_counter()
+    ne = max(3, args.steps // 2)
+    for _ in range(ne):
+        F.fda_apply_host(P.h, xh.data_ptr(), yh.data_ptr(), 1, n)
+    e2e_ms = reduce_max((time.perf_counter() - te) / ne * 1e3)
+
+    # roofline of the dominant pass (M2L in the chosen form: FP32 ALU bound)
+    peaks, src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak_tflops = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    m2l_flops = _m2l_flops(P)
+    m2l_ms = pt32[2]
+    achieved = m2l_flops / (m2l_ms * 1e-3) / 1e12
+    near_gbs = st.bytes_near / 2 / (pt32[5] * 1e-3) / 1e9  # FP32 storage: 8 bytes per entry
+    roofline = {"kernel": "k_m2l<float> (M2L pass, all levels)", "bound": "alu", "achieved": achieved,
+                "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": None,
+                "peak_source": "FP32 FMA rate: %d SMs x 128 lanes x 2 flops x %.0f MHz (%s clocks)" % (nsm, sm_mhz, src),
+                "algorithmic_flops_per_apply": m2l_flops}
+
+    solve = {}
+    if not args.no_solve:
+        b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+        for name, prec in (("chosen", F.FDA_CHOSEN_FP32), ("plain", F.FDA_PLAIN_FP64)):
+            F.fda_set_precision(P.h, prec)
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            xs, info = P.solve(b, args.tol, raise_on_not_converged=False)
+            torch.cuda.synchronize()
+            solve[name] = {"solve_s": time.perf_counter() - ts, "iters": info.iters,
+                           "refinements": info.refinements, "rel_resid_fp64": info.rel_resid_fp64,
+                           "matvec_s": info.matvec_s}
+        F.fda_set_precision(P.h, F.FDA_CHOSEN_FP32)
+        if solve["chosen"]["solve_s"] > 0:
+            solve["speedup_chosen_over_plain"] = solve["plain"]["solve_s"] / solve["chosen"]["solve_s"]
+        solve["setup_s"] = setup_s
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        xc = complex_normal(n, seed=1234)
+        rate, dt, cores = _cpu_oracle_rate(v, f, k, xc, args.cpu_rows)
+        cpu = {"value": rate, "unit": "matvec/s", "cores": cores, "kind": "oracle",
+               "sample": "%d random rows of the dense FP64 oracle matvec (of %d), %.1f s" % (args.cpu_rows, n, dt)}
+
+    line = {"metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": n, "k": k, "eps": args.eps, "leaf_max": 64,
+                       "form": "chosen (FP32 far field and near storage, FP64 setup)",
+                       "l2": "inputs larger than L2 (near-field matrix %.2f GB FP32)" % (st.bytes_near / 2 / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "e2e": {"value": ws * 1e3 / e2e_ms, "unit": "matvec/s", "h2d_bytes_per_step": 16 * n,
+                    "d2h_bytes_per_step": 16 * n},
+            "gpu_launches": launches_per_apply * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "plain_fp64": {"matvec_per_s": 1e3 / plain_ms, "ms_per_matvec": plain_ms,
+                           "pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt64.tolist()))},
+            "chosen_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32.tolist())),
+            "near_field_gbs": near_gbs,
+            "solve": solve,
+            "tree": {"levels": nlev, "boxes": st.n_boxes, "leaves": st.n_leaves, "nnz_near": st.nnz_near,
+                     "m2l_pairs": st.n_m2l, "m2l_ops": st.n_m2l_ops,
+                     "rank_per_level": [st.level_rank[l] for l in range(nlev)],
+                     "regime_per_level": [st.level_regime[l] for l in range(nlev)],
+                     "cones_per_level": [st.level_cones[l] for l in range(nlev)],
+                     "device_gb": st.device_bytes / 1e9}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    P.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _m2l_flops(P):
+    """Real flops of the M2L pass per apply: 8 T_l^2 per interaction pair
+    (one complex multiply-add is 8 real flops)."""
+    st = P.stats()
+    return int(sum(8.0 * st.level_rank[l] ** 2 * st.level_m2l_pairs[l] for l in range(st.n_levels)))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--level", type=int, default=7)
+    ap.add_argument("--k", type=float, default=50.0)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--cpu-rows", type=int, default=1024)
+    ap.add_argument("--ref-rows", type=int, default=384)
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

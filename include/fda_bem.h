@@ -95,6 +95,7 @@ typedef struct {
     int32_t level_boxes[32];
     int32_t level_cones[32];
     double precompute_s, tree_s, near_s;
+    int64_t level_m2l_pairs[32];  /* per level: M2L (target, source) pairs */
 } fda_stats;
 
 typedef struct fda_handle fda_handle;
@@ -145,6 +146,11 @@ fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c
  * be NULL) receives the last column's figures.  Returns
  * FDA_ERR_NOT_CONVERGED when maxit is reached above tol. */
 fda_status fda_solve(fda_handle *h, const fda_c128 *b, fda_c128 *x, int nrhs, double tol, fda_info *info);
+
+/* Select the operator precision used by later fda_apply / fda_solve calls.
+ * FDA_CHOSEN_FP32 needs a handle created with precision = FDA_CHOSEN_FP32
+ * (which also keeps the FP64 operators); otherwise FDA_ERR_STATE. */
+fda_status fda_set_precision(fda_handle *h, int precision);
 
 /* Tree, list and operator statistics (host struct). */
 fda_status fda_get_stats(fda_handle *h, fda_stats *out);

@@ -39,7 +39,8 @@ class fda_stats(ctypes.Structure):
                 ("flops_far", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("level_regime", ctypes.c_int32 * 32), ("level_rank", ctypes.c_int32 * 32),
                 ("level_boxes", ctypes.c_int32 * 32), ("level_cones", ctypes.c_int32 * 32),
-                ("precompute_s", ctypes.c_double), ("tree_s", ctypes.c_double), ("near_s", ctypes.c_double)]
+                ("precompute_s", ctypes.c_double), ("tree_s", ctypes.c_double), ("near_s", ctypes.c_double),
+                ("level_m2l_pairs", ctypes.c_int64 * 32)]
 
 
 _lib = None
@@ -67,13 +68,15 @@ def load(path: str = LIB_PATH):
     lib.fda_solve.argtypes = [H, vp, vp, cint, dbl, ctypes.POINTER(fda_info)]
     lib.fda_get_stats.argtypes = [H, ctypes.POINTER(fda_stats)]
     lib.fda_set_timing.argtypes = [H, cint]
+    lib.fda_set_precision.argtypes = [H, cint]
     lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
     lib.fda_last_error.argtypes = [H]
     lib.fda_last_error.restype = ctypes.c_char_p
     lib.fda_destroy.argtypes = [H]
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
-                 "fda_rhs_plane_wave", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times"):
+                 "fda_rhs_plane_wave", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
+                 "fda_set_precision"):
         getattr(lib, name).restype = cint
     _lib = lib
     return lib
@@ -145,6 +148,10 @@ def fda_get_stats(h) -> fda_stats:
     s = fda_stats()
     _check(h, load().fda_get_stats(h, ctypes.byref(s)))
     return s
+
+
+def fda_set_precision(h, precision):
+    _check(h, load().fda_set_precision(h, int(precision)))
 
 
 def fda_set_timing(h, enable=True):

@@ -292,6 +292,7 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
             out->level_rank[l] = l < h->nlev ? h->lev[l].T : 0;
             out->level_boxes[l] = l < h->nlev ? h->lev[l].nbox : 0;
             out->level_cones[l] = l < h->nlev ? h->lev[l].ncones : 0;
+            out->level_m2l_pairs[l] = l < h->nlev ? h->lev[l].n_il : 0;
             if (l < h->nlev) ops += h->lev[l].n_ops;
         }
         out->n_m2l_ops = ops;
@@ -335,6 +336,21 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
         out->near_s = h->near_s;
         out->precompute_s = h->precompute_s;
     });
+}
+
+fda_status fda_set_precision(fda_handle *h, int precision)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (precision != FDA_PLAIN_FP64 && precision != FDA_CHOSEN_FP32) {
+        h->err = "unknown precision";
+        return FDA_ERR_ARG;
+    }
+    if (precision == FDA_CHOSEN_FP32 && !h->have32) {
+        h->err = "FP32 operators were not built (create the handle with precision = FDA_CHOSEN_FP32)";
+        return FDA_ERR_STATE;
+    }
+    h->cfg.precision = precision;
+    return FDA_OK;
 }
 
 fda_status fda_set_timing(fda_handle *h, int enable)
