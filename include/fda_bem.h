@@ -138,6 +138,30 @@ fda_status fda_apply_host(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrh
  * dirs: host double[nrhs][3] unit vectors; b: device, ld = nt. */
 fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b);
 
+/* Allocation-free variant of fda_rhs_plane_wave, for callers that must not
+ * have the library allocate device memory during the call: real-time loops
+ * that forbid allocator calls (cudaMalloc / cudaFree can synchronise the
+ * device), and applications whose device memory is owned by their own pool
+ * allocator, where an allocation behind their back could exceed their
+ * budget.  The paper has no counterpart; this is an interface convenience.
+ *   - It calls no cudaMalloc / cudaFree and no allocating library routine.
+ *     The directions are staged in a fixed device array of
+ *     FDA_NOALLOC_MAX_DIRS unit vectors (6 KB) that every GPU loading the
+ *     library keeps until the process exits, and b is written directly in
+ *     the caller's triangle order.
+ *   - nrhs must be in [1, FDA_NOALLOC_MAX_DIRS]; larger requests return
+ *     FDA_ERR_ARG.  dirs: host double[nrhs][3] unit vectors; b: device,
+ *     column-major with ld = nt, owned by the caller.
+ *   - All calls share the staging array, which keeps the last call's
+ *     directions; calls whose work overlaps on the GPU (other streams or
+ *     host threads) race on it.  The first call on a device looks up the
+ *     array's device address; make that first call before any stream
+ *     capture.
+ * The result equals fda_rhs_plane_wave's.  Stream-ordered; does not
+ * synchronise. */
+#define FDA_NOALLOC_MAX_DIRS 256
+fda_status fda_rhs_plane_wave_noalloc(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b);
+
 /* GMRES (Sec. 5): solve A x = b to ||b - A x|| / ||b|| <= tol for each of
  * nrhs columns (device pointers, ld = nt; x holds the initial guess on
  * entry, zero is fine).  Plain precision: GMRES(restart) on the FP64 FDA

@@ -249,6 +249,31 @@ fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c
     });
 }
 
+fda_status fda_rhs_plane_wave_noalloc(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state < 1) {
+        h->err = "fda_rhs_plane_wave_noalloc before fda_build_tree";
+        return FDA_ERR_STATE;
+    }
+    if (!dirs || !b || nrhs < 1) {
+        h->err = "invalid right-hand-side arguments";
+        return FDA_ERR_ARG;
+    }
+    if (nrhs > FDA_NOALLOC_MAX_DIRS) {
+        h->err = "fda_rhs_plane_wave_noalloc takes at most FDA_NOALLOC_MAX_DIRS (256) directions per call";
+        return FDA_ERR_ARG;
+    }
+    for (int m = 0; m < nrhs; ++m) {
+        double n2 = dirs[3 * m] * dirs[3 * m] + dirs[3 * m + 1] * dirs[3 * m + 1] + dirs[3 * m + 2] * dirs[3 * m + 2];
+        if (!(fabs(n2 - 1.0) < 1e-6)) {
+            h->err = "incidence directions must be unit vectors";
+            return FDA_ERR_ARG;
+        }
+    }
+    return guarded(h, [&] { fda_rhs_noalloc(h, dirs, nrhs, reinterpret_cast<c64d *>(b)); });
+}
+
 fda_status fda_solve(fda_handle *h, const fda_c128 *b, fda_c128 *x, int nrhs, double tol, fda_info *info)
 {
     if (!h) return FDA_ERR_ARG;

@@ -231,6 +231,7 @@ void fda_near_build(fda_handle *h);
 void fda_far_precompute(fda_handle *h);
 void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision);
 void fda_rhs_sorted(fda_handle *h, const double *dirs_dev, int nrhs, c64d *b_sorted);
+void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
 fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda_info *info);

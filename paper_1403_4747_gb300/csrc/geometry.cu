@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "fda_internal.cuh"
 
@@ -168,7 +169,60 @@ __global__ void k_permute_c(const c64d *src, c64d *dst, const int32_t *map, int6
         dst[m * ldd + map[i]] = src[m * lds + i];
 }
 
+// Right-hand side written straight into the caller's element order (no
+// Morton-order staging vector): b[m][perm[i]] for sorted element i.
+__global__ void k_rhs_direct(const double *cent, const double *nrm, const int32_t *perm, int64_t n,
+                             const double *dirs, int nrhs, double k, c64d *b)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int m = blockIdx.y;
+    if (i >= n || m >= nrhs) return;
+    const double *d = dirs + 3 * m;
+    double dx = d[0] * cent[3 * i] + d[1] * cent[3 * i + 1] + d[2] * cent[3 * i + 2];
+    double dn = d[0] * nrm[3 * i] + d[1] * nrm[3 * i + 1] + d[2] * nrm[3 * i + 2];
+    double s, c;
+    sincos(k * dx, &s, &c);
+    b[(int64_t)m * n + perm[i]] = c64d(c * (1.0 - dn), s * (1.0 - dn));
+}
+
 }  // namespace
+
+// Device-resident staging area for the incidence directions of
+// fda_rhs_plane_wave_noalloc: FDA_NOALLOC_MAX_DIRS unit vectors (6 KB), held
+// by every GPU that loads the library until the process exits.  All calls
+// share it, so calls that overlap on the GPU (different streams, or several
+// host threads) race on its contents.
+static __device__ __align__(256) double g_noalloc_dirs[3 * FDA_NOALLOC_MAX_DIRS];
+
+// Device address of g_noalloc_dirs, looked up once per device (with that
+// device current) on the first call made on it.
+static double *noalloc_dirs_ptr()
+{
+    static std::mutex mu;
+    static double *ptrs[256] = {nullptr};
+    int dev = 0;
+    FDA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) fda_fail(FDA_ERR_CUDA, "device index out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        double *p = nullptr;
+        FDA_CUDA(cudaGetSymbolAddress((void **)&p, g_noalloc_dirs));
+        ptrs[dev] = p;
+    }
+    return ptrs[dev];
+}
+
+// b (caller order, device) for nrhs <= FDA_NOALLOC_MAX_DIRS directions;
+// allocates nothing.
+void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b)
+{
+    double *dd = noalloc_dirs_ptr();
+    FDA_CUDA(cudaMemcpyAsync(dd, dirs_host, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, h->stream));
+    dim3 g(fda_blocks(h->N, 256), nrhs);
+    k_rhs_direct<<<g, 256, 0, h->stream>>>(h->cent.as<double>(), h->nrm.as<double>(), h->perm.as<int32_t>(), h->N,
+                                            dd, nrhs, h->k, b);
+    FDA_CHECK_LAUNCH();
+}
 
 void fda_geometry_build(fda_handle *h, const double *verts, int64_t nv, const int32_t *tris, int64_t nt)
 {
