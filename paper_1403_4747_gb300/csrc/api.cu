@@ -161,6 +161,7 @@ fda_status fda_precompute_translations(fda_handle *h)
             h->have32 = 1;
         }
         fda_alloc_densities(h, want32);
+        if (h->lev_lo >= 0) fda_build_batches(h);
         h->xs.alloc(sizeof(c64d) * h->N);
         h->ys.alloc(sizeof(c64d) * h->N);
         FDA_CUDA(cudaStreamSynchronize(h->stream));

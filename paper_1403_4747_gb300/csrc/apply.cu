@@ -31,21 +31,6 @@ struct lvl_ptrs {
 };
 
 template <typename R>
-__device__ inline int child_cone_dev(const lvl_ptrs<R> &P, int l, int u)
-{
-    int ncp = P.nc[l], ncc = P.nc[l + 1];
-    int face = u / (ncp * ncp), rem = u % (ncp * ncp);
-    int a = rem / ncp, b = rem % ncp;
-    int f = ncp / ncc;
-    return face * ncc * ncc + (a / f) * ncc + (b / f);
-}
-
-__device__ inline int octant_of(const int32_t *coord, int b)
-{
-    return ((coord[3 * b] & 1) << 2) | ((coord[3 * b + 1] & 1) << 1) | (coord[3 * b + 2] & 1);
-}
-
-template <typename R>
 __device__ inline cx<R> ldx(const void *x, int64_t i, int x64)
 {
     if (x64) {
@@ -104,107 +89,6 @@ __global__ void k_s2m(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
         cx<R> acc;
         for (int j = 0; j < nB; ++j) cfma(acc, S[(int64_t)j * T + t], xs[j]);
         q[t] = acc;
-    }
-}
-
-// ---- Step 2: M2M into parent level l
-template <typename R>
-__global__ void k_m2m(lvl_ptrs<R> P, int l, const int32_t *bleaf, const int32_t *c0, const int32_t *c1,
-                      const int32_t *coord)
-{
-    __shared__ cx<R> qc[MAXT];
-    int b = P.box0[l] + blockIdx.x;
-    int u = blockIdx.y;
-    if (bleaf[b]) return;
-    const int Tp = P.T[l], Tc = P.T[l + 1], ncp = P.ncones[l], ncc = P.ncones[l + 1];
-    cx<R> acc[MAXR];
-    for (int c = c0[b]; c < c1[b]; ++c) {
-        int o = octant_of(coord, c);
-        int uc = P.hf[l + 1] ? child_cone_dev(P, l, u) : 0;
-        const cx<R> *src = P.q[l + 1] + ((int64_t)(c - P.box0[l + 1]) * ncc + uc) * Tc;
-        __syncthreads();
-        for (int j = threadIdx.x; j < Tc; j += blockDim.x) qc[j] = src[j];
-        __syncthreads();
-        const cx<R> *M = P.Mt[l] + (int64_t)(o * ncp + u) * Tp * Tc;
-        for (int r = 0; r < MAXR; ++r) {
-            int t = threadIdx.x + r * blockDim.x;
-            if (t >= Tp) break;
-            cx<R> a = acc[r];
-            for (int j = 0; j < Tc; ++j) cfma(a, M[(int64_t)j * Tp + t], qc[j]);
-            acc[r] = a;
-        }
-    }
-    cx<R> *dst = P.q[l] + ((int64_t)(b - P.box0[l]) * ncp + u) * Tp;
-    for (int r = 0; r < MAXR; ++r) {
-        int t = threadIdx.x + r * blockDim.x;
-        if (t < Tp) dst[t] = acc[r];
-    }
-}
-
-// ---- Step 3: M2L at level l (writes p~)
-template <typename R>
-__global__ void k_m2l(lvl_ptrs<R> P, int l, const int64_t *ilp, const int32_t *ils, const int32_t *ilo,
-                      const int32_t *ilc)
-{
-    __shared__ cx<R> qs[MAXT];
-    int b = P.box0[l] + blockIdx.x;
-    int u = blockIdx.y;
-    const int T = P.T[l], nc = P.ncones[l];
-    cx<R> acc[MAXR];
-    for (int64_t e = ilp[b]; e < ilp[b + 1]; ++e) {
-        int cw = ilc[e];
-        if ((cw & 0xffff) != u) continue;
-        int su = cw >> 16;
-        const cx<R> *src = P.q[l] + ((int64_t)(ils[e] - P.box0[l]) * nc + su) * T;
-        __syncthreads();
-        for (int j = threadIdx.x; j < T; j += blockDim.x) qs[j] = src[j];
-        __syncthreads();
-        const cx<R> *K = P.Kt[l] + (int64_t)ilo[e] * T * T;
-        for (int r = 0; r < MAXR; ++r) {
-            int t = threadIdx.x + r * blockDim.x;
-            if (t >= T) break;
-            cx<R> a = acc[r];
-            for (int j = 0; j < T; ++j) cfma(a, K[(int64_t)j * T + t], qs[j]);
-            acc[r] = a;
-        }
-    }
-    cx<R> *dst = P.p[l] + ((int64_t)(b - P.box0[l]) * nc + u) * T;
-    for (int r = 0; r < MAXR; ++r) {
-        int t = threadIdx.x + r * blockDim.x;
-        if (t < T) dst[t] = acc[r];
-    }
-}
-
-// ---- Step 3: L2L from parent level l into child level l+1 (adds to p~)
-template <typename R>
-__global__ void k_l2l(lvl_ptrs<R> P, int l, const int32_t *bpar, const int32_t *coord)
-{
-    __shared__ cx<R> pp[MAXT];
-    int c = P.box0[l + 1] + blockIdx.x;
-    int uc = blockIdx.y;
-    int par = bpar[c];
-    int o = octant_of(coord, c);
-    const int Tp = P.T[l], Tc = P.T[l + 1], ncp = P.ncones[l], ncc = P.ncones[l + 1];
-    cx<R> acc[MAXR];
-    for (int u = 0; u < ncp; ++u) {
-        if (P.hf[l + 1] && child_cone_dev(P, l, u) != uc) continue;
-        const cx<R> *src = P.p[l] + ((int64_t)(par - P.box0[l]) * ncp + u) * Tp;
-        __syncthreads();
-        for (int j = threadIdx.x; j < Tp; j += blockDim.x) pp[j] = src[j];
-        __syncthreads();
-        const cx<R> *Lm = P.Lt[l] + (int64_t)(o * ncp + u) * Tc * Tp;
-        for (int r = 0; r < MAXR; ++r) {
-            int t = threadIdx.x + r * blockDim.x;
-            if (t >= Tc) break;
-            cx<R> a = acc[r];
-            for (int j = 0; j < Tp; ++j) cfma(a, Lm[(int64_t)j * Tc + t], pp[j]);
-            acc[r] = a;
-        }
-    }
-    cx<R> *dst = P.p[l + 1] + ((int64_t)(c - P.box0[l + 1]) * ncc + uc) * Tc;
-    for (int r = 0; r < MAXR; ++r) {
-        int t = threadIdx.x + r * blockDim.x;
-        if (t < Tc) dst[t] = dst[t] + acc[r];
     }
 }
 
@@ -280,30 +164,28 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         return;
     }
     lvl_ptrs<R> P = make_ptrs<R>(h, ops, q, p);
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        const level_info &L = h->lev[l];
+        size_t bytes = sizeof(cx<R>) * (size_t)L.nbox * L.ncones * L.T;
+        FDA_CUDA(cudaMemsetAsync(q[l].p, 0, bytes, s));
+        FDA_CUDA(cudaMemsetAsync(p[l].p, 0, bytes, s));
+    }
     k_s2m<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
                                h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(),
                                ops.St.template as<cx<R>>(), x, x64);
     FDA_CHECK_LAUNCH();
     mark(2);
-    for (int l = h->nlev - 2; l >= h->lev_lo; --l) {
-        dim3 g(h->lev[l].nbox, h->lev[l].ncones);
-        k_m2m<R><<<g, AT, 0, s>>>(P, l, h->box_leaf.as<int32_t>(), h->box_child0.as<int32_t>(),
-                                  h->box_child1.as<int32_t>(), h->box_coord.as<int32_t>());
-        FDA_CHECK_LAUNCH();
-    }
+    // M2M bottom-up: q~_parent += M~ q~_child
+    for (int l = h->nlev - 2; l >= h->lev_lo; --l)
+        fda_run_batch<R>(h->b_m2m[l], P.Mt[l], h->lev[l].T, h->lev[l + 1].T, P.q[l + 1], P.q[l], s);
     mark(3);
-    for (int l = h->lev_lo; l < h->nlev; ++l) {
-        dim3 g(h->lev[l].nbox, h->lev[l].ncones);
-        k_m2l<R><<<g, AT, 0, s>>>(P, l, h->il_ptr.as<int64_t>(), h->il_src.as<int32_t>(), h->il_op.as<int32_t>(),
-                                  h->il_cone.as<int32_t>());
-        FDA_CHECK_LAUNCH();
-    }
+    // M2L at every level: p~_target += K~ q~_source
+    for (int l = h->lev_lo; l < h->nlev; ++l)
+        fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], s);
     mark(4);
-    for (int l = h->lev_lo; l + 1 < h->nlev; ++l) {
-        dim3 g(h->lev[l + 1].nbox, h->lev[l + 1].ncones);
-        k_l2l<R><<<g, AT, 0, s>>>(P, l, h->box_parent.as<int32_t>(), h->box_coord.as<int32_t>());
-        FDA_CHECK_LAUNCH();
-    }
+    // L2L top-down: p~_child += L~ p~_parent
+    for (int l = h->lev_lo; l + 1 < h->nlev; ++l)
+        fda_run_batch<R>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], s);
     mark(5);
     k_l2t<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
                                h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(), ops.Tt.template as<cx<R>>(),

@@ -126,6 +126,15 @@ struct level_info {
     int R_off = 0;       // offsets of the dense offset table lie in [-R_off, R_off]^3
 };
 
+// one batched-translation launch: tiles of (operator, pair range, row block)
+// and (source offset, target offset) pairs, grouped by operator
+struct tr_batch {
+    dbuf tiles, pairs;
+    int ntiles = 0;
+    int np = 32;          // pairs per tile (32 or 64)
+    int64_t npairs = 0;
+};
+
 template <typename T>
 struct far_ops {
     // per level (index = level)
@@ -202,6 +211,9 @@ struct fda_handle {
     far_ops<float> op32;
     int have32 = 0;
 
+    // batched translations per level (M2L at l; M2M and L2L between l and l+1)
+    tr_batch b_m2l[FDA_MAX_LEVELS], b_m2m[FDA_MAX_LEVELS], b_l2l[FDA_MAX_LEVELS];
+
     // densities (per level, [nbox][ncones][T])
     dbuf q64[FDA_MAX_LEVELS], p64[FDA_MAX_LEVELS];
     dbuf q32[FDA_MAX_LEVELS], p32[FDA_MAX_LEVELS];
@@ -235,6 +247,11 @@ void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
 fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda_info *info);
+
+void fda_build_batches(fda_handle *h);
+template <typename R>
+void fda_run_batch(const tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst,
+                   cudaStream_t s);
 
 // scans and sorts (sort.cu)
 void fda_exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, int32_t *total_host);

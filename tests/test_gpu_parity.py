@@ -103,7 +103,9 @@ def test_multi_rhs_columns():
     y2 = P.apply(_dev(x)).cpu().numpy()
     y0 = P.apply(_dev(x[0])).cpu().numpy()
     y1 = P.apply(_dev(x[1])).cpu().numpy()
-    assert np.array_equal(y2[0], y0) and np.array_equal(y2[1], y1)
+    # translations accumulate with atomics, so the summation order (and the
+    # last bits) may differ between calls
+    assert _rel(y2[0], y0) < 1e-13 and _rel(y2[1], y1) < 1e-13
 
 
 @pytest.mark.parametrize("precision", [0, 1])
