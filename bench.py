@@ -173,7 +173,8 @@ def run_native(args):
     k = args.k
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    P = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps)
+    P = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps,
+                     precond=1 if args.blockdiag else 0, restart=args.restart)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     st = P.stats()
@@ -255,19 +256,51 @@ def run_native(args):
     solve = {}
     if not args.no_solve:
         b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
-        for name, prec in (("chosen", F.FDA_CHOSEN_FP32), ("plain", F.FDA_PLAIN_FP64)):
+        runs = [("chosen", F.FDA_CHOSEN_FP32, 0)]
+        if args.blockdiag:
+            runs.append(("chosen_blockdiag", F.FDA_CHOSEN_FP32, 1))
+        if not args.no_plain_unpreconditioned:
+            runs.append(("plain", F.FDA_PLAIN_FP64, 0))
+        for name, prec, pc in runs:
             F.fda_set_precision(P.h, prec)
+            F.fda_set_precond(P.h, pc)
             torch.cuda.synchronize()
             ts = time.perf_counter()
             xs, info = P.solve(b, args.tol, raise_on_not_converged=False)
             torch.cuda.synchronize()
             solve[name] = {"solve_s": time.perf_counter() - ts, "iters": info.iters,
                            "refinements": info.refinements, "rel_resid_fp64": info.rel_resid_fp64,
-                           "matvec_s": info.matvec_s}
+                           "matvec_s": info.matvec_s, "precond": ["none", "blockdiag"][pc]}
         F.fda_set_precision(P.h, F.FDA_CHOSEN_FP32)
-        if solve["chosen"]["solve_s"] > 0:
+        F.fda_set_precond(P.h, 0)
+        if "plain" in solve and solve["chosen"]["solve_s"] > 0:
             solve["speedup_chosen_over_plain"] = solve["plain"]["solve_s"] / solve["chosen"]["solve_s"]
         solve["setup_s"] = setup_s
+        solve["restart"] = args.restart
+        solve["coupling"] = "alpha = +i/k (normal into the body)"
+        if not args.no_alt_coupling:
+            # the conjugate coupling alpha = -i/k: same scattering problem, eigenvalues in the right half-plane
+            P.close()
+            t0 = time.perf_counter()
+            Q = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps, alpha_sign=-1.0,
+                             restart=args.restart)
+            torch.cuda.synchronize()
+            setup_q = time.perf_counter() - t0
+            bq = Q.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+            alt = {}
+            for name, prec in (("chosen", F.FDA_CHOSEN_FP32), ("plain", F.FDA_PLAIN_FP64)):
+                F.fda_set_precision(Q.h, prec)
+                torch.cuda.synchronize()
+                ts = time.perf_counter()
+                xq, info = Q.solve(bq, args.tol, raise_on_not_converged=False)
+                torch.cuda.synchronize()
+                alt[name] = {"solve_s": time.perf_counter() - ts, "iters": info.iters,
+                             "refinements": info.refinements, "rel_resid_fp64": info.rel_resid_fp64}
+            alt["setup_s"] = setup_q
+            alt["speedup_chosen_over_plain"] = alt["plain"]["solve_s"] / max(alt["chosen"]["solve_s"], 1e-9)
+            solve["conjugate_coupling"] = alt
+            Q.close()
+            P = None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -302,7 +335,8 @@ def run_native(args):
                      "device_gb": st.device_bytes / 1e9}}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    P.close()
+    if P is not None:
+        P.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -330,6 +364,10 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--ref-rows", type=int, default=384)
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-plain-unpreconditioned", action="store_true")
+    ap.add_argument("--no-alt-coupling", action="store_true")
+    ap.add_argument("--blockdiag", action="store_true", help="also solve with the block-diagonal preconditioner")
+    ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

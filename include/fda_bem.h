@@ -69,6 +69,9 @@ typedef struct {
     int mode;              /* fda_mode: FDA, or dense all-pairs direct sum (small meshes, testing) */
     int restart;           /* GMRES restart length (default 100) */
     int maxit;             /* GMRES iteration cap (default 1000) */
+    int precond;           /* 0 none (the paper's setting), 1 leaf block-diagonal (right preconditioner) */
+    double alpha_sign;     /* coupling alpha = alpha_sign * i/k: +1 (default) the paper's i/k as written with the
+                              normal into the body; -1 the conjugate coupling */
     void *cuda_stream;     /* cudaStream_t, or NULL */
 } fda_config;
 
@@ -175,6 +178,11 @@ fda_status fda_solve(fda_handle *h, const fda_c128 *b, fda_c128 *x, int nrhs, do
  * FDA_CHOSEN_FP32 needs a handle created with precision = FDA_CHOSEN_FP32
  * (which also keeps the FP64 operators); otherwise FDA_ERR_STATE. */
 fda_status fda_set_precision(fda_handle *h, int precision);
+
+/* Select the preconditioner used by later fda_solve calls: 0 none, 1 leaf
+ * block-diagonal (needs a handle created with precond = 1, which builds the
+ * block inverses during fda_precompute_translations; else FDA_ERR_STATE). */
+fda_status fda_set_precond(fda_handle *h, int precond);
 
 /* Tree, list and operator statistics (host struct). */
 fda_status fda_get_stats(fda_handle *h, fda_stats *out);

@@ -34,6 +34,7 @@ def load():
         lib.orc_gauss_legendre.argtypes = [cint, _dp, _dp]
         lib.orc_num_threads.restype = cint
         lib.orc_rule6.argtypes = [_dp, _dp]
+        lib.orc_set_alpha_sign.argtypes = [dbl]
         lib.orc_layer_rowsum.argtypes = [_dp, _ip, i64, dbl, cint, _dp, cint]
         _lib = lib
     return _lib
@@ -71,6 +72,7 @@ def kernels(x, nx, y, ny, k):
 
 
 def integrate_triangle(x, nx, tri_pts, ny, area, k, levels):
+    load().orc_set_alpha_sign(1.0)
     arrs = [np.ascontiguousarray(q, dtype=np.float64) for q in (x, nx, tri_pts, ny)]
     out = np.empty(2)
     load().orc_integrate_triangle(*[_d(q) for q in arrs], float(area), float(k), int(levels), _d(out))
@@ -90,8 +92,9 @@ def gauss_legendre(n):
     return xs, ws
 
 
-def entry(verts, tris, k, i, j):
+def entry(verts, tris, k, i, j, alpha_sign=1.0):
     v, t = _mesh(verts, tris)
+    load().orc_set_alpha_sign(float(alpha_sign))
     out = np.empty(2)
     load().orc_entry(_d(v), t.ctypes.data_as(_ip), t.shape[0], float(k), int(i), int(j), _d(out))
     return complex(out[0], out[1])
@@ -102,10 +105,11 @@ def is_near_pair(verts, tris, i, j) -> bool:
     return bool(load().orc_is_near_pair(_d(v), t.ctypes.data_as(_ip), int(i), int(j)))
 
 
-def matvec(verts, tris, k, x, rows=None, nthreads=0):
+def matvec(verts, tris, k, x, rows=None, nthreads=0, alpha_sign=1.0):
     """y = A x (all rows, or the listed rows).  x: complex [N] or [nrhs, N];
-    returns complex [len(rows)] or [nrhs, len(rows)]."""
+    returns complex [len(rows)] or [nrhs, len(rows)].  alpha = alpha_sign i/k."""
     v, t = _mesh(verts, tris)
+    load().orc_set_alpha_sign(float(alpha_sign))
     n = t.shape[0]
     x = np.asarray(x, dtype=np.complex128)
     squeeze = x.ndim == 1
@@ -122,17 +126,19 @@ def matvec(verts, tris, k, x, rows=None, nthreads=0):
     return y[0] if squeeze else y
 
 
-def assemble(verts, tris, k, nthreads=0):
+def assemble(verts, tris, k, nthreads=0, alpha_sign=1.0):
     v, t = _mesh(verts, tris)
+    load().orc_set_alpha_sign(float(alpha_sign))
     n = t.shape[0]
     a = np.empty((n, n), dtype=np.complex128)
     load().orc_assemble(_d(v), t.ctypes.data_as(_ip), n, float(k), a.ctypes.data_as(_dp), int(nthreads))
     return a
 
 
-def rhs_plane_wave(verts, tris, k, dirs):
+def rhs_plane_wave(verts, tris, k, dirs, alpha_sign=1.0):
     """b = u_inc + alpha du_inc/dn at centroids; dirs [nrhs, 3] -> [nrhs, N]"""
     v, t = _mesh(verts, tris)
+    load().orc_set_alpha_sign(float(alpha_sign))
     d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
     n = t.shape[0]
     b = np.empty((d.shape[0], n), dtype=np.complex128)
@@ -152,6 +158,7 @@ def layer_rowsum(verts, tris, k, part, nthreads=0):
     """part 1: 1/2 + sum_j D_ij (double layer); part 2: sum_j H_ij
     (hypersingular, no alpha).  Complex [N]."""
     v, t = _mesh(verts, tris)
+    load().orc_set_alpha_sign(1.0)
     n = t.shape[0]
     out = np.empty(2 * n)
     load().orc_layer_rowsum(_d(v), t.ctypes.data_as(_ip), n, float(k), int(part), _d(out), int(nthreads))

@@ -124,6 +124,12 @@ static void kernels_all(const double *x, const double *nx, const double *y, cons
              ((1.0 - I * k * R) * nxny + (k * k * R2 + 3.0 * I * k * R - 3.0) * rnx * rny / R2);
 }
 
+/* Sign s of the coupling alpha = s i/k (s = +1: the paper's alpha = i/k as
+ * written; s = -1: the conjugate coupling).  Set per exported call. */
+static double g_alpha_sign = 1.0;
+
+void orc_set_alpha_sign(double s) { g_alpha_sign = s; }
+
 /* Which layer an integral takes: the Burton-Miller combination of Eq.
  * eq_sum, or (for the pin tests) the double layer or hypersingular layer
  * alone.  Set once per exported call, before any parallel region. */
@@ -136,7 +142,7 @@ static cplx kernel_bm(const double *x, const double *nx, const double *y, const 
     kernels_all(x, nx, y, ny, k, o);
     if (g_part == 1) return o[1];
     if (g_part == 2) return o[3];
-    cplx alpha = I / k;
+    cplx alpha = g_alpha_sign * I / k;
     return o[1] + alpha * o[3];
 }
 
@@ -255,7 +261,7 @@ static cplx entry(const tri_t *Ti, const tri_t *Tj, int same, double k)
     if (same) {
         if (g_part == 1) return 0.5;
         if (g_part == 2) return self_hypersingular(Ti, k);
-        return 0.5 + (I / k) * self_hypersingular(Ti, k);
+        return 0.5 + (g_alpha_sign * I / k) * self_hypersingular(Ti, k);
     }
     double dv[3];
     sub3(Ti->c, Tj->c, dv);
@@ -459,7 +465,7 @@ void orc_rhs_plane_wave(const double *verts, const int32_t *tris, int64_t nt, do
                         int nrhs, double *b)
 {
     cplx *bc = (cplx *)b;
-    cplx alpha = I / k;
+    cplx alpha = g_alpha_sign * I / k;
     for (int m = 0; m < nrhs; ++m)
         for (int64_t t = 0; t < nt; ++t) {
             tri_t T;

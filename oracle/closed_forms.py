@@ -43,12 +43,15 @@ def mie_surface_field(k: float, cos_theta, nmax: int | None = None):
     return u
 
 
-def sphere_eigenvalue(n: int, k: float) -> complex:
+def sphere_eigenvalue(n: int, k: float, alpha_sign: float = 1.0) -> complex:
+    """lambda_n for alpha = alpha_sign i/k: 1/2 + D + alpha H with
+    D[Y_n] = -(i k^2/2)(j_n' h_n + j_n h_n') Y_n and H[Y_n] = i k^3 j_n' h_n' Y_n."""
     jn = special.spherical_jn(n, k)
     jd = special.spherical_jn(n, k, derivative=True)
     hn = _h1(n, k)
     hd = _h1(n, k, derivative=True)
-    return 0.5 - 0.5j * k * k * (jd * hn + jn * hd) - k * k * jd * hd
+    alpha = alpha_sign * 1j / k
+    return 0.5 - 0.5j * k * k * (jd * hn + jn * hd) + alpha * 1j * k ** 3 * jd * hd
 
 
 def legendre_on_mesh(centroids, n: int, axis=(0.0, 0.0, 1.0)):

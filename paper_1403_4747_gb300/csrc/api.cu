@@ -91,6 +91,8 @@ void fda_default_config(fda_config *c)
     c->mode = FDA_MODE_FDA;
     c->restart = 100;
     c->maxit = 1000;
+    c->precond = 0;
+    c->alpha_sign = 1.0;
     c->cuda_stream = nullptr;
 }
 
@@ -103,7 +105,8 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
     if (!(c.eps > 0 && c.eps <= 0.1) || c.leaf_max < 1 || c.leaf_max > 64 || c.p_lf < 3 || c.p_lf > 16 ||
         c.p_hf < 3 || c.p_hf > 16 || c.hf_nr < 1 || c.hf_na < 8 || !(c.hf_wavelengths > 0) || !(c.rho_min >= 2.0) ||
         (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
-        (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.maxit < 1)
+        (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.maxit < 1 || c.precond < 0 ||
+        c.precond > 1 || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0))
         return FDA_ERR_ARG;
     fda_handle *h = new (std::nothrow) fda_handle();
     if (!h) return FDA_ERR_OOM;
@@ -153,6 +156,7 @@ fda_status fda_precompute_translations(fda_handle *h)
         double t0 = now_s();
         fda_near_build(h);
         h->near_s = now_s() - t0;
+        fda_precond_build(h);
         fda_far_precompute(h);
         int want32 = h->cfg.precision == FDA_CHOSEN_FP32;
         if (want32) {
@@ -376,6 +380,21 @@ fda_status fda_set_precision(fda_handle *h, int precision)
         return FDA_ERR_STATE;
     }
     h->cfg.precision = precision;
+    return FDA_OK;
+}
+
+fda_status fda_set_precond(fda_handle *h, int precond)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (precond != 0 && precond != 1) {
+        h->err = "unknown preconditioner";
+        return FDA_ERR_ARG;
+    }
+    if (precond == 1 && !h->pc_M.p) {
+        h->err = "block-diagonal preconditioner was not built (create the handle with precond = 1)";
+        return FDA_ERR_STATE;
+    }
+    h->cfg.precond = precond;
     return FDA_OK;
 }
 

@@ -220,6 +220,9 @@ struct fda_handle {
     int lev_lo = -1;           // coarsest level with interaction-list entries
     std::vector<int3> h_ops[FDA_MAX_LEVELS];  // per level: offset of each distinct M2L operator
 
+    // leaf block-diagonal preconditioner (row-major n_B x n_B per leaf)
+    dbuf pc_M, pc_off;
+
     // timing
     int timing = 0;
     cudaEvent_t ev[8] = {};
@@ -247,6 +250,8 @@ void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
 fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda_info *info);
+void fda_precond_build(fda_handle *h);
+void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z);
 
 void fda_build_batches(fda_handle *h);
 template <typename R>

@@ -141,7 +141,7 @@ __global__ void k_quad_points(const double *v9, const double *area, int64_t n, d
 
 // b_i = e^{ik d.x_i} (1 + alpha ik d.n_i), alpha = i/k (Eq. eq_bm, sound-hard)
 __global__ void k_rhs(const double *cent, const double *nrm, int64_t n, const double *dirs, int nrhs, double k,
-                      c64d *b)
+                      double as, c64d *b)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int m = blockIdx.y;
@@ -152,8 +152,8 @@ __global__ void k_rhs(const double *cent, const double *nrm, int64_t n, const do
     double s, c;
     sincos(k * dx, &s, &c);
     c64d uinc(c, s);
-    // alpha * du_inc/dn = (i/k)(ik dn) u_inc = -dn u_inc
-    c64d f(1.0 - dn, 0.0);
+    // alpha * du_inc/dn = as (i/k)(ik dn) u_inc = -as dn u_inc
+    c64d f(1.0 - as * dn, 0.0);
     b[(int64_t)m * n + i] = uinc * f;
 }
 
@@ -172,7 +172,7 @@ __global__ void k_permute_c(const c64d *src, c64d *dst, const int32_t *map, int6
 // Right-hand side written straight into the caller's element order (no
 // Morton-order staging vector): b[m][perm[i]] for sorted element i.
 __global__ void k_rhs_direct(const double *cent, const double *nrm, const int32_t *perm, int64_t n,
-                             const double *dirs, int nrhs, double k, c64d *b)
+                             const double *dirs, int nrhs, double k, double as, c64d *b)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int m = blockIdx.y;
@@ -182,7 +182,7 @@ __global__ void k_rhs_direct(const double *cent, const double *nrm, const int32_
     double dn = d[0] * nrm[3 * i] + d[1] * nrm[3 * i + 1] + d[2] * nrm[3 * i + 2];
     double s, c;
     sincos(k * dx, &s, &c);
-    b[(int64_t)m * n + perm[i]] = c64d(c * (1.0 - dn), s * (1.0 - dn));
+    b[(int64_t)m * n + perm[i]] = c64d(c * (1.0 - as * dn), s * (1.0 - as * dn));
 }
 
 }  // namespace
@@ -220,7 +220,7 @@ void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b)
     FDA_CUDA(cudaMemcpyAsync(dd, dirs_host, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, h->stream));
     dim3 g(fda_blocks(h->N, 256), nrhs);
     k_rhs_direct<<<g, 256, 0, h->stream>>>(h->cent.as<double>(), h->nrm.as<double>(), h->perm.as<int32_t>(), h->N,
-                                            dd, nrhs, h->k, b);
+                                            dd, nrhs, h->k, h->cfg.alpha_sign, b);
     FDA_CHECK_LAUNCH();
 }
 
@@ -302,7 +302,7 @@ void fda_rhs_sorted(fda_handle *h, const double *dirs_dev, int nrhs, c64d *b_sor
 {
     dim3 g(fda_blocks(h->N, 256), nrhs);
     k_rhs<<<g, 256, 0, h->stream>>>(h->cent.as<double>(), h->nrm.as<double>(), h->N, dirs_dev, nrhs, h->k,
-                                     b_sorted);
+                                     h->cfg.alpha_sign, b_sorted);
     FDA_CHECK_LAUNCH();
 }
 

@@ -124,6 +124,18 @@ struct solver {
         k_combine<<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, n, (int)c.size(), hd.as<c64d>(), sign, w, n);
         FDA_CHECK_LAUNCH();
     }
+    dbuf ptmp;
+    // y = A M x when the preconditioner is on (right preconditioning), else A x
+    void apply_op(const c64d *x, c64d *y, int precision)
+    {
+        if (h->cfg.precond == 1) {
+            if (!ptmp.p) ptmp.alloc(sizeof(c64d) * n);
+            fda_precond_apply(h, x, ptmp.as<c64d>());
+            apply(ptmp.as<c64d>(), y, precision);
+        } else {
+            apply(x, y, precision);
+        }
+    }
     void apply(const c64d *x, c64d *y, int precision)
     {
         auto t0 = std::chrono::steady_clock::now();
@@ -166,7 +178,7 @@ struct solver {
             int j = 0;
             for (; j < m && it < maxit; ++j, ++it) {
                 c64d *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
-                apply(vj, vn, precision);
+                apply_op(vj, vn, precision);
                 std::vector<std::complex<double>> hcol(j + 2, 0.0), c;
                 for (int pass = 0; pass < 2; ++pass) {
                     dots(V, j + 1, vn, c);
@@ -215,7 +227,17 @@ struct solver {
                 for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
                 y[i] = s / H[(size_t)i * m + i];
             }
-            combine(V, y, 1.0, d);
+            if (h->cfg.precond == 1) {
+                // d += M (V y): form V y in w, then apply M into the basis slot V_m (free now)
+                FDA_CUDA(cudaMemsetAsync(w.p, 0, sizeof(c64d) * n, h->stream));
+                combine(V, y, 1.0, w.as<c64d>());
+                c64d *tmp = V + (int64_t)m * n;
+                fda_precond_apply(h, w.as<c64d>(), tmp);
+                std::vector<std::complex<double>> one(1, 1.0);
+                combine(tmp, one, 1.0, d);
+            } else {
+                combine(V, y, 1.0, d);
+            }
             if (it >= maxit && est > tol_rel) {
                 // one last true-residual check happens at the top of the loop
             }

@@ -209,7 +209,7 @@ __global__ void k_emat_s2m(const double *chk, int nchk, const double *centers, c
 // y_m = downward equivalent points of the leaf
 __global__ void k_emat_l2t(const double *eq, int neq, const double *centers, const int32_t *leaf_list,
                            const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend, const double *cent,
-                           const double *nrm, double k, c64d *out)
+                           const double *nrm, double k, double as, c64d *out)
 {
     int b = blockIdx.y;
     int li = leaf_list[b];
@@ -230,10 +230,10 @@ __global__ void k_emat_l2t(const double *eq, int neq, const double *centers, con
             sincos(k * R, &s, &cc);
             double g = 1.0 / (4.0 * FDA_PI * R);
             double rnx = r0 * nx[0] + r1 * nx[1] + r2 * nx[2];
-            // dG/dn_x = -e^{ikR}(1 - ikR) rnx/(4 pi R^3); alpha = i/k
+            // dG/dn_x = -e^{ikR}(1 - ikR) rnx/(4 pi R^3); alpha = as i/k
             double f = -rnx / (4.0 * FDA_PI * R2 * R);
             double dre = f * (cc + k * R * s), dim = f * (s - k * R * cc);
-            v = c64d(cc * g - dim / k, s * g + dre / k);
+            v = c64d(cc * g - as * dim / k, s * g + as * dre / k);
         }
         E[e] = v;  // column-major 64 x neq
     }
@@ -778,7 +778,8 @@ void fda_far_precompute(fda_handle *h)
             k_emat_l2t<<<dim3(32, nb), 256, 0, s>>>(h->chk_up[l].as<double>(), nchk, dctr.as<double>(),
                                                    dlist.as<int32_t>(), h->leaf_box.as<int32_t>(),
                                                    h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
-                                                   h->cent.as<double>(), h->nrm.as<double>(), h->k, E.as<c64d>());
+                                                   h->cent.as<double>(), h->nrm.as<double>(), h->k,
+                                                   h->cfg.alpha_sign, E.as<c64d>());
             FDA_CHECK_LAUNCH();
             for (int b = 0; b < nb; ++b)
                 gj[b] = gemm_job{E.as<c64d>() + (size_t)b * 64 * nchk, h->Uup[l].as<c64d>(),

@@ -31,7 +31,8 @@ __constant__ double c_q6a[2] = {0.44594849091596488632, 0.09157621350977074346};
 __constant__ double c_q6w[2] = {0.22338158967801146570, 0.10995174365532186764};
 
 // Burton-Miller layer kernel: dG/dn_y + alpha d2G/dn_x dn_y, r = x - y
-__device__ inline c64d bm_kernel(const double *x, const double *nx, const double *y, const double *ny, double k)
+__device__ inline c64d bm_kernel(const double *x, const double *nx, const double *y, const double *ny, double k,
+                                 double as)
 {
     double r0 = x[0] - y[0], r1 = x[1] - y[1], r2 = x[2] - y[2];
     double R2 = r0 * r0 + r1 * r1 + r2 * r2;
@@ -50,12 +51,12 @@ __device__ inline c64d bm_kernel(const double *x, const double *nx, const double
     c64d bracket(nn + (kR * kR - 3.0) * t, -kR * nn + 3.0 * kR * t);
     c64d dl = (rny * inv4pR3) * (e * a);        // dG/dn_y
     c64d hs = inv4pR3 * (e * bracket);          // d2G/dn_x dn_y
-    // alpha * hs with alpha = i/k: (i/k)(re + i im) = (-im/k, re/k)
-    return c64d(dl.re - hs.im / k, dl.im + hs.re / k);
+    // alpha * hs with alpha = as i/k: as (i/k)(re + i im) = as (-im/k, re/k)
+    return c64d(dl.re - as * hs.im / k, dl.im + as * hs.re / k);
 }
 
 __device__ inline c64d rule6(const double *x, const double *nx, const double *p0, const double *p1,
-                             const double *p2, const double *ny, double area, double k)
+                             const double *p2, const double *ny, double area, double k, double as)
 {
     c64d s;
     for (int g = 0; g < 2; ++g) {
@@ -65,7 +66,7 @@ __device__ inline c64d rule6(const double *x, const double *nx, const double *p0
         for (int r = 0; r < 3; ++r) {
             double y[3];
             for (int d = 0; d < 3; ++d) y[d] = bc[r][0] * p0[d] + bc[r][1] * p1[d] + bc[r][2] * p2[d];
-            c64d v = bm_kernel(x, nx, y, ny, k);
+            c64d v = bm_kernel(x, nx, y, ny, k, as);
             s.re += wa * v.re;
             s.im += wa * v.im;
         }
@@ -83,7 +84,7 @@ __device__ inline bool near_pair(const double *ci, const double *cj, double h2j)
 __global__ void k_near_regular(const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend,
                                const int64_t *colptr, const int32_t *cols, const int64_t *off, const double *cent,
                                const double *nrm, const double *v9, const double *area, const double *h2, double k,
-                               c64d *A)
+                               double as, c64d *A)
 {
     int li = blockIdx.x, r = blockIdx.y;
     int B = leaf_box[li];
@@ -97,7 +98,7 @@ __global__ void k_near_regular(const int32_t *leaf_box, const int32_t *bbeg, con
         int j = cl[c];
         if (j == i || near_pair(x, cent + 3 * j, h2[j])) continue;
         const double *p = v9 + 9 * (int64_t)j;
-        row[c] = rule6(x, nx, p, p + 3, p + 6, nrm + 3 * j, area[j], k);
+        row[c] = rule6(x, nx, p, p + 3, p + 6, nrm + 3 * j, area[j], k, as);
     }
 }
 
@@ -130,7 +131,7 @@ __global__ void k_near_special_list(const int32_t *leaf_box, const int32_t *bbeg
 
 // one warp per near entry: 64 sub-triangles, two per lane
 __global__ void k_near_subdiv(const special_entry *list, int64_t n, const double *cent, const double *nrm,
-                              const double *v9, const double *area, double k, c64d *A)
+                              const double *v9, const double *area, double k, double as, c64d *A)
 {
     int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -166,7 +167,7 @@ __global__ void k_near_subdiv(const special_entry *list, int64_t n, const double
                 a[d] = na; b[d] = nb; c[d] = ncc;
             }
         }
-        c64d v = rule6(x, nx, a, b, c, ny, sub_area, k);
+        c64d v = rule6(x, nx, a, b, c, ny, sub_area, k, as);
         acc.re += v.re;
         acc.im += v.im;
     }
@@ -179,7 +180,7 @@ __global__ void k_near_subdiv(const special_entry *list, int64_t n, const double
 
 // self entries: 1/2 + alpha * finite part (one thread each)
 __global__ void k_near_self(const special_entry *list, int64_t n, const double *cent, const double *v9, double k,
-                            c64d *A)
+                            double as, c64d *A)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -208,10 +209,10 @@ __global__ void k_near_self(const special_entry *list, int64_t n, const double *
             dim += half * c_gl_w[g] * sn / rho;
         }
     }
-    // H = ik/2 - (st + D)/(4 pi);  A_ii = 1/2 + (i/k) H
+    // H = ik/2 - (st + D)/(4 pi);  A_ii = 1/2 + as (i/k) H
     double Hre = -(st + dre) / (4.0 * FDA_PI);
     double Him = 0.5 * k - dim / (4.0 * FDA_PI);
-    A[e.idx] = c64d(0.5 - Him / k, Hre / k);
+    A[e.idx] = c64d(0.5 - as * Him / k, as * Hre / k);
 }
 
 __global__ void k_to_f32(const c64d *a, c32f *b, int64_t n)
@@ -294,16 +295,18 @@ void fda_near_build(fda_handle *h)
     k_near_regular<<<g, 128, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
                                      h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
                                      h->cent.as<double>(), h->nrm.as<double>(), h->verts9.as<double>(),
-                                     h->area.as<double>(), h->h2.as<double>(), h->k, h->op64.near.as<c64d>());
+                                     h->area.as<double>(), h->h2.as<double>(), h->k, h->cfg.alpha_sign,
+                                     h->op64.near.as<c64d>());
     FDA_CHECK_LAUNCH();
     if (nspec > 0) {
         k_near_subdiv<<<fda_blocks((int64_t)nspec * 32, 256), 256, 0, s>>>(
             list.as<special_entry>(), (int64_t)nspec, h->cent.as<double>(), h->nrm.as<double>(),
-            h->verts9.as<double>(), h->area.as<double>(), h->k, h->op64.near.as<c64d>());
+            h->verts9.as<double>(), h->area.as<double>(), h->k, h->cfg.alpha_sign, h->op64.near.as<c64d>());
         FDA_CHECK_LAUNCH();
         k_near_self<<<fda_blocks((int64_t)nspec, 128), 128, 0, s>>>(list.as<special_entry>(), (int64_t)nspec,
                                                                      h->cent.as<double>(), h->verts9.as<double>(),
-                                                                     h->k, h->op64.near.as<c64d>());
+                                                                     h->k, h->cfg.alpha_sign,
+                                                                     h->op64.near.as<c64d>());
         FDA_CHECK_LAUNCH();
     }
     FDA_CUDA(cudaStreamSynchronize(s));

@@ -152,3 +152,48 @@ def test_errors_are_reported():
         fda_build_tree(h, v, deg, 1.0)
     assert e.value.status == FDA_ERR_ARG
     fda_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_blockdiag_preconditioner_same_solution(precision):
+    """Right preconditioning leaves the solution unchanged (the residual is
+    the unpreconditioned one).  It does not lower the iteration count for
+    this operator; that is measured in the benchmark, not asserted here."""
+    from paper_1403_4747_gb300 import fda_set_precond
+    v, f = icosphere(3)
+    k = 6.0
+    P = _problem(v, f, k, precision=precision, precond=1, maxit=4000, restart=200)
+    b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+    fda_set_precond(P.h, 0)
+    x0, i0 = P.solve(b, 1e-6)
+    fda_set_precond(P.h, 1)
+    x1, i1 = P.solve(b, 1e-6)
+    assert i0.rel_resid_fp64 <= 1e-6 and i1.rel_resid_fp64 <= 1e-6
+    assert _rel(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-5
+
+
+def test_blockdiag_is_exact_inverse_on_a_single_leaf():
+    """20 triangles form one leaf: the block-diagonal preconditioner is then
+    the exact inverse, and GMRES converges in one iteration to the LU
+    solution."""
+    v, f = icosphere(0)
+    k = 2.0
+    P = _problem(v, f, k, precond=1)
+    b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+    x, info = P.solve(b, 1e-10)
+    assert info.iters <= 2
+    u = oracle.lu_solve(oracle.assemble(v, f, k), oracle.rhs_plane_wave(v, f, k, [[0, 0, 1.0]])[0])
+    assert _rel(x.cpu().numpy(), u) < 1e-9
+
+
+def test_conjugate_coupling_parity():
+    """alpha = -i/k: the GPU matvec and right-hand side match the oracle with
+    the same coupling."""
+    v, f = icosphere(4)
+    k = 20.0
+    x = complex_normal(len(f), seed=4)
+    P = _problem(v, f, k, alpha_sign=-1.0)
+    y = P.apply(_dev(x)).cpu().numpy()
+    assert _rel(y, oracle.matvec(v, f, k, x, alpha_sign=-1.0)) < 1e-4
+    b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0])).cpu().numpy()
+    assert _rel(b, oracle.rhs_plane_wave(v, f, k, [[0.0, 0.0, 1.0]], alpha_sign=-1.0)[0]) < 1e-13

@@ -194,18 +194,21 @@ def test_gauss_identity_and_hypersingular_of_constant():
     assert np.abs(h).max() * np.sqrt(h2.mean()) < 1e-5
 
 
-def test_sphere_eigenvalues_converge():
+@pytest.mark.parametrize("alpha_sign", [1.0, -1.0])
+def test_sphere_eigenvalues_converge(alpha_sign):
     """A P_n ~ lambda_n P_n on the unit sphere: the Rayleigh quotient
-    converges to lambda_n (closed form) as the mesh is refined."""
+    converges to lambda_n (closed form) as the mesh is refined, for both
+    signs of the coupling alpha = +-i/k."""
     errs = {}
     for L in (2, 3, 4):
         v, f = icosphere(L)
         c, *_ = oracle.geometry(v, f)
         for n in (0, 1, 2, 4):
             x = oracle.legendre_on_mesh(c, n)
-            y = oracle.matvec(v, f, K, x)
+            y = oracle.matvec(v, f, K, x, alpha_sign=alpha_sign)
             lam = np.vdot(x, y) / np.vdot(x, x)
-            errs[(L, n)] = abs(lam - oracle.sphere_eigenvalue(n, K)) / abs(oracle.sphere_eigenvalue(n, K))
+            ref = oracle.sphere_eigenvalue(n, K, alpha_sign)
+            errs[(L, n)] = abs(lam - ref) / abs(ref)
     for n in (0, 1, 2, 4):
         assert errs[(4, n)] < errs[(3, n)] / 2.5 < errs[(2, n)] / 5
         assert errs[(4, n)] < 8e-3
@@ -271,6 +274,36 @@ def test_eigenvalues_consistent_with_mie():
 
 
 # ---------------------------------------------------------------- solve
+def test_conjugate_coupling_same_solution_right_half_plane():
+    """Both couplings solve the same scattering problem (their LU solutions
+    agree with each other and with the Mie series to discretisation error);
+    with the normal into the body, alpha = -i/k keeps every sphere eigenvalue
+    in the right half-plane while alpha = +i/k spreads them around 0, which is
+    why GMRES needs more iterations for +i/k."""
+    k = 5.0
+    v, f = icosphere(3)
+    c, *_ = oracle.geometry(v, f)
+    ct = (c / np.linalg.norm(c, axis=1, keepdims=True))[:, 2]
+    um = oracle.mie_surface_field(k, ct)
+    sols = {}
+    for s_ in (1.0, -1.0):
+        a = oracle.assemble(v, f, k, alpha_sign=s_)
+        b = oracle.rhs_plane_wave(v, f, k, [[0.0, 0.0, 1.0]], alpha_sign=s_)[0]
+        sols[s_] = oracle.lu_solve(a, b)
+        assert np.linalg.norm(sols[s_] - um) / np.linalg.norm(um) < 2e-2
+    assert np.linalg.norm(sols[1.0] - sols[-1.0]) / np.linalg.norm(sols[1.0]) < 2e-2
+    lam_p = np.array([oracle.sphere_eigenvalue(n, 20.0, 1.0) for n in range(60)])
+    lam_m = np.array([oracle.sphere_eigenvalue(n, 20.0, -1.0) for n in range(60)])
+    assert lam_m.real.min() > 0.4 and lam_p.real.min() < -0.5
+    # where it shows (kD = 40): fewer GMRES iterations for -i/k
+    iters = {}
+    for s_ in (1.0, -1.0):
+        a = oracle.assemble(v, f, 20.0, alpha_sign=s_)
+        b = oracle.rhs_plane_wave(v, f, 20.0, [[0.0, 0.0, 1.0]], alpha_sign=s_)[0]
+        _, iters[s_], _ = oracle.gmres(lambda z: a @ z, b, tol=1e-6, restart=400)
+    assert iters[-1.0] < 0.8 * iters[1.0]
+
+
 def test_solution_converges_to_mie_and_gmres_matches_lu():
     """Rigid sphere, plane wave e^{ikz}, k = 5: the dense-LU solution's error
     against the Mie series decays under refinement, and GMRES at tol 1e-9
