@@ -174,7 +174,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     P = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps,
-                     precond=1 if args.blockdiag else 0, restart=args.restart)
+                     precond=1 if args.blockdiag else 0, restart=args.restart, max_rhs=max(1, args.batch))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     st = P.stats()
@@ -227,6 +227,33 @@ def run_native(args):
     plain_ms = (time.perf_counter() - tp) / nplain * 1e3
     pt64 = pass_times(1)
     F.fda_set_precision(P.h, F.FDA_CHOSEN_FP32)
+
+    # many right-hand sides per pass (incidence directions): every operator
+    # read serves all of them
+    batched = None
+    if args.batch > 1:
+        xb = torch.from_numpy(complex_normal(n, seed=77, nrhs=args.batch)).cuda()
+        yb = torch.empty_like(xb)
+        for _ in range(2):
+            P.apply(xb, yb)
+        torch.cuda.synchronize()
+        nb_steps = max(3, args.steps // 4)
+        e0.record(stream)
+        for _ in range(nb_steps):
+            P.apply(xb, yb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = reduce_max(e0.elapsed_time(e1) / nb_steps)
+        F.fda_set_timing(P.h, True)
+        P.apply(xb, yb)
+        bpt = np.array(F.fda_get_pass_times(P.h))
+        F.fda_set_timing(P.h, False)
+        m2l_b = _m2l_flops(P) * args.batch
+        batched = {"nrhs": args.batch, "ms_per_pass": bms,
+                   "rhs_matvec_per_s": ws * args.batch * 1e3 / bms,
+                   "pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], bpt.tolist())),
+                   "m2l_tflops": m2l_b / (bpt[2] * 1e-3) / 1e12}
+        del xb, yb
 
     # end to end through the C ABI with host buffers (pinned)
     xh = torch.from_numpy(complex_normal(n, seed=99)).pin_memory()
@@ -326,6 +353,7 @@ def run_native(args):
                            "pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt64.tolist()))},
             "chosen_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32.tolist())),
             "near_field_gbs": near_gbs,
+            "batched_rhs": batched,
             "solve": solve,
             "tree": {"levels": nlev, "boxes": st.n_boxes, "leaves": st.n_leaves, "nnz_near": st.nnz_near,
                      "m2l_pairs": st.n_m2l, "m2l_ops": st.n_m2l_ops,
@@ -368,6 +396,7 @@ def main():
     ap.add_argument("--no-alt-coupling", action="store_true")
     ap.add_argument("--blockdiag", action="store_true", help="also solve with the block-diagonal preconditioner")
     ap.add_argument("--restart", type=int, default=100)
+    ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -72,6 +72,8 @@ typedef struct {
     int precond;           /* 0 none (the paper's setting), 1 leaf block-diagonal (right preconditioner) */
     double alpha_sign;     /* coupling alpha = alpha_sign * i/k: +1 (default) the paper's i/k as written with the
                               normal into the body; -1 the conjugate coupling */
+    int max_rhs;           /* right-hand sides one fda_apply pass processes together (1..256, default 1);
+                              densities and staging vectors are sized for it */
     void *cuda_stream;     /* cudaStream_t, or NULL */
 } fda_config;
 
@@ -129,7 +131,9 @@ fda_status fda_build_tree(fda_handle *h, const double *verts, int64_t nv, const 
 fda_status fda_precompute_translations(fda_handle *h);
 
 /* y = A x (Sec. 3.3 Steps 2-4): x, y device pointers, nrhs columns with
- * leading dimension ld (complex elements).  x and y must not overlap. */
+ * leading dimension ld (complex elements).  x and y must not overlap.
+ * Columns are processed max_rhs at a time in one pass (every operator read
+ * serves all of them). */
 fda_status fda_apply(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, int64_t ld);
 
 /* Same as fda_apply with x and y in host memory: the copies to and from the

@@ -25,7 +25,7 @@ class fda_config(ctypes.Structure):
                 ("hf_na", ctypes.c_int), ("leaf_max", ctypes.c_int), ("hf_wavelengths", ctypes.c_double),
                 ("rho_min", ctypes.c_double), ("precision", ctypes.c_int), ("mode", ctypes.c_int),
                 ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("precond", ctypes.c_int),
-                ("alpha_sign", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+                ("alpha_sign", ctypes.c_double), ("max_rhs", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
 
 
 class fda_info(ctypes.Structure):

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <new>
 #include <vector>
@@ -93,6 +94,7 @@ void fda_default_config(fda_config *c)
     c->maxit = 1000;
     c->precond = 0;
     c->alpha_sign = 1.0;
+    c->max_rhs = 1;
     c->cuda_stream = nullptr;
 }
 
@@ -106,7 +108,7 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
         c.p_hf < 3 || c.p_hf > 16 || c.hf_nr < 1 || c.hf_na < 8 || !(c.hf_wavelengths > 0) || !(c.rho_min >= 2.0) ||
         (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
         (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.maxit < 1 || c.precond < 0 ||
-        c.precond > 1 || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0))
+        c.precond > 1 || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0) || c.max_rhs < 1 || c.max_rhs > 256)
         return FDA_ERR_ARG;
     fda_handle *h = new (std::nothrow) fda_handle();
     if (!h) return FDA_ERR_OOM;
@@ -166,8 +168,8 @@ fda_status fda_precompute_translations(fda_handle *h)
         }
         fda_alloc_densities(h, want32);
         if (h->lev_lo >= 0) fda_build_batches(h);
-        h->xs.alloc(sizeof(c64d) * h->N);
-        h->ys.alloc(sizeof(c64d) * h->N);
+        h->xs.alloc(sizeof(c64d) * h->N * h->cfg.max_rhs);
+        h->ys.alloc(sizeof(c64d) * h->N * h->cfg.max_rhs);
         FDA_CUDA(cudaStreamSynchronize(h->stream));
         h->precompute_s = now_s() - t0;
         h->state = 2;
@@ -186,12 +188,16 @@ fda_status fda_apply(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, in
         return FDA_ERR_ARG;
     }
     return guarded(h, [&] {
-        for (int m = 0; m < nrhs; ++m) {
-            const c64d *xm = reinterpret_cast<const c64d *>(x) + (int64_t)m * ld;
-            c64d *ym = reinterpret_cast<c64d *>(y) + (int64_t)m * ld;
-            fda_gather_to_sorted(h, xm, h->xs.as<c64d>());
-            fda_apply_sorted(h, h->xs.as<c64d>(), h->ys.as<c64d>(), h->cfg.precision);
-            fda_scatter_from_sorted(h, h->ys.as<c64d>(), ym);
+        const int mr = std::max(1, h->cfg.max_rhs);
+        for (int m0 = 0; m0 < nrhs; m0 += mr) {
+            int nm = std::min(mr, nrhs - m0);
+            for (int m = 0; m < nm; ++m)
+                fda_gather_to_sorted(h, reinterpret_cast<const c64d *>(x) + (int64_t)(m0 + m) * ld,
+                                     h->xs.as<c64d>() + (int64_t)m * h->N);
+            fda_apply_sorted(h, h->xs.as<c64d>(), h->ys.as<c64d>(), h->cfg.precision, nm);
+            for (int m = 0; m < nm; ++m)
+                fda_scatter_from_sorted(h, h->ys.as<c64d>() + (int64_t)m * h->N,
+                                        reinterpret_cast<c64d *>(y) + (int64_t)(m0 + m) * ld);
         }
     });
 }

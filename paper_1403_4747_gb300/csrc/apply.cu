@@ -11,6 +11,8 @@
 // per box and cone; p~ = U_dn^H p).  Every pass is templated on the real
 // type: double (plain FP64 form) or float (chosen form: FP32 operators and
 // densities, FP32 accumulation, the result added into the FP64 output).
+#include <algorithm>
+
 #include "fda_internal.cuh"
 
 namespace {
@@ -23,6 +25,7 @@ template <typename R>
 struct lvl_ptrs {
     int box0[FDA_MAX_LEVELS], nbox[FDA_MAX_LEVELS], T[FDA_MAX_LEVELS], ncones[FDA_MAX_LEVELS];
     int nc[FDA_MAX_LEVELS], hf[FDA_MAX_LEVELS];
+    int64_t stride[FDA_MAX_LEVELS];  // per right-hand side: nbox * ncones * T
     cx<R> *q[FDA_MAX_LEVELS];
     cx<R> *p[FDA_MAX_LEVELS];
     const cx<R> *Kt[FDA_MAX_LEVELS];
@@ -42,10 +45,16 @@ __device__ inline cx<R> ldx(const void *x, int64_t i, int x64)
 }
 
 // ---- Step 4: near field, y = A_near x (overwrites y)
-template <typename R>
+// Right-hand sides are processed in groups of NR per CTA (blockIdx.z), so
+// every matrix entry read from HBM serves NR products (NR = 1 for a single
+// right-hand side).
+constexpr int NRG = 8;
+
+template <typename R, int NR>
 __global__ void k_near_apply(const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend,
                              const int64_t *colptr, const int64_t *rptr, const int32_t *rb, const int32_t *re,
-                             const int64_t *off, const cx<R> *A, const void *x, int x64, c64d *y)
+                             const int64_t *off, const cx<R> *A, const void *x, int x64, int64_t xstr, int mr,
+                             c64d *y, int64_t ldy)
 {
     int li = blockIdx.x;
     int B = leaf_box[li];
@@ -53,26 +62,39 @@ __global__ void k_near_apply(const int32_t *leaf_box, const int32_t *bbeg, const
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int r = blockIdx.y * (AT / 32) + warp;
     if (r >= nB) return;
+    const int m0 = blockIdx.z * NR;
+    const int nm = min(NR, mr - m0);
     int64_t nc = colptr[li + 1] - colptr[li];
     const cx<R> *row = A + off[li] + (int64_t)r * nc;
-    cx<R> acc;
+    cx<R> acc[NR];
     int64_t coff = 0;
     for (int64_t g = rptr[li]; g < rptr[li + 1]; ++g) {
         int b = rb[g], len = re[g] - b;
-        for (int c = lane; c < len; c += 32) cfma(acc, row[coff + c], ldx<R>(x, b + c, x64));
+        for (int c = lane; c < len; c += 32) {
+            cx<R> a = row[coff + c];
+#pragma unroll
+            for (int mm = 0; mm < NR; ++mm)
+                if (mm < nm) cfma(acc[mm], a, ldx<R>(x, (int64_t)(m0 + mm) * xstr + b + c, x64));
+        }
         coff += len;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
-        acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+#pragma unroll
+    for (int mm = 0; mm < NR; ++mm) {
+        if (mm >= nm) break;  // uniform across the warp
+        cx<R> v = acc[mm];
+        for (int o = 16; o > 0; o >>= 1) {
+            v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+            v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+        }
+        if (lane == 0) y[(int64_t)(m0 + mm) * ldy + i0 + r] = c64d((double)v.re, (double)v.im);
     }
-    if (lane == 0) y[i0 + r] = c64d((double)acc.re, (double)acc.im);
 }
 
 // ---- Step 2: S2M at leaves, q~ = S~ x_B
 template <typename R>
 __global__ void k_s2m(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *blev, const int32_t *bbeg,
-                      const int32_t *bend, const int64_t *loff, const cx<R> *St, const void *x, int x64)
+                      const int32_t *bend, const int64_t *loff, const cx<R> *St, const void *x, int x64,
+                      int64_t xstr, int mr)
 {
     __shared__ cx<R> xs[64];
     int li = blockIdx.x;
@@ -81,21 +103,24 @@ __global__ void k_s2m(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
     int T = P.T[l];
     if (T == 0) return;
     int j0 = bbeg[B], nB = bend[B] - j0;
-    for (int j = threadIdx.x; j < nB; j += blockDim.x) xs[j] = ldx<R>(x, j0 + j, x64);
-    __syncthreads();
     const cx<R> *S = St + loff[li];
-    cx<R> *q = P.q[l] + (int64_t)(B - P.box0[l]) * T;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        cx<R> acc;
-        for (int j = 0; j < nB; ++j) cfma(acc, S[(int64_t)j * T + t], xs[j]);
-        q[t] = acc;
+    for (int m = 0; m < mr; ++m) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < nB; j += blockDim.x) xs[j] = ldx<R>(x, (int64_t)m * xstr + j0 + j, x64);
+        __syncthreads();
+        cx<R> *q = P.q[l] + m * P.stride[l] + (int64_t)(B - P.box0[l]) * T;
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            cx<R> acc;
+            for (int j = 0; j < nB; ++j) cfma(acc, S[(int64_t)j * T + t], xs[j]);
+            q[t] = acc;
+        }
     }
 }
 
 // ---- Step 3: L2T at leaves, y += T~ p~
 template <typename R>
 __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *blev, const int32_t *bbeg,
-                      const int32_t *bend, const int64_t *loff, const cx<R> *Tt, c64d *y)
+                      const int32_t *bend, const int64_t *loff, const cx<R> *Tt, c64d *y, int64_t ldy, int mr)
 {
     __shared__ cx<R> pp[MAXT];
     int li = blockIdx.x;
@@ -104,15 +129,19 @@ __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
     int T = P.T[l];
     if (T == 0) return;
     int i0 = bbeg[B], nB = bend[B] - i0;
-    const cx<R> *src = P.p[l] + (int64_t)(B - P.box0[l]) * T;
-    for (int j = threadIdx.x; j < T; j += blockDim.x) pp[j] = src[j];
-    __syncthreads();
     const cx<R> *Tm = Tt + loff[li];
-    for (int i = threadIdx.x; i < nB; i += blockDim.x) {
-        cx<R> acc;
-        for (int t = 0; t < T; ++t) cfma(acc, Tm[(int64_t)t * 64 + i], pp[t]);
-        c64d v = y[i0 + i];
-        y[i0 + i] = c64d(v.re + (double)acc.re, v.im + (double)acc.im);
+    for (int m = 0; m < mr; ++m) {
+        const cx<R> *src = P.p[l] + m * P.stride[l] + (int64_t)(B - P.box0[l]) * T;
+        __syncthreads();
+        for (int j = threadIdx.x; j < T; j += blockDim.x) pp[j] = src[j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nB; i += blockDim.x) {
+            cx<R> acc;
+            for (int t = 0; t < T; ++t) cfma(acc, Tm[(int64_t)t * 64 + i], pp[t]);
+            c64d *yp = y + (int64_t)m * ldy + i0 + i;
+            c64d v = *yp;
+            *yp = c64d(v.re + (double)acc.re, v.im + (double)acc.im);
+        }
     }
 }
 
@@ -133,6 +162,7 @@ lvl_ptrs<R> make_ptrs(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p)
         P.ncones[l] = l < h->nlev ? h->lev[l].ncones : 1;
         P.nc[l] = l < h->nlev ? h->lev[l].nc : 0;
         P.hf[l] = l < h->nlev ? h->lev[l].hf : 0;
+        P.stride[l] = l < h->nlev ? (int64_t)h->lev[l].nbox * h->lev[l].ncones * h->lev[l].T : 0;
         P.q[l] = q[l].as<cx<R>>();
         P.p[l] = p[l].as<cx<R>>();
         P.Kt[l] = ops.Kt[l].template as<cx<R>>();
@@ -143,8 +173,9 @@ lvl_ptrs<R> make_ptrs(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p)
 }
 
 template <typename R>
-void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x, int x64, c64d *y)
+void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x, int x64, c64d *y, int mr)
 {
+    const int64_t N = h->N;
     cudaStream_t s = h->stream;
     const int NL = h->nleaf;
     auto mark = [&](int i) {
@@ -152,11 +183,21 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     };
     mark(0);
     const int max_rows = h->max_leaf_rows;
-    dim3 gn(NL, (max_rows + AT / 32 - 1) / (AT / 32));
-    k_near_apply<R><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
-                                      h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
-                                      h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(), h->nr_end.as<int32_t>(),
-                                      h->nf_off.as<int64_t>(), ops.near.template as<cx<R>>(), x, x64, y);
+    if (mr == 1) {
+        dim3 gn(NL, (max_rows + AT / 32 - 1) / (AT / 32), 1);
+        k_near_apply<R, 1><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+                                             h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
+                                             h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(),
+                                             h->nr_end.as<int32_t>(), h->nf_off.as<int64_t>(),
+                                             ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+    } else {
+        dim3 gn(NL, (max_rows + AT / 32 - 1) / (AT / 32), (mr + NRG - 1) / NRG);
+        k_near_apply<R, NRG><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+                                               h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
+                                               h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(),
+                                               h->nr_end.as<int32_t>(), h->nf_off.as<int64_t>(),
+                                               ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+    }
     FDA_CHECK_LAUNCH();
     mark(1);
     if (h->lev_lo < 0) {
@@ -166,30 +207,33 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     lvl_ptrs<R> P = make_ptrs<R>(h, ops, q, p);
     for (int l = h->lev_lo; l < h->nlev; ++l) {
         const level_info &L = h->lev[l];
-        size_t bytes = sizeof(cx<R>) * (size_t)L.nbox * L.ncones * L.T;
+        size_t bytes = sizeof(cx<R>) * (size_t)L.nbox * L.ncones * L.T * mr;
         FDA_CUDA(cudaMemsetAsync(q[l].p, 0, bytes, s));
         FDA_CUDA(cudaMemsetAsync(p[l].p, 0, bytes, s));
     }
     k_s2m<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
                                h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(),
-                               ops.St.template as<cx<R>>(), x, x64);
+                               ops.St.template as<cx<R>>(), x, x64, N, mr);
     FDA_CHECK_LAUNCH();
     mark(2);
     // M2M bottom-up: q~_parent += M~ q~_child
     for (int l = h->nlev - 2; l >= h->lev_lo; --l)
-        fda_run_batch<R>(h->b_m2m[l], P.Mt[l], h->lev[l].T, h->lev[l + 1].T, P.q[l + 1], P.q[l], s);
+        fda_run_batch<R>(h->b_m2m[l], P.Mt[l], h->lev[l].T, h->lev[l + 1].T, P.q[l + 1], P.q[l], mr,
+                         P.stride[l + 1], P.stride[l], s);
     mark(3);
     // M2L at every level: p~_target += K~ q~_source
     for (int l = h->lev_lo; l < h->nlev; ++l)
-        fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], s);
+        fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
+                         P.stride[l], s);
     mark(4);
     // L2L top-down: p~_child += L~ p~_parent
     for (int l = h->lev_lo; l + 1 < h->nlev; ++l)
-        fda_run_batch<R>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], s);
+        fda_run_batch<R>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], mr,
+                         P.stride[l], P.stride[l + 1], s);
     mark(5);
     k_l2t<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
                                h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(), ops.Tt.template as<cx<R>>(),
-                               y);
+                               y, N, mr);
     FDA_CHECK_LAUNCH();
     mark(6);
 }
@@ -201,7 +245,7 @@ void fda_alloc_densities(fda_handle *h, int want32)
     for (int l = 0; l < h->nlev; ++l) {
         const level_info &L = h->lev[l];
         if (!L.active || L.T == 0) continue;
-        size_t n = (size_t)L.nbox * L.ncones * L.T;
+        size_t n = (size_t)L.nbox * L.ncones * L.T * std::max(1, h->cfg.max_rhs);
         h->q64[l].alloc(sizeof(c64d) * n);
         h->p64[l].alloc(sizeof(c64d) * n);
         if (want32) {
@@ -212,16 +256,17 @@ void fda_alloc_densities(fda_handle *h, int want32)
 }
 
 // ys = A xs, both complex double in Morton order
-void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision)
+void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, int mr)
 {
+    if (mr < 1 || mr > std::max(1, h->cfg.max_rhs)) fda_fail(FDA_ERR_ARG, "more right-hand sides than max_rhs");
     if (precision == FDA_CHOSEN_FP32) {
         if (!h->have32) fda_fail(FDA_ERR_STATE, "FP32 operators were not built (precision = plain)");
-        if (!h->xs32.p) h->xs32.alloc(sizeof(c32f) * h->N);
-        k_c64_to_c32<<<fda_blocks(h->N, 256), 256, 0, h->stream>>>(xs, h->xs32.as<c32f>(), h->N);
+        if (!h->xs32.p) h->xs32.alloc(sizeof(c32f) * h->N * std::max(1, h->cfg.max_rhs));
+        k_c64_to_c32<<<fda_blocks(h->N * mr, 256), 256, 0, h->stream>>>(xs, h->xs32.as<c32f>(), h->N * mr);
         FDA_CHECK_LAUNCH();
-        apply_impl<float>(h, h->op32, h->q32, h->p32, h->xs32.p, 0, ys);
+        apply_impl<float>(h, h->op32, h->q32, h->p32, h->xs32.p, 0, ys, mr);
     } else {
-        apply_impl<double>(h, h->op64, h->q64, h->p64, xs, 1, ys);
+        apply_impl<double>(h, h->op64, h->q64, h->p64, xs, 1, ys, mr);
     }
     if (h->timing) {
         FDA_CUDA(cudaEventSynchronize(h->ev[6]));

@@ -131,8 +131,12 @@ struct level_info {
 struct tr_batch {
     dbuf tiles, pairs;
     int ntiles = 0;
-    int np = 32;          // pairs per tile (32 or 64)
+    int np = 32;          // columns (pair x right-hand side) per tile (32 or 64)
+    int tm = 64;          // output rows per tile (32 or 64)
+    int tout = 0;         // output rank
+    int mr = 0;           // right-hand sides the current tiles were cut for
     int64_t npairs = 0;
+    std::vector<int> op_start;  // pairs of operator o: [op_start[o], op_start[o+1])
 };
 
 template <typename T>
@@ -244,7 +248,7 @@ void fda_geometry_build(fda_handle *h, const double *verts, int64_t nv, const in
 void fda_tree_build(fda_handle *h);
 void fda_near_build(fda_handle *h);
 void fda_far_precompute(fda_handle *h);
-void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision);
+void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, int mr = 1);
 void fda_rhs_sorted(fda_handle *h, const double *dirs_dev, int nrhs, c64d *b_sorted);
 void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
@@ -255,8 +259,8 @@ void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z);
 
 void fda_build_batches(fda_handle *h);
 template <typename R>
-void fda_run_batch(const tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst,
-                   cudaStream_t s);
+void fda_run_batch(tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst, int mr,
+                   int64_t sstride, int64_t dstride, cudaStream_t s);
 
 // scans and sorts (sort.cu)
 void fda_exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, int32_t *total_host);

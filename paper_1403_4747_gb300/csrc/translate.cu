@@ -6,7 +6,7 @@
 // and L2L).  The (src, dst) pairs are grouped by operator into tiles of up to
 // NP pairs and TM output rows; one CTA streams the operator's TM-row panel
 // through shared memory once and multiplies it against the NP gathered source
-// vectors, a complex GEMM of TM x Tin x NP with 4 x (NP/16) register blocking,
+// vectors, a complex GEMM of TM x Tin x NP with (TM/16) x (NP/16) register blocking,
 // then adds its results into the targets with atomics (targets of one tile are
 // distinct; different operators reach the same target from other CTAs).
 // This replaces one operator read per (target, source) pair by one per tile.
@@ -19,7 +19,6 @@ int fda_child_cone(const fda_handle *h, int l, int u);
 
 namespace {
 
-constexpr int TM = 64;   // output rows per tile
 constexpr int TK = 16;   // inner dimension per shared-memory stage
 constexpr int BT = 256;  // threads
 
@@ -43,19 +42,40 @@ __device__ inline void atomic_add_cx<double>(cx<double> *p, cx<double> v)
     atomicAdd(&p->im, v.im);
 }
 
-template <typename R, int NP>
+// One tile: TM output rows x NP (source, target) pairs.  Thread (tx, ty)
+// owns rows row0 + tx + 16 i (i < TM/16; a warp reads consecutive rows of the
+// operator panel, so shared-memory reads are conflict-free) and pairs
+// ty * PT + j (j < PT = NP/16).
+//
+// With several right-hand sides the source densities of right-hand side m
+// sit at offset m * sstride and the targets at m * dstride (M2M and L2L read
+// one level and write another), and a tile's columns run over (pair,
+// right-hand side) combinations: column v of an operator's range is pair
+// v / mr, side v % mr.
+template <typename R, int TM, int NP>
 __global__ void __launch_bounds__(BT) k_btr(const tr_tile *tiles, const int2 *pairs, const cx<R> *ops, int Tout,
-                                            int Tin, const cx<R> *src, cx<R> *dst)
+                                            int Tin, const cx<R> *src, cx<R> *dst, int mr, int64_t sstride,
+                                            int64_t dstride)
 {
     constexpr int PT = NP / 16;  // pairs per thread
+    constexpr int RT = TM / 16;  // rows per thread
     __shared__ cx<R> As[TK][TM];
-    __shared__ cx<R> Bs[TK][NP];
-    __shared__ int2 pp[NP];
+    __shared__ cx<R> Bs[TK][NP + 1];
+    __shared__ longlong2 pp[NP];
     const tr_tile t = tiles[blockIdx.x];
     const cx<R> *A = ops + (int64_t)t.op * Tout * Tin;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    if (tid < NP) pp[tid] = tid < t.npair ? pairs[t.pair0 + tid] : make_int2(-1, -1);
-    cx<R> acc[4][PT];
+    if (tid < NP) {
+        longlong2 v = make_longlong2(-1, -1);
+        if (tid < t.npair) {
+            int vi = t.pair0 + tid;
+            int pi = vi / mr, m = vi - pi * mr;
+            int2 q = pairs[pi];
+            v = make_longlong2(q.x + m * sstride, q.y + m * dstride);
+        }
+        pp[tid] = v;
+    }
+    cx<R> acc[RT][PT];
     __syncthreads();
     for (int k0 = 0; k0 < Tin; k0 += TK) {
         for (int e = tid; e < TK * TM; e += BT) {
@@ -64,21 +84,21 @@ __global__ void __launch_bounds__(BT) k_btr(const tr_tile *tiles, const int2 *pa
             As[kk][rr] = (c < Tin && r < Tout) ? A[(int64_t)c * Tout + r] : cx<R>();
         }
         for (int e = tid; e < TK * NP; e += BT) {
-            int p = e / TK, kk = e % TK;
+            int p = e / TK, kk = e % TK;  // 16 consecutive entries of one source vector per half-warp
             int c = k0 + kk;
-            int so = pp[p].x;
+            long long so = pp[p].x;
             Bs[kk][p] = (so >= 0 && c < Tin) ? src[so + c] : cx<R>();
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < TK; ++kk) {
-            cx<R> a[4], b[PT];
+            cx<R> a[RT], b[PT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx * 4 + i];
+            for (int i = 0; i < RT; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
             for (int j = 0; j < PT; ++j) b[j] = Bs[kk][ty * PT + j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RT; ++i)
 #pragma unroll
                 for (int j = 0; j < PT; ++j) cfma(acc[i][j], a[i], b[j]);
         }
@@ -88,10 +108,10 @@ __global__ void __launch_bounds__(BT) k_btr(const tr_tile *tiles, const int2 *pa
     for (int j = 0; j < PT; ++j) {
         int p = ty * PT + j;
         if (p >= t.npair) continue;
-        int dof = pp[p].y;
+        long long dof = pp[p].y;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int r = t.row0 + tx * 4 + i;
+        for (int i = 0; i < RT; ++i) {
+            int r = t.row0 + tx + 16 * i;
             if (r < Tout) atomic_add_cx<R>(dst + dof + r, acc[i][j]);
         }
     }
@@ -110,20 +130,36 @@ void make_batch(std::vector<pair_rec> &pr, int nops, int Tout, tr_batch &B)
     std::vector<int2> pairs(pr.size());
     std::vector<int> pos(cnt.begin(), cnt.end() - 1);
     for (auto &p : pr) pairs[pos[p.op]++] = make_int2(p.src, p.dst);
-    double avg = pr.empty() ? 0.0 : (double)pr.size() / std::max(1, nops);
+    // row-tile height: the one that pads Tout the least (ties: 64)
+    int pad64 = (Tout + 63) / 64 * 64 - Tout, pad32 = (Tout + 31) / 32 * 32 - Tout;
+    B.tm = pad64 <= pad32 ? 64 : 32;
+    B.tout = Tout;
+    B.op_start.assign(cnt.begin(), cnt.end());
+    B.npairs = (int64_t)pairs.size();
+    B.pairs.alloc(sizeof(int2) * std::max<size_t>(pairs.size(), 1));
+    if (!pairs.empty()) FDA_CUDA(cudaMemcpy(B.pairs.p, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice));
+    B.mr = 0;
+}
+
+// tiles for mr right-hand sides: each operator's pairs x mr columns, cut
+// into NP-column, TM-row tiles
+void ensure_tiles(tr_batch &B, int mr)
+{
+    if (B.mr == mr) return;
+    const int nops = (int)B.op_start.size() - 1;
+    double avg = B.npairs == 0 ? 0.0 : (double)B.npairs * mr / std::max(1, nops);
     B.np = avg >= 48.0 ? 64 : 32;
     std::vector<tr_tile> tiles;
     for (int o = 0; o < nops; ++o) {
-        int a = cnt[o], b = cnt[o + 1];
+        int a = B.op_start[o] * mr, b = B.op_start[o + 1] * mr;
         for (int p0 = a; p0 < b; p0 += B.np)
-            for (int r0 = 0; r0 < Tout; r0 += TM) tiles.push_back(tr_tile{o, p0, std::min(B.np, b - p0), r0});
+            for (int r0 = 0; r0 < B.tout; r0 += B.tm) tiles.push_back(tr_tile{o, p0, std::min(B.np, b - p0), r0});
     }
     B.ntiles = (int)tiles.size();
-    B.npairs = (int64_t)pairs.size();
     B.tiles.alloc(sizeof(tr_tile) * std::max<size_t>(tiles.size(), 1));
-    B.pairs.alloc(sizeof(int2) * std::max<size_t>(pairs.size(), 1));
-    if (!tiles.empty()) FDA_CUDA(cudaMemcpy(B.tiles.p, tiles.data(), sizeof(tr_tile) * tiles.size(), cudaMemcpyHostToDevice));
-    if (!pairs.empty()) FDA_CUDA(cudaMemcpy(B.pairs.p, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice));
+    if (!tiles.empty())
+        FDA_CUDA(cudaMemcpy(B.tiles.p, tiles.data(), sizeof(tr_tile) * tiles.size(), cudaMemcpyHostToDevice));
+    B.mr = mr;
 }
 
 }  // namespace
@@ -179,18 +215,25 @@ void fda_build_batches(fda_handle *h)
 }
 
 template <typename R>
-void fda_run_batch(const tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst,
-                   cudaStream_t s)
+void fda_run_batch(tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst, int mr,
+                   int64_t sstride, int64_t dstride, cudaStream_t s)
 {
-    if (B.ntiles == 0) return;
-    if (B.np == 64)
-        k_btr<R, 64><<<B.ntiles, BT, 0, s>>>(B.tiles.as<tr_tile>(), B.pairs.as<int2>(), ops, Tout, Tin, src, dst);
+    if (B.npairs == 0) return;
+    ensure_tiles(B, mr);
+    const tr_tile *t = B.tiles.as<tr_tile>();
+    const int2 *pr = B.pairs.as<int2>();
+    if (B.tm == 64 && B.np == 64)
+        k_btr<R, 64, 64><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
+    else if (B.tm == 64)
+        k_btr<R, 64, 32><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
+    else if (B.np == 64)
+        k_btr<R, 32, 64><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
     else
-        k_btr<R, 32><<<B.ntiles, BT, 0, s>>>(B.tiles.as<tr_tile>(), B.pairs.as<int2>(), ops, Tout, Tin, src, dst);
+        k_btr<R, 32, 32><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
     FDA_CHECK_LAUNCH();
 }
 
-template void fda_run_batch<float>(const tr_batch &, const cx<float> *, int, int, const cx<float> *, cx<float> *,
-                                   cudaStream_t);
-template void fda_run_batch<double>(const tr_batch &, const cx<double> *, int, int, const cx<double> *,
-                                    cx<double> *, cudaStream_t);
+template void fda_run_batch<float>(tr_batch &, const cx<float> *, int, int, const cx<float> *, cx<float> *, int,
+                                   int64_t, int64_t, cudaStream_t);
+template void fda_run_batch<double>(tr_batch &, const cx<double> *, int, int, const cx<double> *, cx<double> *,
+                                    int, int64_t, int64_t, cudaStream_t);

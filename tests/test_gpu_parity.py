@@ -197,3 +197,20 @@ def test_conjugate_coupling_parity():
     assert _rel(y, oracle.matvec(v, f, k, x, alpha_sign=-1.0)) < 1e-4
     b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0])).cpu().numpy()
     assert _rel(b, oracle.rhs_plane_wave(v, f, k, [[0.0, 0.0, 1.0]], alpha_sign=-1.0)[0]) < 1e-13
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_right_hand_sides(precision):
+    """max_rhs = 12: 11 columns in one pass (S2M/translations/L2T over all of
+    them, the near field in groups of 8) equal the one-column applies, and
+    column 4 matches the oracle."""
+    v, f = icosphere(4)
+    k = 20.0
+    x = complex_normal(len(f), seed=21, nrhs=11)
+    P1 = _problem(v, f, k, precision=precision)
+    Pm = _problem(v, f, k, precision=precision, max_rhs=12)
+    ym = Pm.apply(_dev(x)).cpu().numpy()
+    for m in range(11):
+        y1 = P1.apply(_dev(x[m])).cpu().numpy()
+        assert _rel(ym[m], y1) < (1e-12 if precision == 0 else 1e-5)
+    assert _rel(ym[4], oracle.matvec(v, f, k, x[4])) < 1e-4
