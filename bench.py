@@ -216,6 +216,10 @@ def run_native(args):
         return acc / reps
 
     pt32 = pass_times(5)
+    # the same passes with the FP32 SIMT M2L, for comparison
+    F.fda_set_tensor_cores(P.h, 0)
+    pt32_simt = pass_times(3)
+    F.fda_set_tensor_cores(P.h, 1)
     F.fda_set_precision(P.h, F.FDA_PLAIN_FP64)
     P.apply(x, y)
     torch.cuda.synchronize()
@@ -274,11 +278,18 @@ def run_native(args):
     m2l_ms = pt32[2]
     achieved = m2l_flops / (m2l_ms * 1e-3) / 1e12
     near_gbs = st.bytes_near / 2 / (pt32[5] * 1e-3) / 1e9  # FP32 storage: 8 bytes per entry
-    roofline = {"kernel": "k_m2l<float> (M2L pass, all levels)", "bound": "alu", "achieved": achieved,
-                "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    roofline = {"kernel": "k_btr_tc<64> (M2L pass on tcgen05, all levels)", "bound": "tensor", "achieved": achieved,
+                "peak": bf16_peak, "unit": "TFLOP/s", "frac": achieved / bf16_peak,
                 "traffic": None,
-                "peak_source": "FP32 FMA rate: %d SMs x 128 lanes x 2 flops x %.0f MHz (%s clocks)" % (nsm, sm_mhz, src),
-                "algorithmic_flops_per_apply": m2l_flops}
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; %s)" % src,
+                "algorithmic_flops_per_apply": m2l_flops,
+                "executed_tensor_flops_per_apply": 3 * m2l_flops,
+                "note": "algorithmic = 8 real flops per complex multiply-add; the split-bf16 form executes 3x that",
+                "simt_fp32_m2l": {"ms": pt32_simt[2], "achieved": m2l_flops / (pt32_simt[2] * 1e-3) / 1e12,
+                                  "peak": fp32_peak_tflops,
+                                  "frac": m2l_flops / (pt32_simt[2] * 1e-3) / 1e12 / fp32_peak_tflops,
+                                  "peak_source": "FP32 FMA rate: %d SMs x 128 lanes x 2 flops x %.0f MHz" % (nsm, sm_mhz)}}
 
     solve = {}
     if not args.no_solve:
@@ -352,6 +363,7 @@ def run_native(args):
             "plain_fp64": {"matvec_per_s": 1e3 / plain_ms, "ms_per_matvec": plain_ms,
                            "pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt64.tolist()))},
             "chosen_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32.tolist())),
+            "chosen_simt_m2l_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32_simt.tolist())),
             "near_field_gbs": near_gbs,
             "batched_rhs": batched,
             "solve": solve,

@@ -74,6 +74,8 @@ typedef struct {
                               normal into the body; -1 the conjugate coupling */
     int max_rhs;           /* right-hand sides one fda_apply pass processes together (1..256, default 1);
                               densities and staging vectors are sized for it */
+    int tensor_cores;      /* chosen precision: run M2L on the tensor cores (split-bf16 tcgen05 GEMMs, FP32
+                              accumulation); 1 (default) or 0 (FP32 SIMT) */
     void *cuda_stream;     /* cudaStream_t, or NULL */
 } fda_config;
 
@@ -182,6 +184,10 @@ fda_status fda_solve(fda_handle *h, const fda_c128 *b, fda_c128 *x, int nrhs, do
  * FDA_CHOSEN_FP32 needs a handle created with precision = FDA_CHOSEN_FP32
  * (which also keeps the FP64 operators); otherwise FDA_ERR_STATE. */
 fda_status fda_set_precision(fda_handle *h, int precision);
+
+/* Switch the tensor-core M2L of the chosen precision on (1) or off (0) for
+ * later calls (needs a handle created with tensor_cores = 1 to turn on). */
+fda_status fda_set_tensor_cores(fda_handle *h, int on);
 
 /* Select the preconditioner used by later fda_solve calls: 0 none, 1 leaf
  * block-diagonal (needs a handle created with precond = 1, which builds the

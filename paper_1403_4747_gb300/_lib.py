@@ -25,7 +25,8 @@ class fda_config(ctypes.Structure):
                 ("hf_na", ctypes.c_int), ("leaf_max", ctypes.c_int), ("hf_wavelengths", ctypes.c_double),
                 ("rho_min", ctypes.c_double), ("precision", ctypes.c_int), ("mode", ctypes.c_int),
                 ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("precond", ctypes.c_int),
-                ("alpha_sign", ctypes.c_double), ("max_rhs", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("alpha_sign", ctypes.c_double), ("max_rhs", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class fda_info(ctypes.Structure):
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
     lib.fda_set_timing.argtypes = [H, cint]
     lib.fda_set_precision.argtypes = [H, cint]
     lib.fda_set_precond.argtypes = [H, cint]
+    lib.fda_set_tensor_cores.argtypes = [H, cint]
     lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
     lib.fda_last_error.argtypes = [H]
     lib.fda_last_error.restype = ctypes.c_char_p
@@ -79,7 +81,7 @@ def load(path: str = LIB_PATH):
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
                  "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
-                 "fda_set_precision", "fda_set_precond"):
+                 "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores"):
         getattr(lib, name).restype = cint
     _lib = lib
     return lib
@@ -166,6 +168,10 @@ def fda_set_precision(h, precision):
 
 def fda_set_precond(h, precond):
     _check(h, load().fda_set_precond(h, int(precond)))
+
+
+def fda_set_tensor_cores(h, on):
+    _check(h, load().fda_set_tensor_cores(h, 1 if on else 0))
 
 
 def fda_set_timing(h, enable=True):

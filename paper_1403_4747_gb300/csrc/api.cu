@@ -95,6 +95,7 @@ void fda_default_config(fda_config *c)
     c->precond = 0;
     c->alpha_sign = 1.0;
     c->max_rhs = 1;
+    c->tensor_cores = 1;
     c->cuda_stream = nullptr;
 }
 
@@ -108,7 +109,8 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
         c.p_hf < 3 || c.p_hf > 16 || c.hf_nr < 1 || c.hf_na < 8 || !(c.hf_wavelengths > 0) || !(c.rho_min >= 2.0) ||
         (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
         (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.maxit < 1 || c.precond < 0 ||
-        c.precond > 1 || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0) || c.max_rhs < 1 || c.max_rhs > 256)
+        c.precond > 1 || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0) || c.max_rhs < 1 || c.max_rhs > 256 ||
+        c.tensor_cores < 0 || c.tensor_cores > 1)
         return FDA_ERR_ARG;
     fda_handle *h = new (std::nothrow) fda_handle();
     if (!h) return FDA_ERR_OOM;
@@ -165,6 +167,7 @@ fda_status fda_precompute_translations(fda_handle *h)
             fda_near_convert_f32(h);
             fda_far_convert_f32(h);
             h->have32 = 1;
+            if (h->cfg.tensor_cores && h->lev_lo >= 0) fda_pack_tc(h);
         }
         fda_alloc_densities(h, want32);
         if (h->lev_lo >= 0) fda_build_batches(h);
@@ -303,6 +306,7 @@ fda_status fda_solve(fda_handle *h, const fda_c128 *b, fda_c128 *x, int nrhs, do
                                           reinterpret_cast<c64d *>(x) + (int64_t)m * h->N, tol, info);
             if (s != FDA_OK) last = s;
         }
+        if (fda_tc_error(h)) fda_fail(FDA_ERR_TIMEOUT, "a tensor-core translation gave up waiting on its copies");
     });
     return st != FDA_OK ? st : last;
 }
@@ -368,6 +372,8 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
             out->bytes_far = (int64_t)by;
         }
         out->device_bytes = (int64_t)handle_bytes(h);
+        for (int l = 0; l < FDA_MAX_LEVELS; ++l) out->device_bytes += (int64_t)h->tc[l].A.bytes;
+        if (fda_tc_error(h)) fda_fail(FDA_ERR_TIMEOUT, "a tensor-core translation gave up waiting on its copies");
         out->tree_s = h->tree_s;
         out->near_s = h->near_s;
         out->precompute_s = h->precompute_s;
@@ -386,6 +392,21 @@ fda_status fda_set_precision(fda_handle *h, int precision)
         return FDA_ERR_STATE;
     }
     h->cfg.precision = precision;
+    return FDA_OK;
+}
+
+fda_status fda_set_tensor_cores(fda_handle *h, int on)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (on != 0 && on != 1) {
+        h->err = "tensor_cores must be 0 or 1";
+        return FDA_ERR_ARG;
+    }
+    if (on && !h->have_tc) {
+        h->err = "tensor-core operators were not built (chosen precision with tensor_cores = 1)";
+        return FDA_ERR_STATE;
+    }
+    h->cfg.tensor_cores = on;
     return FDA_OK;
 }
 

@@ -222,9 +222,14 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
                          P.stride[l + 1], P.stride[l], s);
     mark(3);
     // M2L at every level: p~_target += K~ q~_source
-    for (int l = h->lev_lo; l < h->nlev; ++l)
-        fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
-                         P.stride[l], s);
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        if (sizeof(R) == 4 && h->have_tc && h->cfg.tensor_cores)
+            fda_run_batch_tc(h, l, reinterpret_cast<const c32f *>(P.q[l]), reinterpret_cast<c32f *>(P.p[l]), mr,
+                             P.stride[l]);
+        else
+            fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
+                             P.stride[l], s);
+    }
     mark(4);
     // L2L top-down: p~_child += L~ p~_parent
     for (int l = h->lev_lo; l + 1 < h->nlev; ++l)

@@ -139,6 +139,15 @@ struct tr_batch {
     std::vector<int> op_start;  // pairs of operator o: [op_start[o], op_start[o+1])
 };
 
+// tensor-core M2L operators of one level (bf16 hi/lo panels) and their tiles
+struct tc_ops {
+    dbuf A, tiles;
+    dbuf qb;                        // this level's densities split into bf16 hi/lo (per apply)
+    int nrt = 0, nkc = 0, nkh = 0;  // row tiles (64 complex rows), K stages (32 real), stages per half
+    int64_t op_bytes = 0;
+    int ntiles = 0, tiles_mr = 0, tiles_nc = 0;
+};
+
 template <typename T>
 struct far_ops {
     // per level (index = level)
@@ -215,6 +224,11 @@ struct fda_handle {
     far_ops<float> op32;
     int have32 = 0;
 
+    // tensor-core M2L (chosen precision)
+    tc_ops tc[FDA_MAX_LEVELS];
+    dbuf tc_err;
+    int have_tc = 0;
+
     // batched translations per level (M2L at l; M2M and L2L between l and l+1)
     tr_batch b_m2l[FDA_MAX_LEVELS], b_m2m[FDA_MAX_LEVELS], b_l2l[FDA_MAX_LEVELS];
 
@@ -258,6 +272,9 @@ void fda_precond_build(fda_handle *h);
 void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z);
 
 void fda_build_batches(fda_handle *h);
+void fda_pack_tc(fda_handle *h);
+void fda_run_batch_tc(fda_handle *h, int l, const c32f *src, c32f *dst, int mr, int64_t stride);
+int fda_tc_error(fda_handle *h);
 template <typename R>
 void fda_run_batch(tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst, int mr,
                    int64_t sstride, int64_t dstride, cudaStream_t s);

@@ -214,3 +214,23 @@ def test_batched_right_hand_sides(precision):
         y1 = P1.apply(_dev(x[m])).cpu().numpy()
         assert _rel(ym[m], y1) < (1e-12 if precision == 0 else 1e-5)
     assert _rel(ym[4], oracle.matvec(v, f, k, x[4])) < 1e-4
+
+
+@pytest.mark.parametrize("level,k,nrhs", [(4, 20.0, 1), (5, 25.0, 1), (4, 20.0, 5)])
+def test_tensor_core_m2l_matches_simt_and_oracle(level, k, nrhs):
+    """Chosen precision: the split-bf16 tcgen05 M2L agrees with the FP32
+    SIMT M2L to ~1e-5 and with the oracle to the FDA tolerance."""
+    from paper_1403_4747_gb300 import fda_set_tensor_cores
+    v, f = icosphere(level)
+    x = complex_normal(len(f), seed=31, nrhs=nrhs if nrhs > 1 else None)
+    P = _problem(v, f, k, precision=1, tensor_cores=1, max_rhs=max(1, nrhs))
+    xd = _dev(x)
+    y_tc = P.apply(xd).cpu().numpy()
+    fda_set_tensor_cores(P.h, 0)
+    y_simt = P.apply(xd).cpu().numpy()
+    assert _rel(y_tc, y_simt) < 2e-5
+    if nrhs == 1:
+        rows = np.random.default_rng(5).choice(len(f), 256, replace=False)
+        assert _rel(y_tc[rows], oracle.matvec(v, f, k, x, rows=rows)) < 1e-4
+    else:
+        assert _rel(y_tc[2], oracle.matvec(v, f, k, x[2])) < 1e-4
