@@ -179,9 +179,6 @@ def run_native(args):
     setup_s = time.perf_counter() - t0
     st = P.stats()
     nlev = st.n_levels
-    active = [l for l in range(nlev) if st.level_rank[l] > 0]
-    lev_lo = min(active) if active else nlev
-    launches_per_apply = 2 + 1 + 1 + 1 + 1 + (nlev - lev_lo) + 2 * max(0, nlev - 1 - lev_lo)
 
     x = torch.from_numpy(complex_normal(n, seed=1234)).cuda()
     y = torch.empty_like(x)
@@ -194,11 +191,13 @@ def run_native(args):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nl0 = F.fda_launch_count()
     e0.record(stream)
     for _ in range(args.steps):
         P.apply(x, y)
     e1.record(stream)
     torch.cuda.synchronize()
+    launches = F.fda_launch_count() - nl0
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -356,7 +355,7 @@ def run_native(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": {"value": ws * 1e3 / e2e_ms, "unit": "matvec/s", "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 16 * n},
-            "gpu_launches": launches_per_apply * args.steps,
+            "gpu_launches": launches,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -204,6 +204,11 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out);
 fda_status fda_set_timing(fda_handle *h, int enable);
 fda_status fda_get_pass_times(fda_handle *h, float out[6]);
 
+/* Number of CUDA kernels the library has launched since it was loaded, over
+ * all handles and threads (a monotonic counter; the difference around a
+ * region is the launches made inside it).  Never fails. */
+long long fda_launch_count(void);
+
 /* Message of the last failing call on this handle (never NULL). */
 const char *fda_last_error(const fda_handle *h);
 

@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.fda_set_precond.argtypes = [H, cint]
     lib.fda_set_tensor_cores.argtypes = [H, cint]
     lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
+    lib.fda_launch_count.argtypes = []
+    lib.fda_launch_count.restype = ctypes.c_longlong
     lib.fda_last_error.argtypes = [H]
     lib.fda_last_error.restype = ctypes.c_char_p
     lib.fda_destroy.argtypes = [H]
@@ -182,6 +184,11 @@ def fda_get_pass_times(h):
     arr = (ctypes.c_float * 6)()
     _check(h, load().fda_get_pass_times(h, arr))
     return list(arr)
+
+
+def fda_launch_count() -> int:
+    """Kernels launched by the library since it was loaded (all handles)."""
+    return int(load().fda_launch_count())
 
 
 def fda_last_error(h) -> str:

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <new>
 #include <vector>
@@ -15,6 +16,12 @@
 void fda_alloc_densities(fda_handle *h, int want32);
 void fda_near_convert_f32(fda_handle *h);
 void fda_far_convert_f32(fda_handle *h);
+
+static std::atomic<long long> g_launches{0};
+
+void fda_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" long long fda_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int fda_debug_sync()
 {
@@ -167,10 +174,10 @@ fda_status fda_precompute_translations(fda_handle *h)
             fda_near_convert_f32(h);
             fda_far_convert_f32(h);
             h->have32 = 1;
-            if (h->cfg.tensor_cores && h->lev_lo >= 0) fda_pack_tc(h);
         }
         fda_alloc_densities(h, want32);
         if (h->lev_lo >= 0) fda_build_batches(h);
+        if (want32 && h->cfg.tensor_cores && h->lev_lo >= 0) fda_pack_tc(h);
         h->xs.alloc(sizeof(c64d) * h->N * h->cfg.max_rhs);
         h->ys.alloc(sizeof(c64d) * h->N * h->cfg.max_rhs);
         FDA_CUDA(cudaStreamSynchronize(h->stream));
@@ -372,7 +379,9 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
             out->bytes_far = (int64_t)by;
         }
         out->device_bytes = (int64_t)handle_bytes(h);
-        for (int l = 0; l < FDA_MAX_LEVELS; ++l) out->device_bytes += (int64_t)h->tc[l].A.bytes;
+        for (int l = 0; l < FDA_MAX_LEVELS; ++l)
+            out->device_bytes += (int64_t)(h->tc_m2l[l].A.bytes + h->tc_m2m[l].A.bytes + h->tc_l2l[l].A.bytes +
+                                           h->qs[l].bytes + h->ps[l].bytes);
         if (fda_tc_error(h)) fda_fail(FDA_ERR_TIMEOUT, "a tensor-core translation gave up waiting on its copies");
         out->tree_s = h->tree_s;
         out->near_s = h->near_s;

@@ -216,25 +216,44 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
                                ops.St.template as<cx<R>>(), x, x64, N, mr);
     FDA_CHECK_LAUNCH();
     mark(2);
+    // tensor cores (chosen precision): every translation reads bf16 hi/lo
+    // splits of its source level, made once that level is complete
+    const bool tc = sizeof(R) == 4 && h->have_tc && h->cfg.tensor_cores;
+    auto c32 = [](auto *v) { return reinterpret_cast<c32f *>(v); };
     // M2M bottom-up: q~_parent += M~ q~_child
-    for (int l = h->nlev - 2; l >= h->lev_lo; --l)
-        fda_run_batch<R>(h->b_m2m[l], P.Mt[l], h->lev[l].T, h->lev[l + 1].T, P.q[l + 1], P.q[l], mr,
-                         P.stride[l + 1], P.stride[l], s);
+    for (int l = h->nlev - 2; l >= h->lev_lo; --l) {
+        if (tc) {
+            fda_split_tc(h, l + 1, c32(P.q[l + 1]), h->qs[l + 1], mr);
+            fda_run_tc(h, h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], P.stride[l + 1] / std::max(1, h->lev[l + 1].T),
+                       c32(P.q[l]), mr, P.stride[l]);
+        } else {
+            fda_run_batch<R>(h->b_m2m[l], P.Mt[l], h->lev[l].T, h->lev[l + 1].T, P.q[l + 1], P.q[l], mr,
+                             P.stride[l + 1], P.stride[l], s);
+        }
+    }
+    if (tc) fda_split_tc(h, h->lev_lo, c32(P.q[h->lev_lo]), h->qs[h->lev_lo], mr);
     mark(3);
     // M2L at every level: p~_target += K~ q~_source
     for (int l = h->lev_lo; l < h->nlev; ++l) {
-        if (sizeof(R) == 4 && h->have_tc && h->cfg.tensor_cores)
-            fda_run_batch_tc(h, l, reinterpret_cast<const c32f *>(P.q[l]), reinterpret_cast<c32f *>(P.p[l]), mr,
-                             P.stride[l]);
+        if (tc)
+            fda_run_tc(h, h->b_m2l[l], h->tc_m2l[l], h->qs[l], P.stride[l] / std::max(1, h->lev[l].T), c32(P.p[l]),
+                       mr, P.stride[l]);
         else
             fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
                              P.stride[l], s);
     }
     mark(4);
     // L2L top-down: p~_child += L~ p~_parent
-    for (int l = h->lev_lo; l + 1 < h->nlev; ++l)
-        fda_run_batch<R>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], mr,
-                         P.stride[l], P.stride[l + 1], s);
+    for (int l = h->lev_lo; l + 1 < h->nlev; ++l) {
+        if (tc) {
+            fda_split_tc(h, l, c32(P.p[l]), h->ps[l], mr);
+            fda_run_tc(h, h->b_l2l[l], h->tc_l2l[l], h->ps[l], P.stride[l] / std::max(1, h->lev[l].T),
+                       c32(P.p[l + 1]), mr, P.stride[l + 1]);
+        } else {
+            fda_run_batch<R>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], mr,
+                             P.stride[l], P.stride[l + 1], s);
+        }
+    }
     mark(5);
     k_l2t<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
                                h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(), ops.Tt.template as<cx<R>>(),

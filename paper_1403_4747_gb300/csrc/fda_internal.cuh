@@ -63,8 +63,11 @@ struct fda_error {
 // FDA_DEBUG_SYNC=1 in the environment makes every launch check synchronous,
 // so that a failing kernel is reported at its own launch site.
 int fda_debug_sync();
+// counts every kernel launch of the library (one check follows each launch)
+void fda_count_launch();
 #define FDA_CHECK_LAUNCH()                                                                    \
     do {                                                                                      \
+        fda_count_launch();                                                                   \
         FDA_CUDA(cudaGetLastError());                                                         \
         if (fda_debug_sync()) {                                                               \
             cudaError_t e2_ = cudaDeviceSynchronize();                                        \
@@ -139,11 +142,13 @@ struct tr_batch {
     std::vector<int> op_start;  // pairs of operator o: [op_start[o], op_start[o+1])
 };
 
-// tensor-core M2L operators of one level (bf16 hi/lo panels) and their tiles
+// tensor-core form of one translation batch: the operators as bf16 hi/lo
+// panels (64 complex output rows x 32 complex input columns per panel) and the
+// tiles cut for the current number of right-hand sides
 struct tc_ops {
     dbuf A, tiles;
-    dbuf qb;                        // this level's densities split into bf16 hi/lo (per apply)
-    int nrt = 0, nkc = 0, nkh = 0;  // row tiles (64 complex rows), K stages (32 real), stages per half
+    int Tout = 0, Tin = 0;
+    int nrt = 0, nkc = 0;     // row tiles (64 complex rows), K stages (32 complex columns)
     int64_t op_bytes = 0;
     int ntiles = 0, tiles_mr = 0, tiles_nc = 0;
 };
@@ -225,7 +230,8 @@ struct fda_handle {
     int have32 = 0;
 
     // tensor-core M2L (chosen precision)
-    tc_ops tc[FDA_MAX_LEVELS];
+    tc_ops tc_m2l[FDA_MAX_LEVELS], tc_m2m[FDA_MAX_LEVELS], tc_l2l[FDA_MAX_LEVELS];
+    dbuf qs[FDA_MAX_LEVELS], ps[FDA_MAX_LEVELS];  // FP32 densities split into bf16 hi/lo
     dbuf tc_err;
     int have_tc = 0;
 
@@ -273,7 +279,13 @@ void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z);
 
 void fda_build_batches(fda_handle *h);
 void fda_pack_tc(fda_handle *h);
-void fda_run_batch_tc(fda_handle *h, int l, const c32f *src, c32f *dst, int mr, int64_t stride);
+// split level l's FP32 densities (mr right-hand sides) into bf16 hi/lo
+void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr);
+// dst += op * src for every pair of batch B on the tensor cores; src is the
+// split densities of the source level (svstride vectors per right-hand
+// side), dst the FP32 densities of the target level (dstride elements each)
+void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t svstride, c32f *dst, int mr,
+                int64_t dstride);
 int fda_tc_error(fda_handle *h);
 template <typename R>
 void fda_run_batch(tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst, int mr,

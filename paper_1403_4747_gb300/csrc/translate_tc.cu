@@ -15,8 +15,9 @@
 // 8-row x 16-byte core matrices, LBO = 128 B between core matrices along K,
 // SBO = 512 B between 8-row groups (32 complex columns of K per stage).  The operator
 // panels are stored in HBM already in that layout (built once in setup) and
-// copied to shared memory with cp.async.bulk on an mbarrier; the gathered
-// densities are split and written by the CTA's threads.  Every mbarrier wait
+// copied to shared memory with cp.async.bulk on an mbarrier; the densities,
+// split into bf16 once per level, are gathered column by column with 16-byte
+// cp.async copies that arrive on the same mbarrier.  Every mbarrier wait
 // is bounded: on timeout the kernel records an error, waits (bounded) for its
 // own copies and MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -85,24 +86,28 @@ __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv
     }
 }
 
-// NC = columns per tile (pairs x right-hand sides), 64 or 128.  Two stage
-// buffers: the copies of stage s+1 run while the MMAs of stage s execute.
-template <int NC>
+// NC = columns per tile (pairs x right-hand sides): 32, 64 or 128.  ST stage
+// buffers: while the MMAs of stage s run, stages s+1 .. s+ST-1 are in flight.
+// Each stage's full barrier completes when the operator panel's bulk copy has
+// landed and every thread's cp.async copies of the density panels are done
+// (arrival count = threads + 1); its empty barrier completes when the MMAs
+// that read it are done (tcgen05.commit).
+template <int NC, int ST>
 __global__ void __launch_bounds__(TCT) k_btr_tc(const tc_tile *tiles, const int2 *pairs, const uint8_t *opsA,
-                                                 int64_t op_bytes, int nkc, int Tout, int Tp,
+                                                 int64_t op_bytes, int nkc, int Tout, int Tin,
                                                  const __nv_bfloat16 *qb, c32f *dst, int mr, int64_t svstride,
                                                  int64_t dstride, int *err)
 {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // 1 KB-aligned base inside the dynamic allocation (launched with 1 KB extra)
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    // 128-byte aligned base inside the dynamic allocation (launched with 128 extra)
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     constexpr int BB = NC * KC * 2;            // bytes of one B panel (Br or Bi, hi or lo)
     constexpr int STAGE = 2 * ABYTES + 4 * BB; // A hi, A lo, Br hi, Br lo, Bi hi, Bi lo
     float2 *sD = reinterpret_cast<float2 *>(smem);  // epilogue staging, 64 x NC (reuses the stages)
     __shared__ longlong2 pp[NC];               // (source vector, target offset)
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t full[2], empty[2];
-    __shared__ int abort_flag;
+    __shared__ __align__(8) uint64_t full[ST], empty[ST];
+    __shared__ int abort_flag, ncommit;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const tc_tile t = tiles[blockIdx.x];
 
@@ -112,12 +117,13 @@ __global__ void __launch_bounds__(TCT) k_btr_tc(const tc_tile *tiles, const int2
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])));
+        for (int b = 0; b < ST; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(TCT + 1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag = 0;
+        ncommit = 0;
     }
     for (int c = tid; c < NC; c += TCT) {
         longlong2 v = make_longlong2(-1, -1);
@@ -125,7 +131,7 @@ __global__ void __launch_bounds__(TCT) k_btr_tc(const tc_tile *tiles, const int2
             int vi = t.pair0 + c;
             int pi = vi / mr, m = vi - pi * mr;
             int2 q = pairs[pi];
-            v = make_longlong2(q.x / Tout + m * svstride, q.y + m * dstride);
+            v = make_longlong2(q.x / Tin + m * svstride, q.y + m * dstride);
         }
         pp[c] = v;
     }
@@ -134,43 +140,50 @@ __global__ void __launch_bounds__(TCT) k_btr_tc(const tc_tile *tiles, const int2
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;                    // D1 columns [0, NC)
     const uint32_t tmem2 = tmem_base + NC;              // D2 columns [NC, 2 NC)
+    const int Tp = nkc * KC;  // split vector length of the source level
     const uint8_t *gA = opsA + (int64_t)t.op * op_bytes + (int64_t)t.rt * nkc * 2 * ABYTES;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
-    // stage s into buffer b: operator panel by bulk copy, densities by 16-byte copies
+    // stage s into buffer b, fully asynchronous: operator panel by bulk copy,
+    // density panels by 16-byte cp.async (zero fill for empty columns)
     auto produce = [&](int s, int b) {
         uint8_t *st = smem + b * STAGE;
+        const uint32_t fb = smem_u32(&full[b]);
         if (tid == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[b])),
-                         "r"(2 * ABYTES));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * ABYTES));
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                              smem_u32(st)),
-                         "l"(gA + (int64_t)s * 2 * ABYTES), "r"(2 * ABYTES), "r"(smem_u32(&full[b])));
+                         "l"(gA + (int64_t)s * 2 * ABYTES), "r"(2 * ABYTES), "r"(fb));
         }
         // 16 copies per column: {Br, Bi} x {hi, lo} x 4 groups of 8 columns of K
         for (int e = tid; e < NC * 16; e += TCT) {
             int n = e >> 4, g = (e >> 2) & 3, part = e & 3;  // part: 0 Br hi, 1 Br lo, 2 Bi hi, 3 Bi lo
             long long v = pp[n].x;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (v >= 0)
-                val = *reinterpret_cast<const uint4 *>(qb + v * 4 * Tp + (part & 1) * 2 * Tp + (part >> 1) * Tp +
-                                                       s * KC + g * 8);
-            *reinterpret_cast<uint4 *>(st + 2 * ABYTES + part * BB + core_off(n, g * 8)) = val;
+            const __nv_bfloat16 *srcp = qb;
+            uint32_t bytes = 0;
+            if (v >= 0) {
+                srcp = qb + v * 4 * Tp + (part & 1) * 2 * Tp + (part >> 1) * Tp + s * KC + g * 8;
+                bytes = 16;
+            }
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             smem_u32(st + 2 * ABYTES + part * BB + core_off(n, g * 8))),
+                         "l"(srcp), "r"(bytes));
         }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fb));
     };
 
     bool ok = true;
-    produce(0, 0);
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    for (int s = 0; s < nkc; ++s) {
-        const int b = s & 1;
+    int nprod = 0;  // stages whose copies have been issued
+    for (; nprod < ST - 1 && nprod < nkc; ++nprod) produce(nprod, nprod);
+    int s = 0;
+    for (; s < nkc; ++s) {
+        const int b = s % ST, u = s / ST;
         if (tid == 0) {
-            if (!mbar_wait(smem_u32(&full[b]), (s >> 1) & 1)) {
+            if (!mbar_wait(smem_u32(&full[b]), u & 1)) {
                 atomicExch(err, 1);
                 abort_flag = 1;
-                mbar_wait(smem_u32(&full[b]), (s >> 1) & 1);  // last bounded wait for the copy in flight
             } else {
+                asm volatile("fence.proxy.async.shared::cta;");
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t aHi = smem_u32(smem + b * STAGE), aLo = aHi + ABYTES;
                 const uint32_t rHi = aHi + 2 * ABYTES, rLo = rHi + BB, iHi = rLo + BB, iLo = iHi + BB;
@@ -191,35 +204,35 @@ __global__ void __launch_bounds__(TCT) k_btr_tc(const tc_tile *tiles, const int2
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&empty[b])));
+                ncommit = s + 1;
             }
         }
-        if (s + 1 < nkc) {
-            const int b1 = (s + 1) & 1;
-            // buffer b1 was last read by the MMAs of stage s - 1
-            if (s >= 1 && !mbar_wait(smem_u32(&empty[b1]), ((s - 1) >> 1) & 1)) {
-                if (tid == 0) atomicExch(err, 2);
-                abort_flag = 1;
-            }
-            __syncthreads();
-            if (abort_flag) {
-                ok = false;
-                break;
-            }
-            produce(s + 1, b1);
-            asm volatile("fence.proxy.async.shared::cta;");
+        // the next stage to load reuses the buffer of stage s - 1
+        if (nprod < nkc && s >= 1 && !mbar_wait(smem_u32(&empty[nprod % ST]), ((s - 1) / ST) & 1)) {
+            if (tid == 0) atomicExch(err, 2);
+            abort_flag = 1;
         }
         __syncthreads();
         if (abort_flag) {
             ok = false;
             break;
         }
+        if (nprod < nkc) {
+            produce(nprod, nprod % ST);
+            ++nprod;
+        }
     }
-    // all MMAs done: the last commit covers every earlier one (the outcome is
-    // made uniform across the CTA through abort_flag)
-    if (ok && !mbar_wait(smem_u32(&empty[(nkc - 1) & 1]), ((nkc - 1) >> 1) & 1)) {
+    // drain: this thread's density copies; on abort, the operator copies of
+    // stages issued but not consumed; then the last commit (it covers every
+    // MMA issued before it)
+    asm volatile("cp.async.wait_all;");
+    if (!ok && tid == 0)
+        for (int s2 = s; s2 < nprod; ++s2) mbar_wait(smem_u32(&full[s2 % ST]), (s2 / ST) & 1);
+    __syncthreads();
+    const int nc = ncommit;
+    if (nc > 0 && !mbar_wait(smem_u32(&empty[(nc - 1) % ST]), ((nc - 1) / ST) & 1)) {
         if (tid == 0) atomicExch(err, 2);
         abort_flag = 1;
-        mbar_wait(smem_u32(&empty[(nkc - 1) & 1]), ((nkc - 1) >> 1) & 1);
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
@@ -312,23 +325,62 @@ __global__ void k_pack_tc(const c64d *ops, int nops, int Tout, int Tin, int nrt,
     }
 }
 
+struct tc_args {
+    const tc_tile *tiles;
+    const int2 *pairs;
+    const uint8_t *A;
+    int64_t op_bytes;
+    int nkc, Tout, Tin;
+    const __nv_bfloat16 *qb;
+    c32f *dst;
+    int mr;
+    int64_t svstride, dstride;
+    int *err;
+};
+
+template <int NC, int ST>
+void launch_tc(const tc_args &a, int ntiles, cudaStream_t s)
+{
+    const size_t stage = 2 * (size_t)ABYTES + 4 * (size_t)NC * KC * 2;
+    const size_t smem = 128 + std::max<size_t>(ST * stage, (size_t)64 * NC * sizeof(float2));
+    FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<NC, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_btr_tc<NC, ST><<<ntiles, TCT, smem, s>>>(a.tiles, a.pairs, a.A, a.op_bytes, a.nkc, a.Tout, a.Tin, a.qb, a.dst,
+                                               a.mr, a.svstride, a.dstride, a.err);
+}
+
+void pack_one(fda_handle *h, tc_ops &P, const tr_batch &B, const dbuf &ops64, int nops, int Tout, int Tin)
+{
+    if (B.npairs == 0 || nops == 0 || Tout == 0 || Tin == 0) return;
+    P.Tout = Tout;
+    P.Tin = Tin;
+    P.nrt = (Tout + 63) / 64;
+    P.nkc = (Tin + KC - 1) / KC;
+    P.op_bytes = (int64_t)P.nrt * P.nkc * 2 * ABYTES;
+    P.A.alloc((size_t)P.op_bytes * nops);
+    k_pack_tc<<<2048, 256, 0, h->stream>>>(ops64.as<c64d>(), nops, Tout, Tin, P.nrt, P.nkc, P.A.as<uint8_t>());
+    FDA_CHECK_LAUNCH();
+}
+
 }  // namespace
 
-// pack the M2L operators of every level for the tensor-core kernel
+// pack the M2L, M2M and L2L operators of every level for the tensor-core
+// kernel and size the split density buffers
 void fda_pack_tc(fda_handle *h)
 {
+    const int mrmax = std::max(1, h->cfg.max_rhs);
     for (int l = h->lev_lo; l >= 0 && l < h->nlev; ++l) {
-        level_info &L = h->lev[l];
-        tc_ops &P = h->tc[l];
-        if (L.n_ops == 0 || L.T == 0) continue;
-        P.nrt = (L.T + 63) / 64;
-        P.nkh = (L.T + KC - 1) / KC;
-        P.nkc = P.nkh;
-        P.op_bytes = (int64_t)P.nrt * P.nkc * 2 * ABYTES;
-        P.A.alloc((size_t)P.op_bytes * L.n_ops);
-        k_pack_tc<<<2048, 256, 0, h->stream>>>(h->op64.Kt[l].as<c64d>(), L.n_ops, L.T, L.T, P.nrt, P.nkc,
-                                              P.A.as<uint8_t>());
-        FDA_CHECK_LAUNCH();
+        const level_info &L = h->lev[l];
+        if (L.T == 0) continue;
+        pack_one(h, h->tc_m2l[l], h->b_m2l[l], h->op64.Kt[l], L.n_ops, L.T, L.T);
+        if (l + 1 < h->nlev && h->lev[l + 1].T > 0) {
+            const int Tc = h->lev[l + 1].T;
+            pack_one(h, h->tc_m2m[l], h->b_m2m[l], h->op64.Mt[l], 8 * L.ncones, L.T, Tc);
+            pack_one(h, h->tc_l2l[l], h->b_l2l[l], h->op64.Lt[l], 8 * L.ncones, Tc, L.T);
+        }
+        const size_t nvec = (size_t)L.nbox * L.ncones * mrmax;
+        const size_t Tp = (size_t)((L.T + KC - 1) / KC) * KC;
+        h->qs[l].alloc(sizeof(__nv_bfloat16) * nvec * 4 * Tp);
+        h->ps[l].alloc(sizeof(__nv_bfloat16) * nvec * 4 * Tp);
     }
     h->tc_err.alloc(sizeof(int));
     FDA_CUDA(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), h->stream));
@@ -336,26 +388,28 @@ void fda_pack_tc(fda_handle *h)
     h->have_tc = 1;
 }
 
-// run the M2L batch of level l on the tensor cores (chosen precision)
-void fda_run_batch_tc(fda_handle *h, int l, const c32f *src, c32f *dst, int mr, int64_t stride)
+void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr)
 {
-    tr_batch &B = h->b_m2l[l];
-    tc_ops &P = h->tc[l];
     const level_info &L = h->lev[l];
-    if (B.npairs == 0) return;
-    const int nops = (int)B.op_start.size() - 1;
-    const int NC = (double)B.npairs * mr / std::max(1, nops) >= 96.0 ? 128 : 64;
-    const int Tp = P.nkh * KC;
-    // split this level's densities (all right-hand sides) into bf16 hi/lo
+    if (L.T == 0 || !out.p) return;
+    const int Tp = (L.T + KC - 1) / KC * KC;
     const int64_t nvec = (int64_t)L.nbox * L.ncones * mr;
-    const size_t need = sizeof(__nv_bfloat16) * (size_t)nvec * 4 * Tp;
-    if (P.qb.bytes < need) P.qb.alloc(need);
-    k_split_density<<<1024, 256, 0, h->stream>>>(src, nvec, L.T, Tp, P.qb.as<__nv_bfloat16>());
+    if (out.bytes < sizeof(__nv_bfloat16) * (size_t)nvec * 4 * Tp) fda_fail(FDA_ERR_STATE, "split buffer too small");
+    k_split_density<<<1024, 256, 0, h->stream>>>(src, nvec, L.T, Tp, out.as<__nv_bfloat16>());
     FDA_CHECK_LAUNCH();
-    if (P.tiles_nc != NC) P.tiles_mr = 0;
-    if (P.tiles_mr != mr) {
+}
+
+void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t svstride, c32f *dst, int mr,
+                int64_t dstride)
+{
+    if (B.npairs == 0) return;
+    if (!P.A.p) fda_fail(FDA_ERR_STATE, "tensor-core operators missing for a nonempty translation batch");
+    const int nops = (int)B.op_start.size() - 1;
+    const double avg_cols = (double)B.npairs * mr / std::max(1, nops);
+    // narrow tiles where an operator has few pairs (less padding, more CTAs per SM)
+    const int NC = avg_cols < 48.0 ? 32 : 64;
+    if (P.tiles_nc != NC || P.tiles_mr != mr) {
         std::vector<tc_tile> tiles;
-        const int nops = (int)B.op_start.size() - 1;
         for (int o = 0; o < nops; ++o) {
             int a = B.op_start[o] * mr, b = B.op_start[o + 1] * mr;
             for (int p0 = a; p0 < b; p0 += NC)
@@ -369,21 +423,10 @@ void fda_run_batch_tc(fda_handle *h, int l, const c32f *src, c32f *dst, int mr, 
         P.tiles_nc = NC;
     }
     if (P.ntiles == 0) return;
-    const size_t stage = 2 * (size_t)ABYTES + 4 * (size_t)NC * KC * 2;
-    const size_t smem = 1024 + std::max<size_t>(2 * stage, (size_t)64 * NC * sizeof(float2));
-    const int64_t svstride = (int64_t)L.nbox * L.ncones;  // vectors per right-hand side
-    if (NC == 64) {
-        FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_btr_tc<64><<<P.ntiles, TCT, smem, h->stream>>>(P.tiles.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(),
-                                                          P.op_bytes, P.nkc, L.T, Tp, P.qb.as<__nv_bfloat16>(), dst,
-                                                          mr, svstride, stride, h->tc_err.as<int>());
-    } else {
-        FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_btr_tc<128><<<P.ntiles, TCT, smem, h->stream>>>(P.tiles.as<tc_tile>(), B.pairs.as<int2>(),
-                                                           P.A.as<uint8_t>(), P.op_bytes, P.nkc, L.T, Tp,
-                                                           P.qb.as<__nv_bfloat16>(), dst, mr, svstride, stride,
-                                                           h->tc_err.as<int>());
-    }
+    tc_args a{P.tiles.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.Tout, P.Tin,
+              src.as<__nv_bfloat16>(), dst, mr, svstride, dstride, h->tc_err.as<int>()};
+    if (NC == 32) launch_tc<32, 2>(a, P.ntiles, h->stream);
+    else launch_tc<64, 2>(a, P.ntiles, h->stream);
     FDA_CHECK_LAUNCH();
 }
 
