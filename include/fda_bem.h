@@ -204,6 +204,19 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out);
 fda_status fda_set_timing(fda_handle *h, int enable);
 fda_status fda_get_pass_times(fda_handle *h, float out[6]);
 
+/* Symmetry table of the cone partition of a high-frequency level with
+ * nc x nc cells per cube face (6 nc^2 cones, Sec. 3.1; cone index =
+ * (2 axis + [sign > 0]) nc^2 + a nc + b, a and b the cell along the two other
+ * axes in increasing order).  For every cone u: rep[u] = its representative
+ * cone on the +z face and g[9u..9u+8] = the signed axis permutation
+ * (row-major, entries -1/0/1) with g_u (centre of rep[u]) = centre of u and
+ * g of the opposite cone = -g_u.  The library gives cone u the frame
+ * g_u R_rep(u), so M2L offsets related by these maps (the rotation
+ * invariance of Sec. 4.1.1) share one operator.  Host only (no GPU needed);
+ * rep holds 6 nc^2 ints and g 54 nc^2 ints, both caller-owned.  Returns
+ * FDA_ERR_ARG for nc outside [1, 64] or NULL pointers. */
+int fda_cone_symmetry_table(int nc, int *rep, int *g);
+
 /* Number of CUDA kernels the library has launched since it was loaded, over
  * all handles and threads (a monotonic counter; the difference around a
  * region is the launches made inside it).  Never fails. */

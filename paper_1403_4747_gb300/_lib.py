@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.fda_set_precond.argtypes = [H, cint]
     lib.fda_set_tensor_cores.argtypes = [H, cint]
     lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
+    lib.fda_cone_symmetry_table.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.fda_cone_symmetry_table.restype = ctypes.c_int
     lib.fda_launch_count.argtypes = []
     lib.fda_launch_count.restype = ctypes.c_longlong
     lib.fda_last_error.argtypes = [H]
@@ -184,6 +186,17 @@ def fda_get_pass_times(h):
     arr = (ctypes.c_float * 6)()
     _check(h, load().fda_get_pass_times(h, arr))
     return list(arr)
+
+
+def fda_cone_symmetry_table(nc: int):
+    """(rep, g) of the cone partition with nc x nc cells per face: rep[u] is
+    cone u's representative and g[u] the 3x3 signed permutation mapping it to u."""
+    import numpy as np
+    n = 6 * nc * nc
+    rep = np.zeros(n, dtype=np.int32)
+    g = np.zeros((n, 3, 3), dtype=np.int32)
+    _check(None, load().fda_cone_symmetry_table(nc, rep.ctypes.data, g.ctypes.data))
+    return rep, g
 
 
 def fda_launch_count() -> int:

@@ -21,6 +21,22 @@ static std::atomic<long long> g_launches{0};
 
 void fda_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void fda_cone_symmetry(int nc, std::vector<int> &rep, std::vector<int> &g);
+
+extern "C" int fda_cone_symmetry_table(int nc, int *rep, int *g)
+{
+    if (nc < 1 || nc > 64 || !rep || !g) return FDA_ERR_ARG;
+    try {
+        std::vector<int> r, m;
+        fda_cone_symmetry(nc, r, m);
+        std::copy(r.begin(), r.end(), rep);
+        std::copy(m.begin(), m.end(), g);
+    } catch (...) {
+        return FDA_ERR_NUMERIC;
+    }
+    return FDA_OK;
+}
+
 extern "C" long long fda_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int fda_debug_sync()

@@ -50,43 +50,77 @@ __device__ inline cx<R> ldx(const void *x, int64_t i, int x64)
 // right-hand side).
 constexpr int NRG = 8;
 
+constexpr int NRW = 2;  // rows per warp in the near-field product
+
 template <typename R, int NR>
-__global__ void k_near_apply(const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend,
-                             const int64_t *colptr, const int64_t *rptr, const int32_t *rb, const int32_t *re,
-                             const int64_t *off, const cx<R> *A, const void *x, int x64, int64_t xstr, int mr,
-                             c64d *y, int64_t ldy)
+__global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, const int32_t *bbeg,
+                                                   const int32_t *bend, const int64_t *colptr, const int32_t *cols,
+                                                   const int64_t *off, const cx<R> *A, const void *x, int x64,
+                                                   int64_t xstr, int mr, c64d *y, int64_t ldy)
 {
+    // Each warp takes NRW rows of a leaf (rows r and r + 8 of its group of
+    // 8 NRW); the leaf's columns (its flattened near ranges, shared by all
+    // its rows) are streamed four 32-wide slices at a time, the last ones
+    // predicated, so every lane keeps 4 NRW independent matrix loads in
+    // flight and each column index and x value serves NRW rows.
     int li = blockIdx.x;
     int B = leaf_box[li];
     int i0 = bbeg[B], nB = bend[B] - i0;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int r = blockIdx.y * (AT / 32) + warp;
-    if (r >= nB) return;
+    const int r0 = blockIdx.y * (AT / 32) * NRW + warp;
+    if (r0 >= nB) return;
     const int m0 = blockIdx.z * NR;
     const int nm = min(NR, mr - m0);
-    int64_t nc = colptr[li + 1] - colptr[li];
-    const cx<R> *row = A + off[li] + (int64_t)r * nc;
-    cx<R> acc[NR];
-    int64_t coff = 0;
-    for (int64_t g = rptr[li]; g < rptr[li + 1]; ++g) {
-        int b = rb[g], len = re[g] - b;
-        for (int c = lane; c < len; c += 32) {
-            cx<R> a = row[coff + c];
+    const int64_t c0 = colptr[li];
+    const int nc = (int)(colptr[li + 1] - c0);
+    const int32_t *cl = cols + c0;
+    const cx<R> *rowp[NRW];
+    bool rv[NRW];
+#pragma unroll
+    for (int w = 0; w < NRW; ++w) {
+        const int r = r0 + w * (AT / 32);
+        rv[w] = r < nB;
+        rowp[w] = A + off[li] + (int64_t)(rv[w] ? r : r0) * nc;
+    }
+    cx<R> acc[NRW][NR];
+    for (int cb = 0; cb < nc; cb += 128) {
+        cx<R> a[NRW][4];
+        int j[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int cc = cb + 32 * u + lane;
+            j[u] = 0;
+            if (cc < nc) {
+                j[u] = __ldg(cl + cc);
+#pragma unroll
+                for (int w = 0; w < NRW; ++w)
+                    if (rv[w]) a[w][u] = rowp[w][cc];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int mm = 0; mm < NR; ++mm)
-                if (mm < nm) cfma(acc[mm], a, ldx<R>(x, (int64_t)(m0 + mm) * xstr + b + c, x64));
-        }
-        coff += len;
+                if (mm < nm) {
+                    const cx<R> xv = ldx<R>(x, (int64_t)(m0 + mm) * xstr + j[u], x64);
+#pragma unroll
+                    for (int w = 0; w < NRW; ++w) cfma(acc[w][mm], a[w][u], xv);
+                }
     }
 #pragma unroll
-    for (int mm = 0; mm < NR; ++mm) {
-        if (mm >= nm) break;  // uniform across the warp
-        cx<R> v = acc[mm];
-        for (int o = 16; o > 0; o >>= 1) {
-            v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
-            v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+    for (int w = 0; w < NRW; ++w) {
+        if (!rv[w]) break;  // uniform across the warp
+        const int r = r0 + w * (AT / 32);
+#pragma unroll
+        for (int mm = 0; mm < NR; ++mm) {
+            if (mm >= nm) break;  // uniform across the warp
+            cx<R> v = acc[w][mm];
+            for (int o = 16; o > 0; o >>= 1) {
+                v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+                v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+            }
+            if (lane == 0) y[(int64_t)(m0 + mm) * ldy + i0 + r] = c64d((double)v.re, (double)v.im);
         }
-        if (lane == 0) y[(int64_t)(m0 + mm) * ldy + i0 + r] = c64d((double)v.re, (double)v.im);
     }
 }
 
@@ -184,18 +218,16 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     mark(0);
     const int max_rows = h->max_leaf_rows;
     if (mr == 1) {
-        dim3 gn(NL, (max_rows + AT / 32 - 1) / (AT / 32), 1);
+        dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
         k_near_apply<R, 1><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                              h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
-                                             h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(),
-                                             h->nr_end.as<int32_t>(), h->nf_off.as<int64_t>(),
+                                             h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
                                              ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
     } else {
-        dim3 gn(NL, (max_rows + AT / 32 - 1) / (AT / 32), (mr + NRG - 1) / NRG);
+        dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), (mr + NRG - 1) / NRG);
         k_near_apply<R, NRG><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
-                                               h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(),
-                                               h->nr_end.as<int32_t>(), h->nf_off.as<int64_t>(),
+                                               h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
                                                ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
     }
     FDA_CHECK_LAUNCH();

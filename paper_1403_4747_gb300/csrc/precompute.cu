@@ -14,9 +14,11 @@
 //       end) with hf_na directions each (Fibonacci points on the cap).  Theta
 //       = the largest angle between a face cell's centre direction and its
 //       corners plus 1.3 asin((sqrt 3/2)/rho) for the extent of the target
-//       boxes.  Cone u uses the same points rotated by R_u (+z -> centre
-//       direction of u), so one SVD serves every cone of a level (the
-//       rotation invariance of Sec. 4.1.1).
+//       boxes.  Cone u uses the same points transformed by the orthogonal
+//       R_u (+z -> centre direction of u; R_u = g_u R_rep, a signed axis
+//       permutation of a representative cone's frame), so one SVD serves
+//       every cone of a level (the rotation invariance of Sec. 4.1.1), and
+//       M2L offsets related by the g_u share one operator.
 //   The downward sets are the upward sets with roles swapped (check on the
 //   equivalent set, equivalent on the check set), so G_dn = G_up^T and one
 //   truncated SVD G_up ~ U S V^H (Eq. svdg, epsg: sigma_i >= eps sigma_0)
@@ -43,6 +45,7 @@
 namespace cg = cooperative_groups;
 
 int fda_cone_index_host(double dx, double dy, double dz, int nc);
+void fda_cone_symmetry(int nc, std::vector<int> &rep, std::vector<int> &g);
 
 namespace {
 
@@ -592,10 +595,18 @@ void fda_far_precompute(fda_handle *h)
             double delta = 1.3 * asin(std::min(1.0, (sqrt(3.0) / 2.0) / L.rho));
             double theta = std::min(0.999 * FDA_PI / 2.0, cone_halfangle_host(L.nc) + delta);
             P[l].chk = cone_points(theta, rmin, rmax, cfg.hf_nr, cfg.hf_na);
+            // R_u = g_u R_rep(u): a rotation taking +z to the representative
+            // cone's centre, mapped to cone u by a signed axis permutation
+            std::vector<int> crep, cg;
+            fda_cone_symmetry(L.nc, crep, cg);
             for (int u = 0; u < L.ncones; ++u) {
-                double d[3], R[9];
-                cone_dir_host(u, L.nc, d);
-                rot_to_host(d, R);
+                double d[3], R0[9], R[9];
+                cone_dir_host(crep[u], L.nc, d);
+                rot_to_host(d, R0);
+                const int *g = &cg[9 * (size_t)u];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        R[3 * i + j] = g[3 * i] * R0[j] + g[3 * i + 1] * R0[3 + j] + g[3 * i + 2] * R0[6 + j];
                 P[l].rot.insert(P[l].rot.end(), R, R + 9);
             }
             h->rot[l].alloc(sizeof(double) * P[l].rot.size());

@@ -2,18 +2,22 @@
 // precision: the M2L tiles of translate.cu as bf16 tensor-core GEMMs.
 //
 // A complex tile C (64 rows x NC columns) += A (64 x Tin) B (Tin x NC) is
-// computed from two real GEMMs with the stacked operator [Ar; Ai] (128 rows,
-// M = 128 per tcgen05.mma, each operator element stored once):
-//     D1 = [Ar; Ai] Br,  D2 = [Ar; Ai] Bi,
-//     Cr = D1_top - D2_bottom,  Ci = D2_top + D1_bottom,
-// with D1 and D2 in two tensor-memory accumulators.  Each FP32 value is split
-// into two bf16 numbers, x = x_hi + x_lo, and every product is taken as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in tensor memory,
-// which keeps about 16 significant bits per operand.
+// computed with the stacked operator [Ar; Ai] (128 rows, M = 128 per
+// tcgen05.mma, each operator element stored once) against the column panels
+// [Br Bi] (2 NC columns):
+//     [D1 D2] = [Ar; Ai] [Br Bi],
+//     Cr = D1_top - D2_bottom,  Ci = D2_top + D1_bottom.
+// Each FP32 value is split into two bf16 numbers, x = x_hi + x_lo, and the
+// products A_hi B_hi + A_hi B_lo + A_lo B_hi are taken with FP32 accumulation
+// in tensor memory (about 16 significant bits per operand) as two MMAs per
+// 16 of K: A_hi [B_hi B_lo] (N = 4 NC) and A_lo B_hi (N = 2 NC, added to the
+// first half); the epilogue adds the B_lo half to the B_hi half.
 //
 // Operands in shared memory use the tcgen05 K-major layout without swizzle:
 // 8-row x 16-byte core matrices, LBO = 128 B between core matrices along K,
-// SBO = 512 B between 8-row groups (32 complex columns of K per stage).  The operator
+// SBO = 512 B between 8-row groups (32 complex columns of K per stage); the
+// B panels Br hi, Bi hi, Br lo, Bi lo follow one another, so [Br Bi] hi and
+// the whole [Br Bi hi | Br Bi lo] are single operands of 2 NC and 4 NC rows.  The operator
 // panels are stored in HBM already in that layout (built once in setup) and
 // copied to shared memory with cp.async.bulk on an mbarrier; the densities,
 // split into bf16 once per level, are gathered column by column with 16-byte
@@ -23,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "fda_internal.cuh"
@@ -31,7 +36,6 @@ namespace {
 
 constexpr int KC = 32;            // real K per stage (two MMA k-steps of 16)
 constexpr int ABYTES = 128 * KC * 2;  // one bf16 operand panel stage (hi or lo): 8 KB
-constexpr int TCT = 128;          // threads (4 warps = the 128 TMEM lanes)
 constexpr long long SPIN = 20000000;  // bounded mbarrier polls
 
 struct tc_tile {
@@ -64,231 +68,321 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity)
 // byte offset of element (row, k) inside a [rows x 32] K-major bf16 stage
 __device__ inline int core_off(int row, int k) { return (row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2; }
 
-// Densities of one level split once per apply into bf16 hi/lo: vector v
-// (box, cone, right-hand side) -> [hi: Re(0..Tp) Im(0..Tp)][lo: same],
-// 4 Tp bf16 per vector, Tp = T rounded up to 32, zero beyond T.
+// Densities of one level split once per apply into bf16 hi/lo, laid out
+// for the gather: vector v (box, cone, right-hand side) holds per K chunk of
+// 32 (stage s) the four panels Re hi, Im hi, Re lo, Im lo of 32 values each,
+// 256 contiguous bytes per (vector, stage): 4 Tp bf16 per vector, Tp = T
+// rounded up to 32, zero beyond T.
 __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv_bfloat16 *out)
 {
-    const int64_t total = nvec * 2 * Tp;
+    const int64_t total = nvec * 2 * Tp;  // (vector, Re/Im, j)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t v = e / (2 * Tp);
         int r = (int)(e % (2 * Tp));
-        int j = r < Tp ? r : r - Tp;
+        int im = r / Tp, j = r - im * Tp;
         float x = 0.0f;
         if (j < T) {
             c32f c = q[v * T + j];
-            x = r < Tp ? c.re : c.im;
+            x = im ? c.im : c.re;
         }
         __nv_bfloat16 hi = __float2bfloat16_rn(x);
         __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-        out[v * 4 * Tp + r] = hi;
-        out[v * 4 * Tp + 2 * Tp + r] = lo;
+        __nv_bfloat16 *o = out + v * 4 * Tp + (j / KC) * 4 * KC + im * KC + (j % KC);
+        o[0] = hi;
+        o[2 * KC] = lo;
     }
 }
 
-// NC = columns per tile (pairs x right-hand sides): 32, 64 or 128.  ST stage
-// buffers: while the MMAs of stage s run, stages s+1 .. s+ST-1 are in flight.
-// Each stage's full barrier completes when the operator panel's bulk copy has
-// landed and every thread's cp.async copies of the density panels are done
-// (arrival count = threads + 1); its empty barrier completes when the MMAs
-// that read it are done (tcgen05.commit).
+// Persistent, warp-specialised form.  CTA c takes tiles c, c + grid,
+// c + 2 grid, ...; its warps split the work of every tile:
+//   warps 5-7 (producers): load stage g of the CTA into ring buffer g % ST:
+//       the operator panel by one bulk copy, the tile's density columns (256
+//       contiguous bytes each) by 16-byte cp.async copies (zero fill for
+//       columns with no pair); full[b] completes when all of them have landed
+//       (arrival count = 96 producer threads + 1 for the byte count);
+//   warp 4 (MMA): one thread issues the stage's MMAs into the tile's
+//       accumulator slot and commits them to empty[b] (frees the buffer) and,
+//       after the tile's last stage, to accf[slot];
+//   warps 0-3 (epilogue, one warp per TMEM lane quarter): read the slot,
+//       combine real and imaginary parts and add the result to the targets,
+//       then arrive on acce[slot] (count 128) so the slot can be reused.
+// Two accumulator slots (4 NC TMEM columns each) let the epilogue of tile j
+// overlap the MMAs of tile j + 1.  Every wait is bounded and also gives up
+// once another role has recorded an error; the CTA then waits (bounded) for
+// its copies and MMAs in flight, frees its tensor memory and returns.
+constexpr int EPC = 16;          // epilogue chunk: accumulator columns staged per pass
+constexpr int WS_THREADS = 256;  // 8 warps
+constexpr int NPROD = 96;        // producer threads (warps 5-7)
+
+__device__ inline bool mbar_wait_ab(uint32_t bar, uint32_t parity, const volatile int *abort)
+{
+    uint32_t done = 0;
+    for (long long it = 0; it < SPIN; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity));
+        if (done) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    return false;
+}
+
+// 16 consecutive accumulator columns at each of two TMEM addresses (this
+// warp's 32 lanes); the wait is inside the same statement, so the results
+// cannot be used before the loads have completed
+__device__ inline void tmem_ld16x2(uint32_t addr_a, uint32_t addr_b, uint32_t (&a)[16], uint32_t (&b)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+                   "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]),
+                   "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
+                   "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+                 : "r"(addr_a), "r"(addr_b));
+}
+
+// true on every thread of named barrier `id` (n threads) if pred holds on any
+// of them: a group's decision to stop is taken together, so no thread is
+// left waiting at a later barrier of the group
+__device__ inline bool bar_any(int id, int n, bool pred)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, %3, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)pred), "r"(id), "r"(n));
+    return r != 0;
+}
+
 template <int NC, int ST>
-__global__ void __launch_bounds__(TCT) k_btr_tc(const tc_tile *tiles, const int2 *pairs, const uint8_t *opsA,
-                                                 int64_t op_bytes, int nkc, int Tout, int Tin,
-                                                 const __nv_bfloat16 *qb, c32f *dst, int mr, int64_t svstride,
-                                                 int64_t dstride, int *err)
+__global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int ntiles, const int2 *pairs,
+                                                        const uint8_t *opsA, int64_t op_bytes, int nkc, int Tout,
+                                                        int Tin, const __nv_bfloat16 *qb, c32f *dst, int mr,
+                                                        int64_t svstride, int64_t dstride, int *err)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     // 128-byte aligned base inside the dynamic allocation (launched with 128 extra)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     constexpr int BB = NC * KC * 2;            // bytes of one B panel (Br or Bi, hi or lo)
-    constexpr int STAGE = 2 * ABYTES + 4 * BB; // A hi, A lo, Br hi, Br lo, Bi hi, Bi lo
-    float2 *sD = reinterpret_cast<float2 *>(smem);  // epilogue staging, 64 x NC (reuses the stages)
-    __shared__ longlong2 pp[NC];               // (source vector, target offset)
+    constexpr int STAGE = 2 * ABYTES + 4 * BB; // A hi, A lo, Br hi, Bi hi, Br lo, Bi lo
+    float2 *stg = reinterpret_cast<float2 *>(smem + ST * STAGE);  // epilogue staging [EPC][128 lanes]
+    __shared__ long long srcv[NC];             // producers: source vector per column of the current tile
+    __shared__ long long tgt[NC];              // epilogue: target offset per column of the current tile
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t full[ST], empty[ST];
-    __shared__ int abort_flag, ncommit;
+    __shared__ __align__(8) uint64_t full[ST], empty[ST], accf[2], acce[2];
+    __shared__ int abort_flag, n_issued, n_consumed, n_commit;
+    volatile int *abort_v = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const tc_tile t = tiles[blockIdx.x];
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int Tp = nkc * KC;                   // split vector length of the source level
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(2 * NC));
+                     "r"(8 * NC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         for (int b = 0; b < ST; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(TCT + 1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(NPROD + 1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[b])), "r"(128));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag = 0;
-        ncommit = 0;
-    }
-    for (int c = tid; c < NC; c += TCT) {
-        longlong2 v = make_longlong2(-1, -1);
-        if (c < t.npair) {
-            int vi = t.pair0 + c;
-            int pi = vi / mr, m = vi - pi * mr;
-            int2 q = pairs[pi];
-            v = make_longlong2(q.x / Tin + m * svstride, q.y + m * dstride);
-        }
-        pp[c] = v;
+        n_issued = n_consumed = n_commit = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = tmem_base;                    // D1 columns [0, NC)
-    const uint32_t tmem2 = tmem_base + NC;              // D2 columns [NC, 2 NC)
-    const int Tp = nkc * KC;  // split vector length of the source level
-    const uint8_t *gA = opsA + (int64_t)t.op * op_bytes + (int64_t)t.rt * nkc * 2 * ABYTES;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t tmem = tmem_base;
 
-    // stage s into buffer b, fully asynchronous: operator panel by bulk copy,
-    // density panels by 16-byte cp.async (zero fill for empty columns)
-    auto produce = [&](int s, int b) {
-        uint8_t *st = smem + b * STAGE;
-        const uint32_t fb = smem_u32(&full[b]);
-        if (tid == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * ABYTES));
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                             smem_u32(st)),
-                         "l"(gA + (int64_t)s * 2 * ABYTES), "r"(2 * ABYTES), "r"(fb));
-        }
-        // 16 copies per column: {Br, Bi} x {hi, lo} x 4 groups of 8 columns of K
-        for (int e = tid; e < NC * 16; e += TCT) {
-            int n = e >> 4, g = (e >> 2) & 3, part = e & 3;  // part: 0 Br hi, 1 Br lo, 2 Bi hi, 3 Bi lo
-            long long v = pp[n].x;
-            const __nv_bfloat16 *srcp = qb;
-            uint32_t bytes = 0;
-            if (v >= 0) {
-                srcp = qb + v * 4 * Tp + (part & 1) * 2 * Tp + (part >> 1) * Tp + s * KC + g * 8;
-                bytes = 16;
+    if (warp >= 5) {
+        // ---------------- producers
+        const int tp = tid - 160;
+        int g = 0;
+        bool ok = true;
+        for (int j = 0; j < my_tiles && ok; ++j) {
+            const tc_tile t = tiles[blockIdx.x + (int64_t)j * gridDim.x];
+            asm volatile("bar.sync 1, %0;" ::"r"(NPROD));  // everyone is done with the previous srcv
+            for (int c = tp; c < NC; c += NPROD) {
+                long long v = -1;
+                if (c < t.npair) {
+                    int vi = t.pair0 + c;
+                    int pi = vi / mr, m = vi - pi * mr;
+                    v = pairs[pi].x / Tin + m * svstride;
+                }
+                srcv[c] = v;
             }
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
-                             smem_u32(st + 2 * ABYTES + part * BB + core_off(n, g * 8))),
-                         "l"(srcp), "r"(bytes));
+            asm volatile("bar.sync 1, %0;" ::"r"(NPROD));
+            const uint8_t *gA = opsA + (int64_t)t.op * op_bytes + (int64_t)t.rt * nkc * 2 * ABYTES;
+            for (int s = 0; s < nkc; ++s, ++g) {
+                const int b = g % ST;
+                const bool fail = g >= ST && !mbar_wait_ab(smem_u32(&empty[b]), ((g - ST) / ST) & 1, abort_v);
+                if (bar_any(1, NPROD, fail)) {
+                    if (fail && !*abort_v) atomicExch(err, 2);
+                    *abort_v = 1;
+                    ok = false;
+                    break;
+                }
+                uint8_t *st = smem + b * STAGE;
+                const uint32_t fb = smem_u32(&full[b]);
+                if (tp == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * ABYTES));
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(st)),
+                        "l"(gA + (int64_t)s * 2 * ABYTES), "r"(2 * ABYTES), "r"(fb)
+                        : "memory");
+                    n_issued = g + 1;
+                }
+                // 16 copies of 16 bytes per column (4 panels x 4 K groups).  One warp
+                // instruction covers 8 columns x 4 K groups of one panel: it writes
+                // one 512-byte run of shared memory (no bank conflicts) and reads 64
+                // contiguous bytes per column
+                for (int e = tp; e < NC * 16; e += NPROD) {
+                    const int li = e & 31, ii = e >> 5;
+                    const int part = ii / (NC / 8), n = (ii - part * (NC / 8)) * 8 + (li & 7), gq = li >> 3;
+                    const long long v = srcv[n];
+                    const __nv_bfloat16 *srcp = qb;
+                    uint32_t bytes = 0;
+                    if (v >= 0) {
+                        srcp = qb + v * 4 * Tp + s * 4 * KC + part * KC + gq * 8;
+                        bytes = 16;
+                    }
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                                     smem_u32(st + 2 * ABYTES + part * BB + core_off(n, gq * 8))),
+                                 "l"(srcp), "r"(bytes)
+                                 : "memory");
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fb));
+            }
         }
-        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fb));
-    };
-
-    bool ok = true;
-    int nprod = 0;  // stages whose copies have been issued
-    for (; nprod < ST - 1 && nprod < nkc; ++nprod) produce(nprod, nprod);
-    int s = 0;
-    for (; s < nkc; ++s) {
-        const int b = s % ST, u = s / ST;
-        if (tid == 0) {
-            if (!mbar_wait(smem_u32(&full[b]), u & 1)) {
-                atomicExch(err, 1);
-                abort_flag = 1;
-            } else {
-                asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == 4) {
+        // ---------------- MMA issue (one thread)
+        if (lane == 0) {
+            // bf16 x bf16 -> f32, K-major A and B, M = 128, N = 4 NC or 2 NC
+            const uint32_t idesc_all =
+                (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((4 * NC) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            const uint32_t idesc_hi =
+                (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * NC) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            int g = 0;
+            bool ok = true;
+            for (int j = 0; j < my_tiles && ok; ++j) {
+                const int slot = j & 1;
+                if (j >= 2 && !mbar_wait_ab(smem_u32(&acce[slot]), ((j - 2) >> 1) & 1, abort_v)) {
+                    if (!*abort_v) atomicExch(err, 3);
+                    *abort_v = 1;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t aHi = smem_u32(smem + b * STAGE), aLo = aHi + ABYTES;
-                const uint32_t rHi = aHi + 2 * ABYTES, rLo = rHi + BB, iHi = rLo + BB, iLo = iHi + BB;
-                for (int k = 0; k < KC / 16; ++k) {
-                    const uint32_t so = k * 256;  // two core matrices along K per k-step
-                    const uint64_t da[3] = {smem_desc(aHi + so), smem_desc(aHi + so), smem_desc(aLo + so)};
-                    const uint64_t dr[3] = {smem_desc(rHi + so), smem_desc(rLo + so), smem_desc(rHi + so)};
-                    const uint64_t di[3] = {smem_desc(iHi + so), smem_desc(iLo + so), smem_desc(iHi + so)};
-                    for (int q = 0; q < 3; ++q) {
-                        uint32_t en = (s > 0 || k > 0 || q > 0) ? 1u : 0u;
-                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                                     "l"(da[q]), "l"(dr[q]), "r"(idesc), "r"(en));
-                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem2),
-                                     "l"(da[q]), "l"(di[q]), "r"(idesc), "r"(en));
+                const uint32_t d = tmem + slot * 4 * NC;
+                for (int s = 0; s < nkc; ++s, ++g) {
+                    const int b = g % ST;
+                    if (!mbar_wait_ab(smem_u32(&full[b]), (g / ST) & 1, abort_v)) {
+                        if (!*abort_v) atomicExch(err, 1);
+                        *abort_v = 1;
+                        ok = false;
+                        break;
                     }
+                    asm volatile("fence.proxy.async.shared::cta;");
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t aHi = smem_u32(smem + b * STAGE), aLo = aHi + ABYTES, bAll = aHi + 2 * ABYTES;
+                    for (int k = 0; k < KC / 16; ++k) {
+                        const uint32_t so = k * 256;  // two core matrices along K per k-step
+                        const uint32_t en = (s > 0 || k > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                                     "l"(smem_desc(aHi + so)), "l"(smem_desc(bAll + so)), "r"(idesc_all), "r"(en));
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                                     "l"(smem_desc(aLo + so)), "l"(smem_desc(bAll + so)), "r"(idesc_hi), "r"(1u));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&empty[b])));
+                    n_consumed = g + 1;
+                    n_commit = g + 1;
                 }
+                if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&empty[b])));
-                ncommit = s + 1;
+                    smem_u32(&accf[slot])));
             }
         }
-        // the next stage to load reuses the buffer of stage s - 1
-        if (nprod < nkc && s >= 1 && !mbar_wait(smem_u32(&empty[nprod % ST]), ((s - 1) / ST) & 1)) {
-            if (tid == 0) atomicExch(err, 2);
-            abort_flag = 1;
-        }
-        __syncthreads();
-        if (abort_flag) {
-            ok = false;
-            break;
-        }
-        if (nprod < nkc) {
-            produce(nprod, nprod % ST);
-            ++nprod;
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 0-3 = TMEM lanes 0-127)
+        // lane r < 64 holds Ar rows (D1 -> Re, D2 -> Im); lane r >= 64 holds
+        // Ai rows (D1 -> Im, D2 -> -Re).  Per chunk of EPC columns every lane
+        // stages (D1, D2) column-major; then thread (row, half) combines the
+        // two lanes of its row for EPC / 2 columns and adds them to the target.
+        const int row = (warp & 1) * 32 + lane, half = warp >> 1;
+        for (int j = 0; j < my_tiles; ++j) {
+            const int slot = j & 1;
+            const tc_tile t = tiles[blockIdx.x + (int64_t)j * gridDim.x];
+            asm volatile("bar.sync 2, 128;");  // everyone is done with the previous tgt
+            for (int c = tid; c < NC; c += 128) {
+                long long v = -1;
+                if (c < t.npair) {
+                    int vi = t.pair0 + c;
+                    int pi = vi / mr, m = vi - pi * mr;
+                    v = pairs[pi].y + m * dstride;
+                }
+                tgt[c] = v;
+            }
+            const bool have = mbar_wait_ab(smem_u32(&accf[slot]), (j >> 1) & 1, abort_v);
+            if (bar_any(2, 128, !have)) {
+                if (!have && !*abort_v) atomicExch(err, 4);
+                *abort_v = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // columns of the slot: [0, NC) Br hi, [NC, 2 NC) Bi hi, [2 NC, 3 NC) Br lo, [3 NC, 4 NC) Bi lo
+            const uint32_t d1 = tmem + slot * 4 * NC + ((uint32_t)(warp * 32) << 16), d2 = d1 + NC;
+            const int rowg = t.rt * 64 + row;
+            for (int c0 = 0; c0 < NC; c0 += EPC) {
+                uint32_t v1[16], v2[16], w1[16], w2[16];
+                tmem_ld16x2(d1 + c0, d2 + c0, v1, v2);
+                tmem_ld16x2(d1 + 2 * NC + c0, d2 + 2 * NC + c0, w1, w2);
+#pragma unroll
+                for (int jj = 0; jj < EPC; ++jj)
+                    stg[jj * 128 + tid] = make_float2(__uint_as_float(v1[jj]) + __uint_as_float(w1[jj]),
+                                                      __uint_as_float(v2[jj]) + __uint_as_float(w2[jj]));
+                asm volatile("bar.sync 2, 128;");
+                if (rowg < Tout) {
+#pragma unroll
+                    for (int jj = half * (EPC / 2); jj < (half + 1) * (EPC / 2); ++jj) {
+                        const int n = c0 + jj;
+                        if (n < t.npair) {
+                            const float2 top = stg[jj * 128 + row], bot = stg[jj * 128 + 64 + row];
+                            atomicAdd(reinterpret_cast<float2 *>(dst + tgt[n] + rowg),
+                                      make_float2(top.x - bot.y, top.y + bot.x));
+                        }
+                    }
+                }
+                asm volatile("bar.sync 2, 128;");
+            }
+            // this slot is read: the MMAs of tile j + 2 may overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[slot])));
         }
     }
-    // drain: this thread's density copies; on abort, the operator copies of
-    // stages issued but not consumed; then the last commit (it covers every
-    // MMA issued before it)
-    asm volatile("cp.async.wait_all;");
-    if (!ok && tid == 0)
-        for (int s2 = s; s2 < nprod; ++s2) mbar_wait(smem_u32(&full[s2 % ST]), (s2 / ST) & 1);
     __syncthreads();
-    const int nc = ncommit;
-    if (nc > 0 && !mbar_wait(smem_u32(&empty[(nc - 1) % ST]), ((nc - 1) / ST) & 1)) {
-        if (tid == 0) atomicExch(err, 2);
-        abort_flag = 1;
-    }
+    // drain after an error: copies issued but not consumed, then the last MMA
+    // commit (it covers every MMA issued before it)
+    if (*abort_v && tid == 0)
+        for (int s2 = n_consumed; s2 < n_issued; ++s2) mbar_wait(smem_u32(&full[s2 % ST]), (s2 / ST) & 1);
+    const int nc = n_commit;
+    if (*abort_v && nc > 0 && tid == 0) mbar_wait(smem_u32(&empty[(nc - 1) % ST]), ((nc - 1) / ST) & 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
-    ok = ok && !abort_flag;
-    // epilogue: lane r < 64 holds Ar rows (D1 -> Re, D2 -> Im); lane r >= 64
-    // holds Ai rows (D1 -> Im, D2 -> -Re).  Warps 0-1 write, then warps 2-3 add.
-    const int r = warp * 32 + lane;
-    for (int pass = 0; pass < 2 && ok; ++pass) {
-        if ((warp >> 1) == pass) {
-            float2 *row = sD + (r & 63) * NC;
-            for (int c0 = 0; c0 < NC; c0 += 16) {
-                uint32_t v1[16], v2[16];
-                uint32_t a1 = tmem + ((uint32_t)(warp * 32) << 16) + c0;
-                uint32_t a2 = tmem2 + ((uint32_t)(warp * 32) << 16) + c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v1[0]), "=r"(v1[1]), "=r"(v1[2]), "=r"(v1[3]), "=r"(v1[4]), "=r"(v1[5]), "=r"(v1[6]),
-                      "=r"(v1[7]), "=r"(v1[8]), "=r"(v1[9]), "=r"(v1[10]), "=r"(v1[11]), "=r"(v1[12]), "=r"(v1[13]),
-                      "=r"(v1[14]), "=r"(v1[15])
-                    : "r"(a1));
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v2[0]), "=r"(v2[1]), "=r"(v2[2]), "=r"(v2[3]), "=r"(v2[4]), "=r"(v2[5]), "=r"(v2[6]),
-                      "=r"(v2[7]), "=r"(v2[8]), "=r"(v2[9]), "=r"(v2[10]), "=r"(v2[11]), "=r"(v2[12]), "=r"(v2[13]),
-                      "=r"(v2[14]), "=r"(v2[15])
-                    : "r"(a2));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float d1 = __uint_as_float(v1[j]), d2 = __uint_as_float(v2[j]);
-                    if (pass == 0) {
-                        row[c0 + j] = make_float2(d1, d2);
-                    } else {
-                        float2 o = row[c0 + j];
-                        row[c0 + j] = make_float2(o.x - d2, o.y + d1);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (ok) {
-        const int row0 = t.rt * 64;
-        for (int e = tid; e < 64 * NC; e += TCT) {
-            int rr = e & 63, n = e >> 6;
-            int rowg = row0 + rr;
-            if (n < t.npair && rowg < Tout) {
-                float2 v = sD[rr * NC + n];
-                atomicAdd(reinterpret_cast<float2 *>(dst + pp[n].y + rowg), v);
-            }
-        }
-    }
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * NC));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * NC));
 }
 
 // operator panels: per operator, per row tile (64 complex rows), per stage
@@ -342,10 +436,20 @@ template <int NC, int ST>
 void launch_tc(const tc_args &a, int ntiles, cudaStream_t s)
 {
     const size_t stage = 2 * (size_t)ABYTES + 4 * (size_t)NC * KC * 2;
-    const size_t smem = 128 + std::max<size_t>(ST * stage, (size_t)64 * NC * sizeof(float2));
-    FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<NC, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_btr_tc<NC, ST><<<ntiles, TCT, smem, s>>>(a.tiles, a.pairs, a.A, a.op_bytes, a.nkc, a.Tout, a.Tin, a.qb, a.dst,
-                                               a.mr, a.svstride, a.dstride, a.err);
+    const size_t smem = 128 + ST * stage + (size_t)EPC * 128 * sizeof(float2);
+    static int per_sm = 0, nsm = 0;  // resident CTAs per SM for this instantiation
+    if (!per_sm) {
+        int dev = 0;
+        FDA_CUDA(cudaGetDevice(&dev));
+        FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<NC, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_btr_tc<NC, ST>, WS_THREADS, smem));
+        per_sm = std::min(per_sm, 512 / (8 * NC));  // tensor memory: 8 NC columns per CTA
+        if (per_sm < 1) fda_fail(FDA_ERR_CUDA, "tensor-core translation kernel does not fit on an SM");
+    }
+    const int grid = std::min(ntiles, per_sm * nsm);
+    k_btr_tc<NC, ST><<<grid, WS_THREADS, smem, s>>>(a.tiles, ntiles, a.pairs, a.A, a.op_bytes, a.nkc, a.Tout, a.Tin,
+                                                    a.qb, a.dst, a.mr, a.svstride, a.dstride, a.err);
 }
 
 void pack_one(fda_handle *h, tc_ops &P, const tr_batch &B, const dbuf &ops64, int nops, int Tout, int Tin)
@@ -407,7 +511,8 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     const int nops = (int)B.op_start.size() - 1;
     const double avg_cols = (double)B.npairs * mr / std::max(1, nops);
     // narrow tiles where an operator has few pairs (less padding, more CTAs per SM)
-    const int NC = avg_cols < 48.0 ? 32 : 64;
+    int NC = avg_cols < 48.0 ? 32 : 64;
+    if (const char *e = getenv("FDA_TC_NC")) NC = atoi(e) == 32 ? 32 : 64;
     if (P.tiles_nc != NC || P.tiles_mr != mr) {
         std::vector<tc_tile> tiles;
         for (int o = 0; o < nops; ++o) {
@@ -425,8 +530,18 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (P.ntiles == 0) return;
     tc_args a{P.tiles.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.Tout, P.Tin,
               src.as<__nv_bfloat16>(), dst, mr, svstride, dstride, h->tc_err.as<int>()};
-    if (NC == 32) launch_tc<32, 2>(a, P.ntiles, h->stream);
-    else launch_tc<64, 2>(a, P.ntiles, h->stream);
+    int st = 4;
+    if (const char *e = getenv("FDA_TC_ST")) st = atoi(e);
+    if (NC == 32) {
+        if (st <= 3) launch_tc<32, 3>(a, P.ntiles, h->stream);
+        else if (st == 4) launch_tc<32, 4>(a, P.ntiles, h->stream);
+        else launch_tc<32, 6>(a, P.ntiles, h->stream);
+    } else {
+        if (st <= 2) launch_tc<64, 2>(a, P.ntiles, h->stream);
+        else if (st == 3) launch_tc<64, 3>(a, P.ntiles, h->stream);
+        else if (st == 4) launch_tc<64, 4>(a, P.ntiles, h->stream);
+        else launch_tc<64, 6>(a, P.ntiles, h->stream);
+    }
     FDA_CHECK_LAUNCH();
 }
 

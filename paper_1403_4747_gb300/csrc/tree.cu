@@ -24,6 +24,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <vector>
 
 #include "fda_internal.cuh"
@@ -310,6 +312,75 @@ __global__ void k_block_sizes(const int32_t *leaf_box, const int32_t *bbeg, cons
 // host helpers shared with precompute.cu
 int fda_cone_index_host(double dx, double dy, double dz, int nc) { return cone_index(dx, dy, dz, nc); }
 
+// Symmetry of the cone partition (the rotation invariance of Sec. 4.1.1).
+// The 6 nc^2 cones of a level are the images of a few representative cones
+// on the +z face (cells whose centre (A, B, nc) has 0 <= A <= B) under the 48
+// signed permutations of the axes.  Cone u gets the frame R_u = g_u R_rep(u)
+// with g_u mapping the representative's centre to u's centre, and the
+// opposite cone gets g = -g_u.  Since the kernel depends on distances only,
+// the M2L matrix of offset d, G(R_u eq, d w + R_ub eq) (u, ub the cones of d
+// and -d), equals G(R_rep eq, (g_u^T d) w + g_u^T R_ub eq): offsets with the
+// same representative, rotated offset and relative source frame share one
+// operator.  g is row-major, 9 integers per cone.
+void fda_cone_symmetry(int nc, std::vector<int> &rep, std::vector<int> &g)
+{
+    const int nco = 6 * nc * nc;
+    rep.assign(nco, -1);
+    g.assign(9 * (size_t)nco, 0);
+    auto center = [&](int u, int c[3]) {
+        int face = u / (nc * nc), rem = u % (nc * nc);
+        int a = rem / nc, b = rem % nc;
+        int ax = face / 2, sg = face % 2;
+        int o0 = ax == 0 ? 1 : 0, o1 = ax == 2 ? 1 : 2;
+        c[ax] = sg ? nc : -nc;
+        c[o0] = 2 * a + 1 - nc;
+        c[o1] = 2 * b + 1 - nc;
+    };
+    auto opposite = [&](int u) {
+        int face = u / (nc * nc), rem = u % (nc * nc);
+        int a = rem / nc, b = rem % nc;
+        return (face ^ 1) * nc * nc + (nc - 1 - a) * nc + (nc - 1 - b);
+    };
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    std::vector<std::array<int, 9>> grp;
+    for (const auto &pm : perms)
+        for (int sg = 0; sg < 8; ++sg) {
+            std::array<int, 9> m{};
+            for (int i = 0; i < 3; ++i) m[3 * i + pm[i]] = ((sg >> i) & 1) ? -1 : 1;
+            grp.push_back(m);
+        }
+    std::vector<int> reps;
+    for (int u = 0; u < nco; ++u) {
+        int c[3];
+        center(u, c);
+        if (c[2] == nc && c[0] >= 0 && c[1] >= c[0]) reps.push_back(u);
+    }
+    for (int u = 0; u < nco; ++u) {
+        const int v = opposite(u);
+        if (rep[v] >= 0) {
+            rep[u] = rep[v];
+            for (int k = 0; k < 9; ++k) g[9 * (size_t)u + k] = -g[9 * (size_t)v + k];
+            continue;
+        }
+        int cu[3];
+        center(u, cu);
+        for (size_t r = 0; r < reps.size() && rep[u] < 0; ++r) {
+            int cr[3];
+            center(reps[r], cr);
+            for (const auto &m : grp) {
+                bool hit = true;
+                for (int i = 0; i < 3 && hit; ++i) hit = m[3 * i] * cr[0] + m[3 * i + 1] * cr[1] + m[3 * i + 2] * cr[2] == cu[i];
+                if (hit) {
+                    rep[u] = reps[r];
+                    for (int k = 0; k < 9; ++k) g[9 * (size_t)u + k] = m[k];
+                    break;
+                }
+            }
+        }
+        if (rep[u] < 0) fda_fail(FDA_ERR_NUMERIC, "cone without a representative under the cube group");
+    }
+}
+
 void fda_tree_build(fda_handle *h)
 {
     cudaStream_t s = h->stream;
@@ -535,13 +606,35 @@ void fda_tree_build(fda_handle *h)
         FDA_CUDA(cudaStreamSynchronize(s));
         int nops = 0;
         h->h_ops[l].clear();
+        // high frequency: offsets equal under the cone symmetry share an operator
+        std::vector<int> crep, cg;
+        std::map<std::array<int, 6>, int> key_op;
+        if (L.hf) fda_cone_symmetry(L.nc, crep, cg);
         for (size_t t = 0; t < hu.size(); ++t) {
             if (!hu[t]) {
                 hu[t] = -1;
                 continue;
             }
-            hu[t] = nops++;
             int dz = (int)(t % S) - L.R_off, dy = (int)((t / S) % S) - L.R_off, dx = (int)(t / S / S) - L.R_off;
+            if (L.hf) {
+                const int d[3] = {dx, dy, dz};
+                const int u = cone_index(dx, dy, dz, L.nc), ub = cone_index(-dx, -dy, -dz, L.nc);
+                const int *gu = &cg[9 * (size_t)u], *gb = &cg[9 * (size_t)ub];
+                std::array<int, 6> key{crep[u], 0, 0, 0, 0, crep[ub]};
+                for (int i = 0; i < 3; ++i) key[1 + i] = gu[i] * d[0] + gu[3 + i] * d[1] + gu[6 + i] * d[2];
+                int enc = 0;  // g_u^T g_ub, entries in {-1, 0, 1}, base 3
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        enc = 3 * enc + 1 + gu[i] * gb[j] + gu[3 + i] * gb[3 + j] + gu[6 + i] * gb[6 + j];
+                key[4] = enc;
+                auto it = key_op.find(key);
+                if (it != key_op.end()) {
+                    hu[t] = it->second;
+                    continue;
+                }
+                key_op.emplace(key, nops);
+            }
+            hu[t] = nops++;
             h->h_ops[l].push_back(make_int3(dx, dy, dz));
         }
         L.n_ops = nops;
