@@ -19,6 +19,7 @@ bounded sample of rows of the same workload, on the host cores.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -51,7 +52,7 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -64,10 +65,14 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def mark(self, which):
+        """Wall-clock start or end of the timed region (samples outside it are dropped)."""
+        setattr(self, which, datetime.datetime.now())
 
     def stop(self):
         if self.p is None:
@@ -80,16 +85,20 @@ class ClockSampler:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = getattr(self, "t_begin", None), getattr(self, "t_end", None)
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                if t0 is not None and t1 is not None and not (t0 <= ts <= t1):
+                    continue
+                sm.append(float(parts[2]))
+                smax.append(float(parts[3]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            for n, v in zip(names, parts[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         os.unlink(self.path)
@@ -117,7 +126,9 @@ def run_reference(args):
     v, f = icosphere(args.level)
     n = len(f)
     x = complex_normal(n, seed=1234)
-    rows_n = args.ref_rows
+    # rows per step: at most --ref-rows, and about 10,000 rows over the run so
+    # that any --steps finishes within a few minutes on the host cores
+    rows_n = max(16, min(args.ref_rows, 10000 // max(1, args.steps)))
     rows = np.random.default_rng(7).choice(n, rows_n, replace=False)
     oracle.load()
     for _ in range(args.warmup):
@@ -192,11 +203,13 @@ def run_native(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nl0 = F.fda_launch_count()
+    clocks.mark("t_begin")
     e0.record(stream)
     for _ in range(args.steps):
         P.apply(x, y)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark("t_end")
     launches = F.fda_launch_count() - nl0
     barrier()
     clk = clocks.stop()
@@ -268,27 +281,49 @@ def run_native(args):
         F.fda_apply_host(P.h, xh.data_ptr(), yh.data_ptr(), 1, n)
     e2e_ms = reduce_max((time.perf_counter() - te) / ne * 1e3)
 
-    # roofline of the dominant pass (M2L in the chosen form: FP32 ALU bound)
+    # roofline of the dominant kernel: the tensor-core translation kernel in
+    # the M2L pass (all levels).  Algorithmic work of one apply: every
+    # distinct compressed operator read once (8 bytes per complex entry, FP32
+    # or bf16 hi + lo), the source densities read once and the target
+    # densities read and written once; 8 real flops per complex
+    # multiply-add.  The binding roof is the larger of bytes / HBM peak and
+    # flops / bf16 peak.
     peaks, src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak_tflops = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    m2l_flops = _m2l_flops(P)
-    m2l_ms = pt32[2]
-    achieved = m2l_flops / (m2l_ms * 1e-3) / 1e12
-    near_gbs = st.bytes_near / 2 / (pt32[5] * 1e-3) / 1e9  # FP32 storage: 8 bytes per entry
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-    roofline = {"kernel": "k_btr_tc<64> (M2L pass on tcgen05, all levels)", "bound": "tensor", "achieved": achieved,
-                "peak": bf16_peak, "unit": "TFLOP/s", "frac": achieved / bf16_peak,
-                "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; %s)" % src,
-                "algorithmic_flops_per_apply": m2l_flops,
-                "executed_tensor_flops_per_apply": 3 * m2l_flops,
-                "note": "algorithmic = 8 real flops per complex multiply-add; the split-bf16 form executes 3x that",
-                "simt_fp32_m2l": {"ms": pt32_simt[2], "achieved": m2l_flops / (pt32_simt[2] * 1e-3) / 1e12,
-                                  "peak": fp32_peak_tflops,
-                                  "frac": m2l_flops / (pt32_simt[2] * 1e-3) / 1e12 / fp32_peak_tflops,
-                                  "peak_source": "FP32 FMA rate: %d SMs x 128 lanes x 2 flops x %.0f MHz" % (nsm, sm_mhz)}}
+    m2l_flops = _m2l_flops(P)
+    m2l_bytes = _m2l_bytes(P)
+    m2l_ms = pt32[2]
+    t_hbm, t_tc = m2l_bytes / (hbm_peak * 1e9), m2l_flops / (bf16_peak * 1e12)
+    m2l_gbs = m2l_bytes / (m2l_ms * 1e-3) / 1e9
+    m2l_tflops = m2l_flops / (m2l_ms * 1e-3) / 1e12
+    if t_hbm >= t_tc:
+        roofline = {"bound": "hbm", "achieved": m2l_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": m2l_gbs / hbm_peak}
+    else:
+        roofline = {"bound": "tensor", "achieved": m2l_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                    "frac": m2l_tflops / bf16_peak}
+    roofline.update({
+        "traffic": _m2l_traffic(args),
+        "kernel": "k_btr_tc (tcgen05 gather-GEMM-scatter), M2L launches of one apply (one per level)",
+        "peak_source": "MEASURED_PEAKS.json (%s): hbm_gbs %.0f, bf16_tflops %.1f (burst)" % (src, hbm_peak, bf16_peak),
+        "ms_per_apply": m2l_ms,
+        "algorithmic_bytes_per_apply": m2l_bytes,
+        "algorithmic_flops_per_apply": m2l_flops,
+        "tensor": {"achieved_tflops": m2l_tflops, "frac_of_bf16": m2l_tflops / bf16_peak,
+                   "executed_tflops": 3 * m2l_flops / (m2l_ms * 1e-3) / 1e12,
+                   "note": "split bf16 executes 3 products per multiply-add"},
+        "simt_fp32_m2l": {"ms": pt32_simt[2], "achieved_tflops": m2l_flops / (pt32_simt[2] * 1e-3) / 1e12,
+                          "peak": fp32_peak_tflops,
+                          "frac": m2l_flops / (pt32_simt[2] * 1e-3) / 1e12 / fp32_peak_tflops,
+                          "peak_source": "FP32 FMA rate: %d SMs x 128 lanes x 2 flops x %.0f MHz" % (nsm, sm_mhz)}})
+    near_bytes = 8 * st.nnz_near + 24 * n  # FP32 entries read once; x read and y written once
+    near_gbs = near_bytes / (pt32[5] * 1e-3) / 1e9
+    near_roof = {"kernel": "k_near_apply", "bound": "hbm", "achieved": near_gbs, "peak": hbm_peak, "unit": "GB/s",
+                 "frac": near_gbs / hbm_peak, "ms_per_apply": pt32[5], "algorithmic_bytes_per_apply": near_bytes}
 
     solve = {}
     if not args.no_solve:
@@ -363,7 +398,7 @@ def run_native(args):
                            "pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt64.tolist()))},
             "chosen_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32.tolist())),
             "chosen_simt_m2l_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32_simt.tolist())),
-            "near_field_gbs": near_gbs,
+            "near_field_roofline": near_roof,
             "batched_rhs": batched,
             "solve": solve,
             "tree": {"levels": nlev, "boxes": st.n_boxes, "leaves": st.n_leaves, "nnz_near": st.nnz_near,
@@ -382,6 +417,38 @@ def run_native(args):
     return 0
 
 
+def _m2l_traffic(args):
+    """DRAM bytes of the M2L pass per matvec from the committed ncu summary
+    (sphere level 7, k = 50, eps 1e-4), or None for another workload or if the
+    kernel source changed since the counters were taken."""
+    import hashlib
+    if (args.level, args.k, args.eps) != (7, 50.0, 1e-4):
+        return None
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_btr_tc_traffic_sphere_l7_k50.json")))
+        src = open(os.path.join(ROOT, "paper_1403_4747_gb300", "csrc", "translate_tc.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        return rec["m2l_dram_bytes_per_matvec"]
+    except Exception:
+        return None
+
+
+def _m2l_bytes(P):
+    """Algorithmic bytes of the M2L pass per apply: distinct operators once
+    (8 bytes per complex entry), source densities read once, target
+    densities read and written once (8 bytes per complex value)."""
+    st = P.stats()
+    total = 0
+    for l in range(st.n_levels):
+        T = st.level_rank[l]
+        if T == 0 or st.level_m2l_pairs[l] == 0:
+            continue
+        total += 8 * st.level_m2l_ops[l] * T * T
+        total += 3 * 8 * st.level_boxes[l] * st.level_cones[l] * T
+    return int(total)
+
+
 def _m2l_flops(P):
     """Real flops of the M2L pass per apply: 8 T_l^2 per interaction pair
     (one complex multiply-add is 8 real flops)."""
@@ -392,7 +459,7 @@ def _m2l_flops(P):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--level", type=int, default=7)

@@ -103,6 +103,7 @@ typedef struct {
     int32_t level_cones[32];
     double precompute_s, tree_s, near_s;
     int64_t level_m2l_pairs[32];  /* per level: M2L (target, source) pairs */
+    int32_t level_m2l_ops[32];    /* per level: distinct M2L operators (after the cone symmetry) */
 } fda_stats;
 
 typedef struct fda_handle fda_handle;

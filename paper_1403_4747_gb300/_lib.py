@@ -42,7 +42,8 @@ class fda_stats(ctypes.Structure):
                 ("level_regime", ctypes.c_int32 * 32), ("level_rank", ctypes.c_int32 * 32),
                 ("level_boxes", ctypes.c_int32 * 32), ("level_cones", ctypes.c_int32 * 32),
                 ("precompute_s", ctypes.c_double), ("tree_s", ctypes.c_double), ("near_s", ctypes.c_double),
-                ("level_m2l_pairs", ctypes.c_int64 * 32)]
+                ("level_m2l_pairs", ctypes.c_int64 * 32),
+                ("level_m2l_ops", ctypes.c_int32 * 32)]
 
 
 _lib = None

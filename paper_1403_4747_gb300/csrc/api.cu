@@ -356,6 +356,7 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
             out->level_boxes[l] = l < h->nlev ? h->lev[l].nbox : 0;
             out->level_cones[l] = l < h->nlev ? h->lev[l].ncones : 0;
             out->level_m2l_pairs[l] = l < h->nlev ? h->lev[l].n_il : 0;
+            out->level_m2l_ops[l] = l < h->nlev ? h->lev[l].n_ops : 0;
             if (l < h->nlev) ops += h->lev[l].n_ops;
         }
         out->n_m2l_ops = ops;

@@ -1,5 +1,6 @@
-// Tensor-core (tcgen05) form of the batched translations for the chosen
-// precision: the M2L tiles of translate.cu as bf16 tensor-core GEMMs.
+// Tensor-core (tcgen05) form of the batched translations (M2M, M2L, L2L) for
+// the chosen precision: the operator-grouped tiles of translate.cu as bf16
+// tensor-core GEMMs.
 //
 // A complex tile C (64 rows x NC columns) += A (64 x Tin) B (Tin x NC) is
 // computed with the stacked operator [Ar; Ai] (128 rows, M = 128 per
@@ -17,17 +18,16 @@
 // 8-row x 16-byte core matrices, LBO = 128 B between core matrices along K,
 // SBO = 512 B between 8-row groups (32 complex columns of K per stage); the
 // B panels Br hi, Bi hi, Br lo, Bi lo follow one another, so [Br Bi] hi and
-// the whole [Br Bi hi | Br Bi lo] are single operands of 2 NC and 4 NC rows.  The operator
-// panels are stored in HBM already in that layout (built once in setup) and
-// copied to shared memory with cp.async.bulk on an mbarrier; the densities,
-// split into bf16 once per level, are gathered column by column with 16-byte
-// cp.async copies that arrive on the same mbarrier.  Every mbarrier wait
-// is bounded: on timeout the kernel records an error, waits (bounded) for its
-// own copies and MMAs, frees its tensor memory and returns.
+// the whole [Br Bi hi | Br Bi lo] are single operands of 2 NC and 4 NC rows.
+// The operator panels are stored in HBM already in that layout (built once in
+// setup) and copied to shared memory with cp.async.bulk on an mbarrier; the
+// densities, split into bf16 once per level, are gathered column by column
+// with 16-byte cp.async copies that arrive on the same mbarrier.  Every
+// mbarrier wait is bounded: on timeout the kernel records an error, waits
+// (bounded) for its own copies and MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
-#include <cstdlib>
 #include <vector>
 
 #include "fda_internal.cuh"
@@ -242,18 +242,16 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                         : "memory");
                     n_issued = g + 1;
                 }
-                // 16 copies of 16 bytes per column (4 panels x 4 K groups).  One warp
-                // instruction covers 8 columns x 4 K groups of one panel: it writes
-                // one 512-byte run of shared memory (no bank conflicts) and reads 64
-                // contiguous bytes per column
+                // 16 copies of 16 bytes per column: panel part = c16 / 4 (Re hi, Im hi,
+                // Re lo, Im lo), K group gq = c16 % 4; one column's stage is 256
+                // contiguous bytes, so a warp instruction reads two whole columns
                 for (int e = tp; e < NC * 16; e += NPROD) {
-                    const int li = e & 31, ii = e >> 5;
-                    const int part = ii / (NC / 8), n = (ii - part * (NC / 8)) * 8 + (li & 7), gq = li >> 3;
+                    const int n = e >> 4, c16 = e & 15, part = c16 >> 2, gq = c16 & 3;
                     const long long v = srcv[n];
                     const __nv_bfloat16 *srcp = qb;
                     uint32_t bytes = 0;
                     if (v >= 0) {
-                        srcp = qb + v * 4 * Tp + s * 4 * KC + part * KC + gq * 8;
+                        srcp = qb + v * 4 * Tp + s * 4 * KC + c16 * 8;
                         bytes = 16;
                     }
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
@@ -511,8 +509,7 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     const int nops = (int)B.op_start.size() - 1;
     const double avg_cols = (double)B.npairs * mr / std::max(1, nops);
     // narrow tiles where an operator has few pairs (less padding, more CTAs per SM)
-    int NC = avg_cols < 48.0 ? 32 : 64;
-    if (const char *e = getenv("FDA_TC_NC")) NC = atoi(e) == 32 ? 32 : 64;
+    const int NC = avg_cols < 48.0 ? 32 : 64;
     if (P.tiles_nc != NC || P.tiles_mr != mr) {
         std::vector<tc_tile> tiles;
         for (int o = 0; o < nops; ++o) {
@@ -530,18 +527,10 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (P.ntiles == 0) return;
     tc_args a{P.tiles.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.Tout, P.Tin,
               src.as<__nv_bfloat16>(), dst, mr, svstride, dstride, h->tc_err.as<int>()};
-    int st = 4;
-    if (const char *e = getenv("FDA_TC_ST")) st = atoi(e);
-    if (NC == 32) {
-        if (st <= 3) launch_tc<32, 3>(a, P.ntiles, h->stream);
-        else if (st == 4) launch_tc<32, 4>(a, P.ntiles, h->stream);
-        else launch_tc<32, 6>(a, P.ntiles, h->stream);
-    } else {
-        if (st <= 2) launch_tc<64, 2>(a, P.ntiles, h->stream);
-        else if (st == 3) launch_tc<64, 3>(a, P.ntiles, h->stream);
-        else if (st == 4) launch_tc<64, 4>(a, P.ntiles, h->stream);
-        else launch_tc<64, 6>(a, P.ntiles, h->stream);
-    }
+    // four stage buffers (one CTA per SM holds the 8 NC accumulator columns
+    // of NC = 64; NC = 32 fits two)
+    if (NC == 32) launch_tc<32, 4>(a, P.ntiles, h->stream);
+    else launch_tc<64, 4>(a, P.ntiles, h->stream);
     FDA_CHECK_LAUNCH();
 }
 
