@@ -69,7 +69,8 @@ typedef struct {
     int mode;              /* fda_mode: FDA, or dense all-pairs direct sum (small meshes, testing) */
     int restart;           /* GMRES restart length (default 100) */
     int maxit;             /* GMRES iteration cap (default 1000) */
-    int precond;           /* 0 none (the paper's setting), 1 leaf block-diagonal (right preconditioner) */
+    int precond;           /* 0 none (the paper's setting), 1 leaf block-diagonal (right preconditioner);
+                              the learned preconditioner (2) is selected with fda_set_precond after fda_sai_set */
     double alpha_sign;     /* coupling alpha = alpha_sign * i/k: +1 (default) the paper's i/k as written with the
                               normal into the body; -1 the conjugate coupling */
     int max_rhs;           /* right-hand sides one fda_apply pass processes together (1..256, default 1);
@@ -192,7 +193,8 @@ fda_status fda_set_tensor_cores(fda_handle *h, int on);
 
 /* Select the preconditioner used by later fda_solve calls: 0 none, 1 leaf
  * block-diagonal (needs a handle created with precond = 1, which builds the
- * block inverses during fda_precompute_translations; else FDA_ERR_STATE). */
+ * block inverses during fda_precompute_translations; else FDA_ERR_STATE),
+ * 2 learned SAI (needs fda_sai_set first; else FDA_ERR_STATE). */
 fda_status fda_set_precond(fda_handle *h, int precond);
 
 /* Tree, list and operator statistics (host struct). */
@@ -204,6 +206,58 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out);
  * field (S2T).  Returns FDA_ERR_STATE if timing is off. */
 fda_status fda_set_timing(fda_handle *h, int enable);
 fda_status fda_get_pass_times(fda_handle *h, float out[6]);
+
+/* ---- Learned sparse approximate inverse (SAI) preconditioner ----
+ * Not in the paper (which solves unpreconditioned, Sec. 5.3): a right
+ * preconditioner M on the leaf-block pattern (i, j in the same leaf) whose
+ * entries a small network predicts from the pair's local geometry and k
+ * (8 rotation-invariant features: k|x_j - x_i|, the two normal projections of
+ * the unit separation, n_i.n_j, k sqrt(area_i), k sqrt(area_j), [i == j],
+ * sqrt(area_j)/max(|x_j - x_i|, sqrt(area_j)); two tanh layers of 32; output
+ * Re, Im of M_ij).  Training minimises
+ *     L = (1/sum_B n_B) sum_B ||M_B A_BB - I||_F^2
+ * over the leaf self blocks A_BB of the near-field matrix (Eq. eq_sum) that
+ * fda_precompute_translations built.  Weights are fda_sai_num_params() floats,
+ * caller-owned, layout W1[32][8], b1[32], W2[32][32], b2[32], W3[2][32], b3[2]. */
+typedef struct {
+    int epochs;               /* full-batch Adam steps (default 400) */
+    double lr;                /* Adam step size (default 3e-3) */
+    unsigned long long seed;  /* seed of fda_sai_init_weights used by callers (default 1) */
+} fda_sai_config;
+
+typedef struct {
+    double loss_init;   /* L of the initial weights over all training blocks */
+    double loss_final;  /* L after training */
+    double train_s;     /* wall time of the training call */
+} fda_sai_report;
+
+int fda_sai_num_params(void);
+fda_status fda_sai_default_config(fda_sai_config *cfg);
+/* Xavier-uniform weights from splitmix64(seed), zero biases (host). */
+fda_status fda_sai_init_weights(unsigned long long seed, float *weights);
+/* Train on the leaf blocks of nhandles precomputed handles (their own
+ * near-field matrices, FP32 kernels on the first handle's stream).  weights:
+ * host, in = initial, out = trained.  FDA_ERR_STATE before precompute,
+ * FDA_ERR_NUMERIC if the loss stops being finite; message on handles[0]. */
+fda_status fda_sai_train(fda_handle *const *handles, int nhandles, const fda_sai_config *cfg, float *weights,
+                         fda_sai_report *rep);
+/* Evaluate the network on h's leaf blocks and keep the result as h's learned
+ * preconditioner (select it with fda_set_precond(h, 2)).  loss (optional,
+ * host) receives L of the stored M against the FP64 blocks. */
+fda_status fda_sai_set(fda_handle *h, const float *weights, double *loss);
+/* Loss L and gradient dL/dweights (fda_sai_num_params() doubles) of the
+ * training kernels for caller-supplied data (host arrays, copied in): n elements
+ * with centroids [n][3], normals [n][3], areas [n], wavenumber k; nblocks
+ * blocks, block b = elements block_elems[block_ptr[b] .. block_ptr[b+1]) (1 to
+ * 64 each, block_ptr[0] = 0), blocks = each block's n_b x n_b matrix
+ * row-major, concatenated.  precision = FDA_PLAIN_FP64 runs the FP64
+ * instantiation of the kernels, FDA_CHOSEN_FP32 the FP32 one that training
+ * uses (weights and blocks rounded to FP32).  Needs a GPU; no handle (returns
+ * the status only). */
+fda_status fda_sai_loss_grad(int64_t n, const double *centroids, const double *normals, const double *areas,
+                             double k, int nblocks, const int64_t *block_ptr, const int32_t *block_elems,
+                             const fda_c128 *blocks, const double *weights, int precision, double *loss,
+                             double *grad);
 
 /* Symmetry table of the cone partition of a high-frequency level with
  * nc x nc cells per cube face (6 nc^2 cones, Sec. 3.1; cone index =

@@ -46,6 +46,14 @@ class fda_stats(ctypes.Structure):
                 ("level_m2l_ops", ctypes.c_int32 * 32)]
 
 
+class fda_sai_config(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
+class fda_sai_report(ctypes.Structure):
+    _fields_ = [("loss_init", ctypes.c_double), ("loss_final", ctypes.c_double), ("train_s", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -78,6 +86,16 @@ def load(path: str = LIB_PATH):
     lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
     lib.fda_cone_symmetry_table.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.fda_cone_symmetry_table.restype = ctypes.c_int
+    lib.fda_sai_num_params.argtypes = []
+    lib.fda_sai_num_params.restype = cint
+    lib.fda_sai_default_config.argtypes = [ctypes.POINTER(fda_sai_config)]
+    lib.fda_sai_init_weights.argtypes = [ctypes.c_ulonglong, vp]
+    lib.fda_sai_train.argtypes = [vp, cint, ctypes.POINTER(fda_sai_config), vp, ctypes.POINTER(fda_sai_report)]
+    lib.fda_sai_set.argtypes = [H, vp, vp]
+    lib.fda_sai_loss_grad.argtypes = [i64, vp, vp, vp, dbl, cint, vp, vp, vp, vp, cint, vp, vp]
+    for name in ("fda_sai_default_config", "fda_sai_init_weights", "fda_sai_train", "fda_sai_set",
+                 "fda_sai_loss_grad"):
+        getattr(lib, name).restype = cint
     lib.fda_launch_count.argtypes = []
     lib.fda_launch_count.restype = ctypes.c_longlong
     lib.fda_last_error.argtypes = [H]
@@ -198,6 +216,64 @@ def fda_cone_symmetry_table(nc: int):
     g = np.zeros((n, 3, 3), dtype=np.int32)
     _check(None, load().fda_cone_symmetry_table(nc, rep.ctypes.data, g.ctypes.data))
     return rep, g
+
+
+def fda_sai_num_params() -> int:
+    return int(load().fda_sai_num_params())
+
+
+def fda_sai_default_config(**overrides) -> fda_sai_config:
+    c = fda_sai_config()
+    _check(None, load().fda_sai_default_config(ctypes.byref(c)))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def fda_sai_init_weights(seed: int):
+    """Initial network weights (float32 numpy array)."""
+    import numpy as np
+    w = np.zeros(fda_sai_num_params(), dtype=np.float32)
+    _check(None, load().fda_sai_init_weights(seed, w.ctypes.data))
+    return w
+
+
+def fda_sai_train(handles, cfg: fda_sai_config, weights):
+    """Train in place on the leaf blocks of the given handles; returns the report."""
+    import numpy as np
+    assert weights.dtype == np.float32 and weights.flags.c_contiguous
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    rep = fda_sai_report()
+    _check(handles[0], load().fda_sai_train(ctypes.cast(arr, ctypes.c_void_p), len(handles), ctypes.byref(cfg),
+                                            weights.ctypes.data, ctypes.byref(rep)))
+    return rep
+
+
+def fda_sai_set(h, weights) -> float:
+    """Evaluate the network on h's leaf blocks as its learned preconditioner; returns the loss."""
+    import numpy as np
+    assert weights.dtype == np.float32 and weights.flags.c_contiguous
+    loss = ctypes.c_double()
+    _check(h, load().fda_sai_set(h, weights.ctypes.data, ctypes.byref(loss)))
+    return loss.value
+
+
+def fda_sai_loss_grad(cent, nrm, area, k, block_ptr, block_elems, blocks, weights, precision=FDA_PLAIN_FP64):
+    """Loss and gradient of the training kernels for caller-supplied blocks (host numpy arrays)."""
+    import numpy as np
+    cent = np.ascontiguousarray(cent, dtype=np.float64)
+    nrm = np.ascontiguousarray(nrm, dtype=np.float64)
+    area = np.ascontiguousarray(area, dtype=np.float64)
+    bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+    be = np.ascontiguousarray(block_elems, dtype=np.int32)
+    A = np.ascontiguousarray(blocks, dtype=np.complex128)
+    W = np.ascontiguousarray(weights, dtype=np.float64)
+    loss = ctypes.c_double()
+    grad = np.zeros(fda_sai_num_params(), dtype=np.float64)
+    _check(None, load().fda_sai_loss_grad(len(area), cent.ctypes.data, nrm.ctypes.data, area.ctypes.data, float(k),
+                                          len(bp) - 1, bp.ctypes.data, be.ctypes.data, A.ctypes.data, W.ctypes.data,
+                                          precision, ctypes.byref(loss), grad.ctypes.data))
+    return loss.value, grad
 
 
 def fda_launch_count() -> int:

@@ -439,12 +439,16 @@ fda_status fda_set_tensor_cores(fda_handle *h, int on)
 fda_status fda_set_precond(fda_handle *h, int precond)
 {
     if (!h) return FDA_ERR_ARG;
-    if (precond != 0 && precond != 1) {
+    if (precond < 0 || precond > 2) {
         h->err = "unknown preconditioner";
         return FDA_ERR_ARG;
     }
     if (precond == 1 && !h->pc_M.p) {
         h->err = "block-diagonal preconditioner was not built (create the handle with precond = 1)";
+        return FDA_ERR_STATE;
+    }
+    if (precond == 2 && !h->sai_M.p) {
+        h->err = "learned preconditioner not set (call fda_sai_set first)";
         return FDA_ERR_STATE;
     }
     h->cfg.precond = precond;
@@ -485,3 +489,83 @@ void fda_destroy(fda_handle *h)
 }
 
 }  // extern "C"
+
+// ---- learned SAI preconditioner
+
+extern "C" int fda_sai_num_params(void) { return fda_sai_nparams(); }
+
+extern "C" fda_status fda_sai_default_config(fda_sai_config *c)
+{
+    if (!c) return FDA_ERR_ARG;
+    c->epochs = 400;
+    c->lr = 3e-3;
+    c->seed = 1;
+    return FDA_OK;
+}
+
+extern "C" fda_status fda_sai_init_weights(unsigned long long seed, float *weights)
+{
+    if (!weights) return FDA_ERR_ARG;
+    fda_sai_init(seed, weights);
+    return FDA_OK;
+}
+
+extern "C" fda_status fda_sai_train(fda_handle *const *handles, int nhandles, const fda_sai_config *cfg,
+                                    float *weights, fda_sai_report *rep)
+{
+    if (!handles || nhandles < 1 || !cfg || !weights || cfg->epochs < 0 || !(cfg->lr > 0)) return FDA_ERR_ARG;
+    for (int q = 0; q < nhandles; ++q) {
+        if (!handles[q]) return FDA_ERR_ARG;
+        if (handles[q]->state != 2) {
+            handles[q]->err = "fda_sai_train needs fda_precompute_translations first";
+            return FDA_ERR_STATE;
+        }
+    }
+    return guarded(handles[0], [&] {
+        double l0 = 0, l1 = 0, ts = 0;
+        fda_sai_train_impl(handles, nhandles, cfg->epochs, cfg->lr, weights, &l0, &l1, &ts);
+        if (rep) {
+            rep->loss_init = l0;
+            rep->loss_final = l1;
+            rep->train_s = ts;
+        }
+    });
+}
+
+extern "C" fda_status fda_sai_set(fda_handle *h, const float *weights, double *loss)
+{
+    if (!h || !weights) return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = "fda_sai_set needs fda_precompute_translations first";
+        return FDA_ERR_STATE;
+    }
+    return guarded(h, [&] {
+        double l = fda_sai_set_impl(h, weights);
+        if (loss) *loss = l;
+    });
+}
+
+extern "C" fda_status fda_sai_loss_grad(int64_t n, const double *centroids, const double *normals,
+                                        const double *areas, double k, int nblocks, const int64_t *block_ptr,
+                                        const int32_t *block_elems, const fda_c128 *blocks, const double *weights,
+                                        int precision, double *loss, double *grad)
+{
+    if (n < 1 || !centroids || !normals || !areas || !(k > 0) || nblocks < 1 || !block_ptr || !block_elems ||
+        !blocks || !weights || !loss || !grad || block_ptr[0] != 0 ||
+        (precision != FDA_PLAIN_FP64 && precision != FDA_CHOSEN_FP32))
+        return FDA_ERR_ARG;
+    for (int b = 0; b < nblocks; ++b)
+        if (block_ptr[b + 1] <= block_ptr[b]) return FDA_ERR_ARG;
+    try {
+        fda_sai_loss_grad_impl(n, centroids, normals, areas, k, nblocks, block_ptr, block_elems,
+                               reinterpret_cast<const c64d *>(blocks), weights, precision == FDA_CHOSEN_FP32, loss,
+                               grad);
+    } catch (const fda_error &e) {
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        return FDA_ERR_OOM;
+    } catch (...) {
+        return FDA_ERR_CUDA;
+    }
+    return FDA_OK;
+}

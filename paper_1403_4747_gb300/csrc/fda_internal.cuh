@@ -246,6 +246,8 @@ struct fda_handle {
 
     // leaf block-diagonal preconditioner (row-major n_B x n_B per leaf)
     dbuf pc_M, pc_off;
+    // learned SAI preconditioner on the same pattern (set by fda_sai_set)
+    dbuf sai_M, sai_off;
 
     // timing
     int timing = 0;
@@ -278,6 +280,14 @@ void fda_precond_build(fda_handle *h);
 void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z);
 
 void fda_build_batches(fda_handle *h);
+int fda_sai_nparams();
+void fda_sai_init(uint64_t seed, float *W);
+void fda_sai_train_impl(fda_handle *const *hs, int nh, int epochs, double lr, float *W, double *loss0,
+                        double *loss1, double *train_s);
+double fda_sai_set_impl(fda_handle *h, const float *W);
+void fda_sai_loss_grad_impl(int64_t n, const double *cent, const double *nrm, const double *area, double k, int nb,
+                            const int64_t *bptr, const int32_t *belem, const c64d *A, const double *W, int fp32,
+                            double *loss, double *grad);
 void fda_pack_tc(fda_handle *h);
 // split level l's FP32 densities (mr right-hand sides) into bf16 hi/lo
 void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr);

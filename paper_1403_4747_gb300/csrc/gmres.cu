@@ -128,7 +128,7 @@ struct solver {
     // y = A M x when the preconditioner is on (right preconditioning), else A x
     void apply_op(const c64d *x, c64d *y, int precision)
     {
-        if (h->cfg.precond == 1) {
+        if (h->cfg.precond != 0) {
             if (!ptmp.p) ptmp.alloc(sizeof(c64d) * n);
             fda_precond_apply(h, x, ptmp.as<c64d>());
             apply(ptmp.as<c64d>(), y, precision);
@@ -227,7 +227,7 @@ struct solver {
                 for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
                 y[i] = s / H[(size_t)i * m + i];
             }
-            if (h->cfg.precond == 1) {
+            if (h->cfg.precond != 0) {
                 // d += M (V y): form V y in w, then apply M into the basis slot V_m (free now)
                 FDA_CUDA(cudaMemsetAsync(w.p, 0, sizeof(c64d) * n, h->stream));
                 combine(V, y, 1.0, w.as<c64d>());

@@ -175,11 +175,14 @@ void fda_precond_build(fda_handle *h)
     if (hs == 2) fda_fail(FDA_ERR_NUMERIC, "singular leaf self block in the preconditioner");
 }
 
-// z = M r (both sorted order, complex double)
+// z = M r (both sorted order, complex double); M = the block-diagonal
+// inverse (precond 1) or the learned SAI blocks (precond 2), same pattern
 void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z)
 {
+    const bool learned = h->cfg.precond == 2;
     k_blockdiag_apply<<<h->nleaf, PT, 0, h->stream>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
-                                                      h->box_end.as<int32_t>(), h->pc_off.as<int64_t>(),
-                                                      h->pc_M.as<c64d>(), r, z);
+                                                      h->box_end.as<int32_t>(),
+                                                      (learned ? h->sai_off : h->pc_off).as<int64_t>(),
+                                                      (learned ? h->sai_M : h->pc_M).as<c64d>(), r, z);
     FDA_CHECK_LAUNCH();
 }
