@@ -203,6 +203,7 @@ def run_native(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nl0 = F.fda_launch_count()
+    gr0 = P.stats().graph_replays
     clocks.mark("t_begin")
     e0.record(stream)
     for _ in range(args.steps):
@@ -211,6 +212,7 @@ def run_native(args):
     torch.cuda.synchronize()
     clocks.mark("t_end")
     launches = F.fda_launch_count() - nl0
+    graph_replays = P.stats().graph_replays - gr0
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -391,6 +393,7 @@ def run_native(args):
             "e2e": {"value": ws * 1e3 / e2e_ms, "unit": "matvec/s", "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 16 * n},
             "gpu_launches": launches,
+            "cuda_graph_replays": graph_replays,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,

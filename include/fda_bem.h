@@ -78,6 +78,14 @@ typedef struct {
     int tensor_cores;      /* chosen precision: run M2L on the tensor cores (split-bf16 tcgen05 GEMMs, FP32
                               accumulation); 1 (default) or 0 (FP32 SIMT) */
     void *cuda_stream;     /* cudaStream_t, or NULL */
+    int graphs;            /* 1 (default): from the second apply with the same precision, right-hand-side
+                              count and tensor-core switch on, each operator application (fda_apply and
+                              every GMRES product) replays one captured CUDA graph on a library stream
+                              joined to cuda_stream; 0: launch the kernels one by one (timing mode also
+                              does) */
+    int autotune;          /* 1 (default): at setup, time each tensor-core translation batch with 32- and
+                              64-column tiles and 2 and 4 ring stages and keep the fastest (one right-hand
+                              side); 0: fixed rule (32 columns where an operator has few pairs, else 64) */
 } fda_config;
 
 typedef struct {
@@ -105,6 +113,8 @@ typedef struct {
     double precompute_s, tree_s, near_s;
     int64_t level_m2l_pairs[32];  /* per level: M2L (target, source) pairs */
     int32_t level_m2l_ops[32];    /* per level: distinct M2L operators (after the cone symmetry) */
+    int64_t graph_replays;        /* operator applications replayed from captured CUDA graphs so far */
+    int32_t graph_fallback;       /* 1 if a capture failed and the handle launches kernels one by one */
 } fda_stats;
 
 typedef struct fda_handle fda_handle;
@@ -274,7 +284,8 @@ int fda_cone_symmetry_table(int nc, int *rep, int *g);
 
 /* Number of CUDA kernels the library has launched since it was loaded, over
  * all handles and threads (a monotonic counter; the difference around a
- * region is the launches made inside it).  Never fails. */
+ * region is the launches made inside it; a CUDA-graph replay counts the
+ * kernels the graph holds).  Never fails. */
 long long fda_launch_count(void);
 
 /* Message of the last failing call on this handle (never NULL). */

@@ -26,7 +26,8 @@ class fda_config(ctypes.Structure):
                 ("rho_min", ctypes.c_double), ("precision", ctypes.c_int), ("mode", ctypes.c_int),
                 ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("precond", ctypes.c_int),
                 ("alpha_sign", ctypes.c_double), ("max_rhs", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("graphs", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class fda_info(ctypes.Structure):
@@ -43,7 +44,8 @@ class fda_stats(ctypes.Structure):
                 ("level_boxes", ctypes.c_int32 * 32), ("level_cones", ctypes.c_int32 * 32),
                 ("precompute_s", ctypes.c_double), ("tree_s", ctypes.c_double), ("near_s", ctypes.c_double),
                 ("level_m2l_pairs", ctypes.c_int64 * 32),
-                ("level_m2l_ops", ctypes.c_int32 * 32)]
+                ("level_m2l_ops", ctypes.c_int32 * 32), ("graph_replays", ctypes.c_int64),
+                ("graph_fallback", ctypes.c_int32)]
 
 
 class fda_sai_config(ctypes.Structure):

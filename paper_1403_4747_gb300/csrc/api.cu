@@ -20,6 +20,8 @@ void fda_far_convert_f32(fda_handle *h);
 static std::atomic<long long> g_launches{0};
 
 void fda_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void fda_count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long fda_launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void fda_cone_symmetry(int nc, std::vector<int> &rep, std::vector<int> &g);
 
@@ -120,6 +122,8 @@ void fda_default_config(fda_config *c)
     c->max_rhs = 1;
     c->tensor_cores = 1;
     c->cuda_stream = nullptr;
+    c->graphs = 1;
+    c->autotune = 1;
 }
 
 fda_status fda_create(const fda_config *cfg, fda_handle **out)
@@ -132,7 +136,7 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
         c.p_hf < 3 || c.p_hf > 16 || c.hf_nr < 1 || c.hf_na < 8 || !(c.hf_wavelengths > 0) || !(c.rho_min >= 2.0) ||
         (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
         (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.maxit < 1 || c.precond < 0 ||
-        c.precond > 1 || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0) || c.max_rhs < 1 || c.max_rhs > 256 ||
+        c.precond > 1 || (c.graphs != 0 && c.graphs != 1) || (c.autotune != 0 && c.autotune != 1) || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0) || c.max_rhs < 1 || c.max_rhs > 256 ||
         c.tensor_cores < 0 || c.tensor_cores > 1)
         return FDA_ERR_ARG;
     fda_handle *h = new (std::nothrow) fda_handle();
@@ -193,7 +197,10 @@ fda_status fda_precompute_translations(fda_handle *h)
         }
         fda_alloc_densities(h, want32);
         if (h->lev_lo >= 0) fda_build_batches(h);
-        if (want32 && h->cfg.tensor_cores && h->lev_lo >= 0) fda_pack_tc(h);
+        if (want32 && h->cfg.tensor_cores && h->lev_lo >= 0) {
+            fda_pack_tc(h);
+            if (h->cfg.autotune) fda_autotune_tc(h);
+        }
         h->xs.alloc(sizeof(c64d) * h->N * h->cfg.max_rhs);
         h->ys.alloc(sizeof(c64d) * h->N * h->cfg.max_rhs);
         FDA_CUDA(cudaStreamSynchronize(h->stream));
@@ -220,7 +227,7 @@ fda_status fda_apply(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, in
             for (int m = 0; m < nm; ++m)
                 fda_gather_to_sorted(h, reinterpret_cast<const c64d *>(x) + (int64_t)(m0 + m) * ld,
                                      h->xs.as<c64d>() + (int64_t)m * h->N);
-            fda_apply_sorted(h, h->xs.as<c64d>(), h->ys.as<c64d>(), h->cfg.precision, nm);
+            fda_apply_staged(h, h->cfg.precision, nm);
             for (int m = 0; m < nm; ++m)
                 fda_scatter_from_sorted(h, h->ys.as<c64d>() + (int64_t)m * h->N,
                                         reinterpret_cast<c64d *>(y) + (int64_t)(m0 + m) * ld);
@@ -240,14 +247,16 @@ fda_status fda_apply_host(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrh
         return FDA_ERR_ARG;
     }
     return guarded(h, [&] {
-        dbuf dx, dy;
-        dx.alloc(sizeof(c64d) * h->N);
-        dy.alloc(sizeof(c64d) * h->N);
+        if (!h->io_x.p) {
+            h->io_x.alloc(sizeof(c64d) * h->N);
+            h->io_y.alloc(sizeof(c64d) * h->N);
+        }
+        dbuf &dx = h->io_x, &dy = h->io_y;
         for (int m = 0; m < nrhs; ++m) {
             FDA_CUDA(cudaMemcpyAsync(dx.p, x + (int64_t)m * ld, sizeof(c64d) * h->N, cudaMemcpyHostToDevice,
                                      h->stream));
             fda_gather_to_sorted(h, dx.as<c64d>(), h->xs.as<c64d>());
-            fda_apply_sorted(h, h->xs.as<c64d>(), h->ys.as<c64d>(), h->cfg.precision);
+            fda_apply_staged(h, h->cfg.precision, 1);
             fda_scatter_from_sorted(h, h->ys.as<c64d>(), dy.as<c64d>());
             FDA_CUDA(cudaMemcpyAsync(y + (int64_t)m * ld, dy.p, sizeof(c64d) * h->N, cudaMemcpyDeviceToHost,
                                      h->stream));
@@ -360,6 +369,8 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
             if (l < h->nlev) ops += h->lev[l].n_ops;
         }
         out->n_m2l_ops = ops;
+        out->graph_replays = h->graph_replays;
+        out->graph_fallback = h->graphs_broken;
         int rb = h->cfg.precision == FDA_CHOSEN_FP32 ? 8 : 16;
         out->bytes_near = h->nnz_near * rb;
         // far-field flop count (real flops, 8 per complex multiply-add)
@@ -485,6 +496,7 @@ void fda_destroy(fda_handle *h)
     if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
     for (int i = 0; i < 8; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    fda_graphs_release(h);
     delete h;
 }
 

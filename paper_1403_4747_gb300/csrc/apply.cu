@@ -337,3 +337,129 @@ void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, in
         h->pass_ms[4] = t[5];
     }
 }
+
+// ---- tile-shape autotuner for the tensor-core batches
+// For every M2M, M2L and L2L batch, each candidate (columns per tile, ring
+// stages) is run twice on the FP32 densities of one right-hand side (their
+// values do not change the work) and timed with CUDA events on the library
+// stream; the faster candidate of the second runs is kept for one right-hand
+// side.  Runs once, at the end of fda_precompute_translations.
+void fda_autotune_tc(fda_handle *h)
+{
+    if (!h->have_tc || h->lev_lo < 0) return;
+    cudaStream_t s = h->stream;
+    cudaEvent_t e0, e1;
+    FDA_CUDA(cudaEventCreate(&e0));
+    FDA_CUDA(cudaEventCreate(&e1));
+    lvl_ptrs<float> P = make_ptrs<float>(h, h->op32, h->q32, h->p32);
+    static const int cand[4][2] = {{32, 2}, {32, 4}, {64, 2}, {64, 4}};
+    auto tune = [&](tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst, int64_t ds) {
+        if (B.npairs == 0 || !T.A.p) return;
+        float best = 1e30f;
+        for (const auto &c : cand) {
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                FDA_CUDA(cudaEventRecord(e0, s));
+                fda_run_tc(h, B, T, src, sv, reinterpret_cast<c32f *>(dst), 1, ds, c[0], c[1]);
+                FDA_CUDA(cudaEventRecord(e1, s));
+                FDA_CUDA(cudaEventSynchronize(e1));
+                FDA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (ms < best) {
+                best = ms;
+                T.nc_tuned = c[0];
+                T.st_tuned = c[1];
+            }
+        }
+    };
+    auto sv = [&](int l) { return P.stride[l] / std::max(1, h->lev[l].T); };
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        if (h->lev[l].T == 0) continue;
+        tune(h->b_m2l[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<float *>(P.p[l]), P.stride[l]);
+        if (l + 1 < h->nlev && h->lev[l + 1].T > 0) {
+            tune(h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], sv(l + 1), reinterpret_cast<float *>(P.q[l]), P.stride[l]);
+            tune(h->b_l2l[l], h->tc_l2l[l], h->ps[l], sv(l), reinterpret_cast<float *>(P.p[l + 1]), P.stride[l + 1]);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (fda_tc_error(h)) fda_fail(FDA_ERR_TIMEOUT, "a tensor-core translation gave up waiting on its copies");
+}
+
+// ---- one CUDA graph per operator application
+// The first apply with a given (precision, right-hand sides, tensor-core
+// switch) runs eagerly, which also cuts the tiles and sizes every buffer the
+// apply touches; the second captures the same launch sequence on the
+// handle's private stream; later ones replay it.  The graph reads h->xs and
+// writes h->ys.  A capture that fails falls back to eager launches for good.
+void fda_apply_staged(fda_handle *h, int precision, int mr)
+{
+    const c64d *xs = h->xs.as<c64d>();
+    c64d *ys = h->ys.as<c64d>();
+    if (h->timing || !h->cfg.graphs || h->graphs_broken) {
+        fda_apply_sorted(h, xs, ys, precision, mr);
+        return;
+    }
+    const int key = precision | (h->cfg.tensor_cores << 1) | (mr << 2);
+    fda_handle::apply_graph *g = nullptr;
+    for (auto &e : h->graphs)
+        if (e.key == key) g = &e;
+    if (!g) {
+        fda_apply_sorted(h, xs, ys, precision, mr);
+        h->graphs.push_back(fda_handle::apply_graph{key, nullptr, 0});
+        return;
+    }
+    if (!h->gstream) {
+        FDA_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+        FDA_CUDA(cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming));
+        FDA_CUDA(cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming));
+    }
+    if (!g->exec) {
+        cudaStream_t user = h->stream;
+        cudaGraph_t graph = nullptr;
+        FDA_CUDA(cudaStreamSynchronize(user));
+        h->stream = h->gstream;
+        bool ok = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        const long long n0 = fda_launches_so_far();
+        if (ok) {
+            try {
+                fda_apply_sorted(h, xs, ys, precision, mr);
+            } catch (...) {
+                ok = false;
+            }
+            // the captured launches were counted but did not run
+            g->kernels = fda_launches_so_far() - n0;
+            fda_count_launches(-g->kernels);
+            ok = (cudaStreamEndCapture(h->gstream, &graph) == cudaSuccess) && ok && graph;
+        }
+        h->stream = user;
+        if (ok) ok = cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            (void)cudaGetLastError();
+            g->exec = nullptr;
+            h->graphs_broken = 1;
+            fda_apply_sorted(h, xs, ys, precision, mr);
+            return;
+        }
+    }
+    FDA_CUDA(cudaEventRecord(h->gev[0], h->stream));
+    FDA_CUDA(cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
+    FDA_CUDA(cudaGraphLaunch(g->exec, h->gstream));
+    ++h->graph_replays;
+    fda_count_launches(g->kernels);
+    FDA_CUDA(cudaEventRecord(h->gev[1], h->gstream));
+    FDA_CUDA(cudaStreamWaitEvent(h->stream, h->gev[1], 0));
+}
+
+void fda_graphs_release(fda_handle *h)
+{
+    if (h->gstream) cudaStreamSynchronize(h->gstream);
+    for (auto &e : h->graphs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    h->graphs.clear();
+    for (int i = 0; i < 2; ++i)
+        if (h->gev[i]) cudaEventDestroy(h->gev[i]);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
+    h->gstream = nullptr;
+}

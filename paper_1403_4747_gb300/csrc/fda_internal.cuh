@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "../../include/fda_bem.h"
@@ -63,8 +64,11 @@ struct fda_error {
 // FDA_DEBUG_SYNC=1 in the environment makes every launch check synchronous,
 // so that a failing kernel is reported at its own launch site.
 int fda_debug_sync();
-// counts every kernel launch of the library (one check follows each launch)
+// counts every kernel launch of the library (one check follows each launch;
+// a graph replay adds the kernels it holds)
 void fda_count_launch();
+void fda_count_launches(long long n);
+long long fda_launches_so_far();
 #define FDA_CHECK_LAUNCH()                                                                    \
     do {                                                                                      \
         fda_count_launch();                                                                   \
@@ -131,26 +135,32 @@ struct level_info {
 
 // one batched-translation launch: tiles of (operator, pair range, row block)
 // and (source offset, target offset) pairs, grouped by operator
+// tiles of a batch cut for one (right-hand sides, columns per tile); kept
+// until the handle is destroyed, because captured graphs point into them
+struct tile_set {
+    int mr = 0, nc = 0, n = 0;
+    dbuf buf;
+};
+
 struct tr_batch {
-    dbuf tiles, pairs;
-    int ntiles = 0;
-    int np = 32;          // columns (pair x right-hand side) per tile (32 or 64)
+    dbuf pairs;
     int tm = 64;          // output rows per tile (32 or 64)
     int tout = 0;         // output rank
-    int mr = 0;           // right-hand sides the current tiles were cut for
     int64_t npairs = 0;
     std::vector<int> op_start;  // pairs of operator o: [op_start[o], op_start[o+1])
+    std::deque<tile_set> tilesets;  // columns per tile: 64 if an operator averages >= 48, else 32
 };
 
 // tensor-core form of one translation batch: the operators as bf16 hi/lo
 // panels (64 complex output rows x 32 complex input columns per panel) and the
 // tiles cut for the current number of right-hand sides
 struct tc_ops {
-    dbuf A, tiles;
+    dbuf A;
     int Tout = 0, Tin = 0;
     int nrt = 0, nkc = 0;     // row tiles (64 complex rows), K stages (32 complex columns)
     int64_t op_bytes = 0;
-    int ntiles = 0, tiles_mr = 0, tiles_nc = 0;
+    std::deque<tile_set> tilesets;
+    int nc_tuned = 0, st_tuned = 0;  // autotuner's choice for one right-hand side (0 = rule)
 };
 
 template <typename T>
@@ -249,6 +259,19 @@ struct fda_handle {
     // learned SAI preconditioner on the same pattern (set by fda_sai_set)
     dbuf sai_M, sai_off;
 
+    // captured applies (one CUDA graph per precision, right-hand sides and
+    // tensor-core switch), replayed on gstream joined to stream by events
+    struct apply_graph {
+        int key;
+        cudaGraphExec_t exec;
+        long long kernels;  // kernel launches captured in it
+    };
+    std::vector<apply_graph> graphs;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {};
+    int graphs_broken = 0;
+    int64_t graph_replays = 0;
+
     // timing
     int timing = 0;
     cudaEvent_t ev[8] = {};
@@ -259,6 +282,7 @@ struct fda_handle {
     dbuf work64;               // general FP64 workspace (x staging etc.)
     dbuf xs, ys;               // sorted-order staging vectors (complex double)
     dbuf xs32;                 // sorted-order complex float staging
+    dbuf io_x, io_y;           // device copies of host vectors (fda_apply_host)
     dbuf solve_ws;             // GMRES basis
     dbuf red;                  // reduction scratch
 };
@@ -271,6 +295,9 @@ void fda_tree_build(fda_handle *h);
 void fda_near_build(fda_handle *h);
 void fda_far_precompute(fda_handle *h);
 void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, int mr = 1);
+// h->ys = A h->xs (sorted order, mr right-hand sides) through the graph cache
+void fda_apply_staged(fda_handle *h, int precision, int mr);
+void fda_graphs_release(fda_handle *h);
 void fda_rhs_sorted(fda_handle *h, const double *dirs_dev, int nrhs, c64d *b_sorted);
 void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
@@ -295,7 +322,9 @@ void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr);
 // split densities of the source level (svstride vectors per right-hand
 // side), dst the FP32 densities of the target level (dstride elements each)
 void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t svstride, c32f *dst, int mr,
-                int64_t dstride);
+                int64_t dstride, int nc = 0, int st = 0);
+// time the tile shapes of every tensor-core batch once and keep the fastest
+void fda_autotune_tc(fda_handle *h);
 int fda_tc_error(fda_handle *h);
 template <typename R>
 void fda_run_batch(tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R> *src, cx<R> *dst, int mr,

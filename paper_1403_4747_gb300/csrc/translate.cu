@@ -138,28 +138,33 @@ void make_batch(std::vector<pair_rec> &pr, int nops, int Tout, tr_batch &B)
     B.npairs = (int64_t)pairs.size();
     B.pairs.alloc(sizeof(int2) * std::max<size_t>(pairs.size(), 1));
     if (!pairs.empty()) FDA_CUDA(cudaMemcpy(B.pairs.p, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice));
-    B.mr = 0;
+    B.tilesets.clear();
 }
 
 // tiles for mr right-hand sides: each operator's pairs x mr columns, cut
 // into NP-column, TM-row tiles
-void ensure_tiles(tr_batch &B, int mr)
+const tile_set &ensure_tiles(tr_batch &B, int mr)
 {
-    if (B.mr == mr) return;
+    for (const auto &t : B.tilesets)
+        if (t.mr == mr) return t;
     const int nops = (int)B.op_start.size() - 1;
     double avg = B.npairs == 0 ? 0.0 : (double)B.npairs * mr / std::max(1, nops);
-    B.np = avg >= 48.0 ? 64 : 32;
+    const int np = avg >= 48.0 ? 64 : 32;
     std::vector<tr_tile> tiles;
     for (int o = 0; o < nops; ++o) {
         int a = B.op_start[o] * mr, b = B.op_start[o + 1] * mr;
-        for (int p0 = a; p0 < b; p0 += B.np)
-            for (int r0 = 0; r0 < B.tout; r0 += B.tm) tiles.push_back(tr_tile{o, p0, std::min(B.np, b - p0), r0});
+        for (int p0 = a; p0 < b; p0 += np)
+            for (int r0 = 0; r0 < B.tout; r0 += B.tm) tiles.push_back(tr_tile{o, p0, std::min(np, b - p0), r0});
     }
-    B.ntiles = (int)tiles.size();
-    B.tiles.alloc(sizeof(tr_tile) * std::max<size_t>(tiles.size(), 1));
+    B.tilesets.emplace_back();
+    tile_set &t = B.tilesets.back();
+    t.mr = mr;
+    t.nc = np;
+    t.n = (int)tiles.size();
+    t.buf.alloc(sizeof(tr_tile) * std::max<size_t>(tiles.size(), 1));
     if (!tiles.empty())
-        FDA_CUDA(cudaMemcpy(B.tiles.p, tiles.data(), sizeof(tr_tile) * tiles.size(), cudaMemcpyHostToDevice));
-    B.mr = mr;
+        FDA_CUDA(cudaMemcpy(t.buf.p, tiles.data(), sizeof(tr_tile) * tiles.size(), cudaMemcpyHostToDevice));
+    return t;
 }
 
 }  // namespace
@@ -219,17 +224,17 @@ void fda_run_batch(tr_batch &B, const cx<R> *ops, int Tout, int Tin, const cx<R>
                    int64_t sstride, int64_t dstride, cudaStream_t s)
 {
     if (B.npairs == 0) return;
-    ensure_tiles(B, mr);
-    const tr_tile *t = B.tiles.as<tr_tile>();
+    const tile_set &ts = ensure_tiles(B, mr);
+    const tr_tile *t = ts.buf.as<tr_tile>();
     const int2 *pr = B.pairs.as<int2>();
-    if (B.tm == 64 && B.np == 64)
-        k_btr<R, 64, 64><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
+    if (B.tm == 64 && ts.nc == 64)
+        k_btr<R, 64, 64><<<ts.n, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
     else if (B.tm == 64)
-        k_btr<R, 64, 32><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
-    else if (B.np == 64)
-        k_btr<R, 32, 64><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
+        k_btr<R, 64, 32><<<ts.n, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
+    else if (ts.nc == 64)
+        k_btr<R, 32, 64><<<ts.n, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
     else
-        k_btr<R, 32, 32><<<B.ntiles, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
+        k_btr<R, 32, 32><<<ts.n, BT, 0, s>>>(t, pr, ops, Tout, Tin, src, dst, mr, sstride, dstride);
     FDA_CHECK_LAUNCH();
 }
 

@@ -483,6 +483,8 @@ void fda_pack_tc(fda_handle *h)
         const size_t Tp = (size_t)((L.T + KC - 1) / KC) * KC;
         h->qs[l].alloc(sizeof(__nv_bfloat16) * nvec * 4 * Tp);
         h->ps[l].alloc(sizeof(__nv_bfloat16) * nvec * 4 * Tp);
+        FDA_CUDA(cudaMemsetAsync(h->qs[l].p, 0, h->qs[l].bytes, h->stream));
+        FDA_CUDA(cudaMemsetAsync(h->ps[l].p, 0, h->ps[l].bytes, h->stream));
     }
     h->tc_err.alloc(sizeof(int));
     FDA_CUDA(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), h->stream));
@@ -502,35 +504,51 @@ void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr)
 }
 
 void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t svstride, c32f *dst, int mr,
-                int64_t dstride)
+                int64_t dstride, int nc, int st)
 {
     if (B.npairs == 0) return;
     if (!P.A.p) fda_fail(FDA_ERR_STATE, "tensor-core operators missing for a nonempty translation batch");
     const int nops = (int)B.op_start.size() - 1;
     const double avg_cols = (double)B.npairs * mr / std::max(1, nops);
-    // narrow tiles where an operator has few pairs (less padding, more CTAs per SM)
-    const int NC = avg_cols < 48.0 ? 32 : 64;
-    if (P.tiles_nc != NC || P.tiles_mr != mr) {
+    // tile width and stage count: the caller's, else the tuned ones (one
+    // right-hand side), else narrow tiles where an operator has few columns
+    int NC = avg_cols < 48.0 ? 32 : 64, ST = 4;
+    if (mr == 1 && P.nc_tuned) {
+        NC = P.nc_tuned;
+        ST = P.st_tuned;
+    }
+    if (nc) NC = nc;
+    if (st) ST = st;
+    const tile_set *ts = nullptr;
+    for (const auto &t : P.tilesets)
+        if (t.mr == mr && t.nc == NC) ts = &t;
+    if (!ts) {
         std::vector<tc_tile> tiles;
         for (int o = 0; o < nops; ++o) {
             int a = B.op_start[o] * mr, b = B.op_start[o + 1] * mr;
             for (int p0 = a; p0 < b; p0 += NC)
                 for (int rt = 0; rt < P.nrt; ++rt) tiles.push_back(tc_tile{o, p0, std::min(NC, b - p0), rt});
         }
-        P.ntiles = (int)tiles.size();
-        P.tiles.alloc(sizeof(tc_tile) * std::max<size_t>(tiles.size(), 1));
+        P.tilesets.emplace_back();
+        tile_set &t = P.tilesets.back();
+        t.mr = mr;
+        t.nc = NC;
+        t.n = (int)tiles.size();
+        t.buf.alloc(sizeof(tc_tile) * std::max<size_t>(tiles.size(), 1));
         if (!tiles.empty())
-            FDA_CUDA(cudaMemcpy(P.tiles.p, tiles.data(), sizeof(tc_tile) * tiles.size(), cudaMemcpyHostToDevice));
-        P.tiles_mr = mr;
-        P.tiles_nc = NC;
+            FDA_CUDA(cudaMemcpy(t.buf.p, tiles.data(), sizeof(tc_tile) * tiles.size(), cudaMemcpyHostToDevice));
+        ts = &t;
     }
-    if (P.ntiles == 0) return;
-    tc_args a{P.tiles.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.Tout, P.Tin,
+    if (ts->n == 0) return;
+    tc_args a{ts->buf.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.Tout, P.Tin,
               src.as<__nv_bfloat16>(), dst, mr, svstride, dstride, h->tc_err.as<int>()};
-    // four stage buffers (one CTA per SM holds the 8 NC accumulator columns
-    // of NC = 64; NC = 32 fits two)
-    if (NC == 32) launch_tc<32, 4>(a, P.ntiles, h->stream);
-    else launch_tc<64, 4>(a, P.ntiles, h->stream);
+    if (NC == 32) {
+        if (ST == 2) launch_tc<32, 2>(a, ts->n, h->stream);
+        else launch_tc<32, 4>(a, ts->n, h->stream);
+    } else {
+        if (ST == 2) launch_tc<64, 2>(a, ts->n, h->stream);
+        else launch_tc<64, 4>(a, ts->n, h->stream);
+    }
     FDA_CHECK_LAUNCH();
 }
 

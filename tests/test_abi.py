@@ -38,12 +38,12 @@ def test_default_config(lib):
     from paper_1403_4747_gb300 import fda_default_config
     c = fda_default_config()
     assert c.eps == 1e-4 and c.leaf_max == 64 and c.p_lf == 8 and c.restart == 100
-    assert c.precision == 0 and c.mode == 0
+    assert c.precision == 0 and c.mode == 0 and c.graphs == 1 and c.autotune == 1
 
 
 @pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", 0.5), ("leaf_max", 0), ("leaf_max", 65),
                                          ("p_lf", 2), ("precision", 3), ("mode", 7), ("restart", 0),
-                                         ("rho_min", 1.0)])
+                                         ("rho_min", 1.0), ("graphs", 2), ("autotune", 3), ("precond", 2)])
 def test_invalid_config_rejected_without_gpu(lib, field, value):
     from paper_1403_4747_gb300 import fda_default_config, fda_create, FDAError, FDA_ERR_ARG
     c = fda_default_config(**{field: value})
