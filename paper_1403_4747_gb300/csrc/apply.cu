@@ -339,8 +339,8 @@ void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, in
 }
 
 // ---- tile-shape autotuner for the tensor-core batches
-// For every M2M, M2L and L2L batch, each candidate (columns per tile, ring
-// stages) is run twice on the FP32 densities of one right-hand side (their
+// For every M2M, M2L and L2L batch, each candidate (columns per tile, row
+// tiles per tile, ring stages) is run twice on the FP32 densities of one right-hand side (their
 // values do not change the work) and timed with CUDA events on the library
 // stream; the faster candidate of the second runs is kept for one right-hand
 // side.  Runs once, at the end of fda_precompute_translations.
@@ -352,15 +352,17 @@ void fda_autotune_tc(fda_handle *h)
     FDA_CUDA(cudaEventCreate(&e0));
     FDA_CUDA(cudaEventCreate(&e1));
     lvl_ptrs<float> P = make_ptrs<float>(h, h->op32, h->q32, h->p32);
-    static const int cand[4][2] = {{32, 2}, {32, 4}, {64, 2}, {64, 4}};
+    // (columns, row tiles, stages)
+    static const int cand[6][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4}, {64, 2, 3}};
     auto tune = [&](tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst, int64_t ds) {
         if (B.npairs == 0 || !T.A.p) return;
         float best = 1e30f;
         for (const auto &c : cand) {
+            if (c[1] > T.nrt) continue;
             float ms = 0.0f;
             for (int rep = 0; rep < 2; ++rep) {
                 FDA_CUDA(cudaEventRecord(e0, s));
-                fda_run_tc(h, B, T, src, sv, reinterpret_cast<c32f *>(dst), 1, ds, c[0], c[1]);
+                fda_run_tc(h, B, T, src, sv, reinterpret_cast<c32f *>(dst), 1, ds, c[0], c[1], c[2]);
                 FDA_CUDA(cudaEventRecord(e1, s));
                 FDA_CUDA(cudaEventSynchronize(e1));
                 FDA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -368,7 +370,8 @@ void fda_autotune_tc(fda_handle *h)
             if (ms < best) {
                 best = ms;
                 T.nc_tuned = c[0];
-                T.st_tuned = c[1];
+                T.r_tuned = c[1];
+                T.st_tuned = c[2];
             }
         }
     };

@@ -138,7 +138,7 @@ struct level_info {
 // tiles of a batch cut for one (right-hand sides, columns per tile); kept
 // until the handle is destroyed, because captured graphs point into them
 struct tile_set {
-    int mr = 0, nc = 0, n = 0;
+    int mr = 0, nc = 0, rows = 1, n = 0;  // right-hand sides, columns and row tiles per tile, tiles
     dbuf buf;
 };
 
@@ -160,7 +160,7 @@ struct tc_ops {
     int nrt = 0, nkc = 0;     // row tiles (64 complex rows), K stages (32 complex columns)
     int64_t op_bytes = 0;
     std::deque<tile_set> tilesets;
-    int nc_tuned = 0, st_tuned = 0;  // autotuner's choice for one right-hand side (0 = rule)
+    int nc_tuned = 0, r_tuned = 1, st_tuned = 0;  // autotuner's choice for one right-hand side (0 = rule)
 };
 
 template <typename T>
@@ -322,7 +322,7 @@ void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr);
 // split densities of the source level (svstride vectors per right-hand
 // side), dst the FP32 densities of the target level (dstride elements each)
 void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t svstride, c32f *dst, int mr,
-                int64_t dstride, int nc = 0, int st = 0);
+                int64_t dstride, int nc = 0, int rows = 0, int st = 0);
 // time the tile shapes of every tensor-core batch once and keep the fastest
 void fda_autotune_tc(fda_handle *h);
 int fda_tc_error(fda_handle *h);

@@ -10,15 +10,16 @@
 //     Cr = D1_top - D2_bottom,  Ci = D2_top + D1_bottom.
 // Each FP32 value is split into two bf16 numbers, x = x_hi + x_lo, and the
 // products A_hi B_hi + A_hi B_lo + A_lo B_hi are taken with FP32 accumulation
-// in tensor memory (about 16 significant bits per operand) as two MMAs per
-// 16 of K: A_hi [B_hi B_lo] (N = 4 NC) and A_lo B_hi (N = 2 NC, added to the
-// first half); the epilogue adds the B_lo half to the B_hi half.
+// in tensor memory (about 16 significant bits per operand) as three MMAs per
+// 16 of K, each with N = 2 NC.  A CTA tile covers R consecutive 64-row tiles
+// of one operator, so every density column gathered into shared memory
+// serves R row tiles.
 //
 // Operands in shared memory use the tcgen05 K-major layout without swizzle:
 // 8-row x 16-byte core matrices, LBO = 128 B between core matrices along K,
 // SBO = 512 B between 8-row groups (32 complex columns of K per stage); the
 // B panels Br hi, Bi hi, Br lo, Bi lo follow one another, so [Br Bi] hi and
-// the whole [Br Bi hi | Br Bi lo] are single operands of 2 NC and 4 NC rows.
+// [Br Bi] lo are single operands of 2 NC rows.
 // The operator panels are stored in HBM already in that layout (built once in
 // setup) and copied to shared memory with cp.async.bulk on an mbarrier; the
 // densities, split into bf16 once per level, are gathered column by column
@@ -39,7 +40,7 @@ constexpr int ABYTES = 128 * KC * 2;  // one bf16 operand panel stage (hi or lo)
 constexpr long long SPIN = 20000000;  // bounded mbarrier polls
 
 struct tc_tile {
-    int op, pair0, npair, rt;     // operator, first column, columns, row tile (64 complex rows)
+    int op, pair0, npair, rt;     // operator, first column, columns, first row tile (64 complex rows)
 };
 
 __device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -96,17 +97,19 @@ __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv
 // Persistent, warp-specialised form.  CTA c takes tiles c, c + grid,
 // c + 2 grid, ...; its warps split the work of every tile:
 //   warps 5-7 (producers): load stage g of the CTA into ring buffer g % ST:
-//       the operator panel by one bulk copy, the tile's density columns (256
-//       contiguous bytes each) by 16-byte cp.async copies (zero fill for
-//       columns with no pair); full[b] completes when all of them have landed
-//       (arrival count = 96 producer threads + 1 for the byte count);
+//       the operator panels of the tile's row tiles by one bulk copy each,
+//       the tile's density columns (256 contiguous bytes each) by 16-byte
+//       cp.async copies (zero fill for columns with no pair); full[b]
+//       completes when all of them have landed (arrival count = 96 producer
+//       threads + 1 for the byte count);
 //   warp 4 (MMA): one thread issues the stage's MMAs into the tile's
-//       accumulator slot and commits them to empty[b] (frees the buffer) and,
-//       after the tile's last stage, to accf[slot];
+//       accumulator slot (R row tiles x [D1 D2]) and commits them to
+//       empty[b] (frees the buffer) and, after the tile's last stage, to
+//       accf[slot];
 //   warps 0-3 (epilogue, one warp per TMEM lane quarter): read the slot,
 //       combine real and imaginary parts and add the result to the targets,
 //       then arrive on acce[slot] (count 128) so the slot can be reused.
-// Two accumulator slots (4 NC TMEM columns each) let the epilogue of tile j
+// Two accumulator slots (2 R NC TMEM columns each) let the epilogue of tile j
 // overlap the MMAs of tile j + 1.  Every wait is bounded and also gives up
 // once another role has recorded an error; the CTA then waits (bounded) for
 // its copies and MMAs in flight, frees its tensor memory and returns.
@@ -158,19 +161,22 @@ __device__ inline bool bar_any(int id, int n, bool pred)
     return r != 0;
 }
 
-template <int NC, int ST>
+template <int NC, int R, int ST>
 __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int ntiles, const int2 *pairs,
-                                                        const uint8_t *opsA, int64_t op_bytes, int nkc, int Tout,
-                                                        int Tin, const __nv_bfloat16 *qb, c32f *dst, int mr,
+                                                        const uint8_t *opsA, int64_t op_bytes, int nkc, int nrt,
+                                                        int Tout, int Tin, const __nv_bfloat16 *qb, c32f *dst, int mr,
                                                         int64_t svstride, int64_t dstride, int *err)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     // 128-byte aligned base inside the dynamic allocation (launched with 128 extra)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    constexpr int BB = NC * KC * 2;            // bytes of one B panel (Br or Bi, hi or lo)
-    constexpr int STAGE = 2 * ABYTES + 4 * BB; // A hi, A lo, Br hi, Bi hi, Br lo, Bi lo
+    constexpr int BB = NC * KC * 2;                // bytes of one B panel (Br or Bi, hi or lo)
+    constexpr int AR = R * 2 * ABYTES;             // A hi, A lo of each of the R row tiles
+    constexpr int STAGE = AR + 4 * BB;             // then Br hi, Bi hi, Br lo, Bi lo
+    constexpr int SLOT = R * 2 * NC;               // TMEM columns of one accumulator slot
     float2 *stg = reinterpret_cast<float2 *>(smem + ST * STAGE);  // epilogue staging [EPC][128 lanes]
     __shared__ long long srcv[NC];             // producers: source vector per column of the current tile
+    __shared__ int stage_nr[ST];               // row tiles present in the tile of each stage
     __shared__ long long tgt[NC];              // epilogue: target offset per column of the current tile
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) uint64_t full[ST], empty[ST], accf[2], acce[2];
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(8 * NC));
+                     "r"(2 * SLOT));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -221,6 +227,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                 srcv[c] = v;
             }
             asm volatile("bar.sync 1, %0;" ::"r"(NPROD));
+            const int nr = min(R, nrt - t.rt);  // row tiles of this tile
             const uint8_t *gA = opsA + (int64_t)t.op * op_bytes + (int64_t)t.rt * nkc * 2 * ABYTES;
             for (int s = 0; s < nkc; ++s, ++g) {
                 const int b = g % ST;
@@ -234,12 +241,15 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                 uint8_t *st = smem + b * STAGE;
                 const uint32_t fb = smem_u32(&full[b]);
                 if (tp == 0) {
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * ABYTES));
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            smem_u32(st)),
-                        "l"(gA + (int64_t)s * 2 * ABYTES), "r"(2 * ABYTES), "r"(fb)
-                        : "memory");
+                    stage_nr[b] = nr;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                 "r"(nr * 2 * ABYTES));
+                    for (int r = 0; r < nr; ++r)
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                smem_u32(st + r * 2 * ABYTES)),
+                            "l"(gA + ((int64_t)r * nkc + s) * 2 * ABYTES), "r"(2 * ABYTES), "r"(fb)
+                            : "memory");
                     n_issued = g + 1;
                 }
                 // 16 copies of 16 bytes per column: panel part = c16 / 4 (Re hi, Im hi,
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                         bytes = 16;
                     }
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
-                                     smem_u32(st + 2 * ABYTES + part * BB + core_off(n, gq * 8))),
+                                     smem_u32(st + AR + part * BB + core_off(n, gq * 8))),
                                  "l"(srcp), "r"(bytes)
                                  : "memory");
                 }
@@ -266,10 +276,8 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
     } else if (warp == 4) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
-            // bf16 x bf16 -> f32, K-major A and B, M = 128, N = 4 NC or 2 NC
-            const uint32_t idesc_all =
-                (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((4 * NC) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-            const uint32_t idesc_hi =
+            // bf16 x bf16 -> f32, K-major A and B, M = 128, N = 2 NC
+            const uint32_t idesc =
                 (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * NC) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
             int g = 0;
             bool ok = true;
@@ -281,7 +289,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t d = tmem + slot * 4 * NC;
+                const uint32_t dslot = tmem + slot * SLOT;
                 for (int s = 0; s < nkc; ++s, ++g) {
                     const int b = g % ST;
                     if (!mbar_wait_ab(smem_u32(&full[b]), (g / ST) & 1, abort_v)) {
@@ -292,16 +300,24 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                     }
                     asm volatile("fence.proxy.async.shared::cta;");
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t aHi = smem_u32(smem + b * STAGE), aLo = aHi + ABYTES, bAll = aHi + 2 * ABYTES;
-                    for (int k = 0; k < KC / 16; ++k) {
-                        const uint32_t so = k * 256;  // two core matrices along K per k-step
-                        const uint32_t en = (s > 0 || k > 0) ? 1u : 0u;
-                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                                     "l"(smem_desc(aHi + so)), "l"(smem_desc(bAll + so)), "r"(idesc_all), "r"(en));
-                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                                     "l"(smem_desc(aLo + so)), "l"(smem_desc(bAll + so)), "r"(idesc_hi), "r"(1u));
+                    const int nr = stage_nr[b];
+                    const uint32_t base = smem_u32(smem + b * STAGE);
+                    const uint32_t bHi = base + AR, bLo = bHi + 2 * BB;
+                    for (int r = 0; r < nr; ++r) {
+                        const uint32_t aHi = base + r * 2 * ABYTES, aLo = aHi + ABYTES, d = dslot + r * 2 * NC;
+                        for (int k = 0; k < KC / 16; ++k) {
+                            const uint32_t so = k * 256;  // two core matrices along K per k-step
+                            const uint32_t en = (s > 0 || k > 0) ? 1u : 0u;
+                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                                         "l"(smem_desc(aHi + so)), "l"(smem_desc(bHi + so)), "r"(idesc), "r"(en));
+                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                                         "l"(smem_desc(aHi + so)), "l"(smem_desc(bLo + so)), "r"(idesc), "r"(1u));
+                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                                         "l"(smem_desc(aLo + so)), "l"(smem_desc(bHi + so)), "r"(idesc), "r"(1u));
+                        }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&empty[b])));
@@ -341,30 +357,31 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // columns of the slot: [0, NC) Br hi, [NC, 2 NC) Bi hi, [2 NC, 3 NC) Br lo, [3 NC, 4 NC) Bi lo
-            const uint32_t d1 = tmem + slot * 4 * NC + ((uint32_t)(warp * 32) << 16), d2 = d1 + NC;
-            const int rowg = t.rt * 64 + row;
-            for (int c0 = 0; c0 < NC; c0 += EPC) {
-                uint32_t v1[16], v2[16], w1[16], w2[16];
-                tmem_ld16x2(d1 + c0, d2 + c0, v1, v2);
-                tmem_ld16x2(d1 + 2 * NC + c0, d2 + 2 * NC + c0, w1, w2);
+            // row tile r of the slot: columns [2 r NC, 2 r NC + NC) hold D1, the next NC D2
+            const int nr = min(R, nrt - t.rt);
+            for (int r = 0; r < nr; ++r) {
+                const uint32_t d1 = tmem + slot * SLOT + r * 2 * NC + ((uint32_t)(warp * 32) << 16), d2 = d1 + NC;
+                const int rowg = (t.rt + r) * 64 + row;
+                for (int c0 = 0; c0 < NC; c0 += EPC) {
+                    uint32_t v1[16], v2[16];
+                    tmem_ld16x2(d1 + c0, d2 + c0, v1, v2);
 #pragma unroll
-                for (int jj = 0; jj < EPC; ++jj)
-                    stg[jj * 128 + tid] = make_float2(__uint_as_float(v1[jj]) + __uint_as_float(w1[jj]),
-                                                      __uint_as_float(v2[jj]) + __uint_as_float(w2[jj]));
-                asm volatile("bar.sync 2, 128;");
-                if (rowg < Tout) {
+                    for (int jj = 0; jj < EPC; ++jj)
+                        stg[jj * 128 + tid] = make_float2(__uint_as_float(v1[jj]), __uint_as_float(v2[jj]));
+                    asm volatile("bar.sync 2, 128;");
+                    if (rowg < Tout) {
 #pragma unroll
-                    for (int jj = half * (EPC / 2); jj < (half + 1) * (EPC / 2); ++jj) {
-                        const int n = c0 + jj;
-                        if (n < t.npair) {
-                            const float2 top = stg[jj * 128 + row], bot = stg[jj * 128 + 64 + row];
-                            atomicAdd(reinterpret_cast<float2 *>(dst + tgt[n] + rowg),
-                                      make_float2(top.x - bot.y, top.y + bot.x));
+                        for (int jj = half * (EPC / 2); jj < (half + 1) * (EPC / 2); ++jj) {
+                            const int n = c0 + jj;
+                            if (n < t.npair) {
+                                const float2 top = stg[jj * 128 + row], bot = stg[jj * 128 + 64 + row];
+                                atomicAdd(reinterpret_cast<float2 *>(dst + tgt[n] + rowg),
+                                          make_float2(top.x - bot.y, top.y + bot.x));
+                            }
                         }
                     }
+                    asm volatile("bar.sync 2, 128;");
                 }
-                asm volatile("bar.sync 2, 128;");
             }
             // this slot is read: the MMAs of tile j + 2 may overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -380,7 +397,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
     if (*abort_v && nc > 0 && tid == 0) mbar_wait(smem_u32(&empty[(nc - 1) % ST]), ((nc - 1) / ST) & 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * NC));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SLOT));
 }
 
 // operator panels: per operator, per row tile (64 complex rows), per stage
@@ -422,7 +439,7 @@ struct tc_args {
     const int2 *pairs;
     const uint8_t *A;
     int64_t op_bytes;
-    int nkc, Tout, Tin;
+    int nkc, nrt, Tout, Tin;
     const __nv_bfloat16 *qb;
     c32f *dst;
     int mr;
@@ -430,24 +447,25 @@ struct tc_args {
     int *err;
 };
 
-template <int NC, int ST>
+template <int NC, int R, int ST>
 void launch_tc(const tc_args &a, int ntiles, cudaStream_t s)
 {
-    const size_t stage = 2 * (size_t)ABYTES + 4 * (size_t)NC * KC * 2;
+    const size_t stage = (size_t)R * 2 * ABYTES + 4 * (size_t)NC * KC * 2;
     const size_t smem = 128 + ST * stage + (size_t)EPC * 128 * sizeof(float2);
     static int per_sm = 0, nsm = 0;  // resident CTAs per SM for this instantiation
     if (!per_sm) {
         int dev = 0;
         FDA_CUDA(cudaGetDevice(&dev));
         FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<NC, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        FDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_btr_tc<NC, ST>, WS_THREADS, smem));
-        per_sm = std::min(per_sm, 512 / (8 * NC));  // tensor memory: 8 NC columns per CTA
+        FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<NC, R, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_btr_tc<NC, R, ST>, WS_THREADS, smem));
+        per_sm = std::min(per_sm, 512 / (4 * R * NC));  // tensor memory: two slots of 2 R NC columns per CTA
         if (per_sm < 1) fda_fail(FDA_ERR_CUDA, "tensor-core translation kernel does not fit on an SM");
     }
     const int grid = std::min(ntiles, per_sm * nsm);
-    k_btr_tc<NC, ST><<<grid, WS_THREADS, smem, s>>>(a.tiles, ntiles, a.pairs, a.A, a.op_bytes, a.nkc, a.Tout, a.Tin,
-                                                    a.qb, a.dst, a.mr, a.svstride, a.dstride, a.err);
+    k_btr_tc<NC, R, ST><<<grid, WS_THREADS, smem, s>>>(a.tiles, ntiles, a.pairs, a.A, a.op_bytes, a.nkc, a.nrt,
+                                                       a.Tout, a.Tin, a.qb, a.dst, a.mr, a.svstride, a.dstride,
+                                                       a.err);
 }
 
 void pack_one(fda_handle *h, tc_ops &P, const tr_batch &B, const dbuf &ops64, int nops, int Tout, int Tin)
@@ -504,35 +522,40 @@ void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr)
 }
 
 void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t svstride, c32f *dst, int mr,
-                int64_t dstride, int nc, int st)
+                int64_t dstride, int nc, int rows, int st)
 {
     if (B.npairs == 0) return;
     if (!P.A.p) fda_fail(FDA_ERR_STATE, "tensor-core operators missing for a nonempty translation batch");
     const int nops = (int)B.op_start.size() - 1;
     const double avg_cols = (double)B.npairs * mr / std::max(1, nops);
-    // tile width and stage count: the caller's, else the tuned ones (one
-    // right-hand side), else narrow tiles where an operator has few columns
-    int NC = avg_cols < 48.0 ? 32 : 64, ST = 4;
+    // tile shape (columns, row tiles, ring stages): the caller's, else the
+    // tuned one (one right-hand side), else narrow tiles where an operator
+    // has few columns, one row tile, four stages
+    int NC = avg_cols < 48.0 ? 32 : 64, R = 1, ST = 4;
     if (mr == 1 && P.nc_tuned) {
         NC = P.nc_tuned;
+        R = P.r_tuned;
         ST = P.st_tuned;
     }
     if (nc) NC = nc;
+    if (rows) R = rows;
     if (st) ST = st;
+    if (R > P.nrt) R = 1;
     const tile_set *ts = nullptr;
     for (const auto &t : P.tilesets)
-        if (t.mr == mr && t.nc == NC) ts = &t;
+        if (t.mr == mr && t.nc == NC && t.rows == R) ts = &t;
     if (!ts) {
         std::vector<tc_tile> tiles;
         for (int o = 0; o < nops; ++o) {
             int a = B.op_start[o] * mr, b = B.op_start[o + 1] * mr;
             for (int p0 = a; p0 < b; p0 += NC)
-                for (int rt = 0; rt < P.nrt; ++rt) tiles.push_back(tc_tile{o, p0, std::min(NC, b - p0), rt});
+                for (int rt = 0; rt < P.nrt; rt += R) tiles.push_back(tc_tile{o, p0, std::min(NC, b - p0), rt});
         }
         P.tilesets.emplace_back();
         tile_set &t = P.tilesets.back();
         t.mr = mr;
         t.nc = NC;
+        t.rows = R;
         t.n = (int)tiles.size();
         t.buf.alloc(sizeof(tc_tile) * std::max<size_t>(tiles.size(), 1));
         if (!tiles.empty())
@@ -540,14 +563,17 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
         ts = &t;
     }
     if (ts->n == 0) return;
-    tc_args a{ts->buf.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.Tout, P.Tin,
+    tc_args a{ts->buf.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.nrt, P.Tout, P.Tin,
               src.as<__nv_bfloat16>(), dst, mr, svstride, dstride, h->tc_err.as<int>()};
-    if (NC == 32) {
-        if (ST == 2) launch_tc<32, 2>(a, ts->n, h->stream);
-        else launch_tc<32, 4>(a, ts->n, h->stream);
+    if (R == 2) {
+        if (NC == 32) launch_tc<32, 2, 4>(a, ts->n, h->stream);
+        else launch_tc<64, 2, 3>(a, ts->n, h->stream);
+    } else if (NC == 32) {
+        if (ST == 2) launch_tc<32, 1, 2>(a, ts->n, h->stream);
+        else launch_tc<32, 1, 4>(a, ts->n, h->stream);
     } else {
-        if (ST == 2) launch_tc<64, 2>(a, ts->n, h->stream);
-        else launch_tc<64, 4>(a, ts->n, h->stream);
+        if (ST == 2) launch_tc<64, 1, 2>(a, ts->n, h->stream);
+        else launch_tc<64, 1, 4>(a, ts->n, h->stream);
     }
     FDA_CHECK_LAUNCH();
 }
