@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
     constexpr int AR = R * 2 * ABYTES;             // A hi, A lo of each of the R row tiles
     constexpr int STAGE = AR + 4 * BB;             // then Br hi, Bi hi, Br lo, Bi lo
     constexpr int SLOT = R * 2 * NC;               // TMEM columns of one accumulator slot
+    constexpr int TALLOC = 2 * SLOT <= 128 ? 128 : (2 * SLOT <= 256 ? 256 : 512);  // power of two
     float2 *stg = reinterpret_cast<float2 *>(smem + ST * STAGE);  // epilogue staging [EPC][128 lanes]
     __shared__ long long srcv[NC];             // producers: source vector per column of the current tile
     __shared__ int stage_nr[ST];               // row tiles present in the tile of each stage
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(2 * SLOT));
+                     "r"(TALLOC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
     if (*abort_v && nc > 0 && tid == 0) mbar_wait(smem_u32(&empty[(nc - 1) % ST]), ((nc - 1) / ST) & 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SLOT));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TALLOC));
 }
 
 // operator panels: per operator, per row tile (64 complex rows), per stage
@@ -459,7 +460,8 @@ void launch_tc(const tc_args &a, int ntiles, cudaStream_t s)
         FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<NC, R, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         FDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_btr_tc<NC, R, ST>, WS_THREADS, smem));
-        per_sm = std::min(per_sm, 512 / (4 * R * NC));  // tensor memory: two slots of 2 R NC columns per CTA
+        const int talloc = 4 * R * NC <= 128 ? 128 : (4 * R * NC <= 256 ? 256 : 512);
+        per_sm = std::min(per_sm, 512 / talloc);  // tensor memory: two slots of 2 R NC columns per CTA
         if (per_sm < 1) fda_fail(FDA_ERR_CUDA, "tensor-core translation kernel does not fit on an SM");
     }
     const int grid = std::min(ntiles, per_sm * nsm);
@@ -541,6 +543,7 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (rows) R = rows;
     if (st) ST = st;
     if (R > P.nrt) R = 1;
+    if (R == 3) NC = 32;  // three row tiles fit tensor memory only with 32 columns
     const tile_set *ts = nullptr;
     for (const auto &t : P.tilesets)
         if (t.mr == mr && t.nc == NC && t.rows == R) ts = &t;
@@ -565,7 +568,9 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (ts->n == 0) return;
     tc_args a{ts->buf.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.nrt, P.Tout, P.Tin,
               src.as<__nv_bfloat16>(), dst, mr, svstride, dstride, h->tc_err.as<int>()};
-    if (R == 2) {
+    if (R == 3) {
+        launch_tc<32, 3, 3>(a, ts->n, h->stream);
+    } else if (R == 2) {
         if (NC == 32) launch_tc<32, 2, 4>(a, ts->n, h->stream);
         else launch_tc<64, 2, 3>(a, ts->n, h->stream);
     } else if (NC == 32) {
