@@ -67,7 +67,7 @@ typedef struct {
     double rho_min;        /* high-frequency far field starts at max(rho_min, w/lambda) widths (2.2) */
     int precision;         /* fda_precision: plain FP64 or chosen FP32 far field and near storage */
     int mode;              /* fda_mode: FDA, or dense all-pairs direct sum (small meshes, testing) */
-    int restart;           /* GMRES restart length (default 100) */
+    int restart;           /* GMRES restart length, 1 to 255 (default 100) */
     int maxit;             /* GMRES iteration cap (default 1000) */
     int precond;           /* 0 none (the paper's setting), 1 leaf block-diagonal (right preconditioner);
                               the learned preconditioner (2) is selected with fda_set_precond after fda_sai_set */

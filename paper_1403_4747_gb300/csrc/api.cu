@@ -135,7 +135,7 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
     if (!(c.eps > 0 && c.eps <= 0.1) || c.leaf_max < 1 || c.leaf_max > 64 || c.p_lf < 3 || c.p_lf > 16 ||
         c.p_hf < 3 || c.p_hf > 16 || c.hf_nr < 1 || c.hf_na < 8 || !(c.hf_wavelengths > 0) || !(c.rho_min >= 2.0) ||
         (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
-        (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.maxit < 1 || c.precond < 0 ||
+        (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.restart > 255 || c.maxit < 1 || c.precond < 0 ||
         c.precond > 1 || (c.graphs != 0 && c.graphs != 1) || (c.autotune != 0 && c.autotune != 1) || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0) || c.max_rhs < 1 || c.max_rhs > 256 ||
         c.tensor_cores < 0 || c.tensor_cores > 1)
         return FDA_ERR_ARG;

@@ -21,33 +21,56 @@
 namespace {
 
 constexpr int RT = 256;
-constexpr int RCH = 512;  // chunks per vector for the two-stage dot products
+constexpr int RCH = 128;  // chunks per vector for the two-stage dot products
 
-// partial[i * RCH + c] = sum over chunk c of conj(V_i[n]) w[n]
-__global__ void k_dots(const c64d *V, int64_t ldv, int nv, const c64d *w, int64_t n, c64d *partial)
+// partial[i * RCH + c] = sum over chunk c of conj(V_i[n]) w[n].  A CTA takes
+// one chunk of the index range and a group of DVG vectors: every thread
+// reads its w values once and accumulates DVG products from them, then the
+// DVG sums are reduced across the CTA.
+constexpr int DVG = 8;  // vectors per CTA
+
+__global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv, const c64d *w, int64_t n,
+                                             c64d *partial)
 {
-    __shared__ double sr[RT], si[RT];
-    int i = blockIdx.y, c = blockIdx.x;
-    int64_t per = (n + RCH - 1) / RCH;
-    int64_t b = (int64_t)c * per, e = b + per < n ? b + per : n;
-    double ar = 0.0, ai = 0.0;
-    const c64d *v = V + (int64_t)i * ldv;
+    __shared__ double sr[RT / 32][DVG], si[RT / 32][DVG];
+    const int c = blockIdx.x, i0 = blockIdx.y * DVG, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ng = min(DVG, nv - i0);
+    const int64_t per = (n + RCH - 1) / RCH;
+    const int64_t b = (int64_t)c * per, e = b + per < n ? b + per : n;
+    double ar[DVG], ai[DVG];
+#pragma unroll
+    for (int g = 0; g < DVG; ++g) ar[g] = ai[g] = 0.0;
     for (int64_t t = b + threadIdx.x; t < e; t += RT) {
-        c64d a = v[t], x = w[t];
-        ar += a.re * x.re + a.im * x.im;
-        ai += a.re * x.im - a.im * x.re;
+        const c64d x = w[t];
+#pragma unroll
+        for (int g = 0; g < DVG; ++g)
+            if (g < ng) {
+                const c64d a = V[(int64_t)(i0 + g) * ldv + t];
+                ar[g] += a.re * x.re + a.im * x.im;
+                ai[g] += a.re * x.im - a.im * x.re;
+            }
     }
-    sr[threadIdx.x] = ar;
-    si[threadIdx.x] = ai;
-    __syncthreads();
-    for (int s = RT / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-            sr[threadIdx.x] += sr[threadIdx.x + s];
-            si[threadIdx.x] += si[threadIdx.x + s];
+#pragma unroll
+    for (int g = 0; g < DVG; ++g)
+        for (int o = 16; o > 0; o >>= 1) {
+            ar[g] += __shfl_xor_sync(0xffffffffu, ar[g], o);
+            ai[g] += __shfl_xor_sync(0xffffffffu, ai[g], o);
         }
-        __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int g = 0; g < DVG; ++g) {
+            sr[warp][g] = ar[g];
+            si[warp][g] = ai[g];
+        }
+    __syncthreads();
+    if (threadIdx.x < ng) {
+        double r = 0.0, im = 0.0;
+        for (int q = 0; q < RT / 32; ++q) {
+            r += sr[q][threadIdx.x];
+            im += si[q][threadIdx.x];
+        }
+        partial[(int64_t)(i0 + threadIdx.x) * RCH + c] = c64d(r, im);
     }
-    if (threadIdx.x == 0) partial[(int64_t)i * RCH + c] = c64d(sr[0], si[0]);
 }
 
 __global__ void k_dots_finish(const c64d *partial, int nv, c64d *out)
@@ -72,13 +95,27 @@ __global__ void k_dots_finish(const c64d *partial, int nv, c64d *out)
     if (threadIdx.x == 0) out[i] = c64d(sr[0], si[0]);
 }
 
-// w[n] += sign * sum_i V_i[n] c[i]
-__global__ void k_combine(const c64d *V, int64_t ldv, int nv, const c64d *c, double sign, c64d *w, int64_t n)
+// w[n] += sign * sum_i V_i[n] c[i]; the coefficients are staged in shared
+// memory and the vectors read four at a time
+__global__ void __launch_bounds__(RT) k_combine(const c64d *V, int64_t ldv, int nv, const c64d *c, double sign,
+                                                c64d *w, int64_t n)
 {
+    __shared__ c64d cs[256];
+    for (int i = threadIdx.x; i < nv && i < 256; i += RT) cs[i] = c[i];
+    __syncthreads();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     c64d acc;
-    for (int i = 0; i < nv; ++i) cfma(acc, V[(int64_t)i * ldv + t], c[i]);
+    int i = 0;
+    for (; i + 3 < nv; i += 4) {
+        const c64d a0 = V[(int64_t)i * ldv + t], a1 = V[(int64_t)(i + 1) * ldv + t];
+        const c64d a2 = V[(int64_t)(i + 2) * ldv + t], a3 = V[(int64_t)(i + 3) * ldv + t];
+        cfma(acc, a0, cs[i]);
+        cfma(acc, a1, cs[i + 1]);
+        cfma(acc, a2, cs[i + 2]);
+        cfma(acc, a3, cs[i + 3]);
+    }
+    for (; i < nv; ++i) cfma(acc, V[(int64_t)i * ldv + t], cs[i]);
     w[t] = c64d(w[t].re + sign * acc.re, w[t].im + sign * acc.im);
 }
 
@@ -103,7 +140,7 @@ struct solver {
 
     void dots(const c64d *V, int nv, const c64d *w, std::vector<std::complex<double>> &out)
     {
-        dim3 g(RCH, nv);
+        dim3 g(RCH, (nv + DVG - 1) / DVG);
         k_dots<<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>());
         FDA_CHECK_LAUNCH();
         k_dots_finish<<<nv, RT, 0, h->stream>>>(partial.as<c64d>(), nv, hd.as<c64d>());
@@ -150,7 +187,9 @@ struct solver {
     }
 
     // GMRES(m) on A_prec: solve A d = r to ||r - A d|| <= tol_rel ||r||; d in/out
-    int gmres(const c64d *r, c64d *d, double tol_rel, int precision, int maxit, int &iters_out, double &est)
+    // (d_zero: the caller knows d = 0, so the first residual is r itself)
+    int gmres(const c64d *r, c64d *d, double tol_rel, int precision, int maxit, int &iters_out, double &est,
+              bool d_zero = false)
     {
         const int m = std::max(1, h->cfg.restart);
         dbuf Vb, w;
@@ -165,11 +204,17 @@ struct solver {
             return 0;
         }
         int it = 0;
+        bool first = true;
         while (true) {
-            // residual of the current d: v0 = r - A d
-            apply(d, w.as<c64d>(), precision);
-            k_axpby<<<fda_blocks(n, RT), RT, 0, h->stream>>>(r, 1.0, w.as<c64d>(), -1.0, V, n);
-            FDA_CHECK_LAUNCH();
+            // residual of the current d: v0 = r - A d (no product while d = 0)
+            if (first && d_zero) {
+                FDA_CUDA(cudaMemcpyAsync(V, r, sizeof(c64d) * n, cudaMemcpyDeviceToDevice, h->stream));
+            } else {
+                apply(d, w.as<c64d>(), precision);
+                k_axpby<<<fda_blocks(n, RT), RT, 0, h->stream>>>(r, 1.0, w.as<c64d>(), -1.0, V, n);
+                FDA_CHECK_LAUNCH();
+            }
+            first = false;
             double beta = norm(V);
             if (!std::isfinite(beta)) fda_fail(FDA_ERR_NUMERIC, "non-finite residual in GMRES");
             est = beta / rnorm0;
@@ -284,6 +329,7 @@ fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda
     double bnorm = S.norm(bs.as<c64d>());
     int iters = 0, refinements = 0;
     double rel = 0.0;
+    bool rel_of_x = false;  // rel already holds the FP64 residual of the current x
     fda_status st = FDA_OK;
     if (bnorm == 0.0) {
         FDA_CUDA(cudaMemsetAsync(xs.p, 0, sizeof(c64d) * n, h->stream));
@@ -291,20 +337,28 @@ fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda
         int it = 0;
         double est = 0;
         // solve A x = b directly: r = b, d = x
-        int rc = S.gmres(bs.as<c64d>(), xs.as<c64d>(), tol, FDA_PLAIN_FP64, h->cfg.maxit, it, est);
+        const bool x_zero = S.norm(xs.as<c64d>()) == 0.0;
+        int rc = S.gmres(bs.as<c64d>(), xs.as<c64d>(), tol, FDA_PLAIN_FP64, h->cfg.maxit, it, est, x_zero);
         iters = it;
         refinements = 0;
         (void)rc;
     } else {
         // outer FP64 residual, inner FP32 GMRES
         int budget = h->cfg.maxit;
+        bool x_zero = S.norm(xs.as<c64d>()) == 0.0;
         for (int pass = 0; pass < 20; ++pass) {
-            S.apply(xs.as<c64d>(), ax.as<c64d>(), FDA_PLAIN_FP64);
-            ++refinements;
-            k_sub<<<fda_blocks(n, RT), RT, 0, h->stream>>>(bs.as<c64d>(), ax.as<c64d>(), r.as<c64d>(), n);
-            FDA_CHECK_LAUNCH();
-            double rn = S.norm(r.as<c64d>());
-            rel = rn / bnorm;
+            if (x_zero) {
+                // r = b - A 0 = b: no FP64 product needed
+                FDA_CUDA(cudaMemcpyAsync(r.p, bs.p, sizeof(c64d) * n, cudaMemcpyDeviceToDevice, h->stream));
+                rel = 1.0;
+            } else {
+                S.apply(xs.as<c64d>(), ax.as<c64d>(), FDA_PLAIN_FP64);
+                ++refinements;
+                k_sub<<<fda_blocks(n, RT), RT, 0, h->stream>>>(bs.as<c64d>(), ax.as<c64d>(), r.as<c64d>(), n);
+                FDA_CHECK_LAUNCH();
+                rel = S.norm(r.as<c64d>()) / bnorm;
+                rel_of_x = true;
+            }
             if (rel <= tol || budget <= 0) break;
             // the FP32 operator reaches ~1e-6 relative at best: ask the inner
             // solve for at most 1e-5 and let the FP64 refinement passes do the rest
@@ -312,15 +366,17 @@ fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda
             FDA_CUDA(cudaMemsetAsync(d.p, 0, sizeof(c64d) * n, h->stream));
             int it = 0;
             double est = 0;
-            S.gmres(r.as<c64d>(), d.as<c64d>(), tin, FDA_CHOSEN_FP32, budget, it, est);
+            S.gmres(r.as<c64d>(), d.as<c64d>(), tin, FDA_CHOSEN_FP32, budget, it, est, true);
             iters += it;
             budget -= it;
             k_add<<<fda_blocks(n, RT), RT, 0, h->stream>>>(xs.as<c64d>(), d.as<c64d>(), n);
             FDA_CHECK_LAUNCH();
+            x_zero = false;
+            rel_of_x = false;
         }
     }
-    // final FP64 residual
-    if (bnorm > 0) {
+    // final FP64 residual (unless the refinement loop just computed it)
+    if (bnorm > 0 && !rel_of_x) {
         S.apply(xs.as<c64d>(), ax.as<c64d>(), FDA_PLAIN_FP64);
         k_sub<<<fda_blocks(n, RT), RT, 0, h->stream>>>(bs.as<c64d>(), ax.as<c64d>(), r.as<c64d>(), n);
         FDA_CHECK_LAUNCH();

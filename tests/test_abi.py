@@ -42,7 +42,7 @@ def test_default_config(lib):
 
 
 @pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", 0.5), ("leaf_max", 0), ("leaf_max", 65),
-                                         ("p_lf", 2), ("precision", 3), ("mode", 7), ("restart", 0),
+                                         ("p_lf", 2), ("precision", 3), ("mode", 7), ("restart", 0), ("restart", 256),
                                          ("rho_min", 1.0), ("graphs", 2), ("autotune", 3), ("precond", 2)])
 def test_invalid_config_rejected_without_gpu(lib, field, value):
     from paper_1403_4747_gb300 import fda_default_config, fda_create, FDAError, FDA_ERR_ARG
