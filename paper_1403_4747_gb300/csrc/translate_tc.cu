@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
     constexpr int STAGE = AR + 4 * BB;             // then Br hi, Bi hi, Br lo, Bi lo
     constexpr int SLOT = R * 2 * NC;               // TMEM columns of one accumulator slot
     constexpr int TALLOC = 2 * SLOT <= 128 ? 128 : (2 * SLOT <= 256 ? 256 : 512);  // power of two
+    static_assert(NC <= NPROD, "one tile column per producer thread");
     float2 *stg = reinterpret_cast<float2 *>(smem + ST * STAGE);  // epilogue staging [EPC][128 lanes]
     __shared__ long long srcv[NC];             // producers: source vector per column of the current tile
     __shared__ int stage_nr[ST];               // row tiles present in the tile of each stage
@@ -212,21 +213,34 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
 
     if (warp >= 5) {
         // ---------------- producers
+        // Tile descriptors are fetched two tiles ahead and the column's pair
+        // one tile ahead, so the global-memory latency of both is hidden
+        // behind the previous tile's stages (NC <= NPROD: one column per
+        // thread).
         const int tp = tid - 160;
+        auto tile_at = [&](int j) {
+            return j < my_tiles ? tiles[blockIdx.x + (int64_t)j * gridDim.x] : tc_tile{0, 0, 0, 0};
+        };
+        auto col_src = [&](const tc_tile &t, int2 q) -> long long {
+            if (tp >= t.npair) return -1;
+            const int vi = t.pair0 + tp;
+            const int m = vi - (vi / mr) * mr;
+            return q.x / Tin + m * svstride;
+        };
+        auto pair_of = [&](const tc_tile &t) {
+            if (tp >= t.npair) return make_int2(0, 0);
+            return pairs[(t.pair0 + tp) / mr];
+        };
+        tc_tile t_next = tile_at(1), t_cur = tile_at(0);
+        long long v_cur = col_src(t_cur, pair_of(t_cur));
         int g = 0;
         bool ok = true;
         for (int j = 0; j < my_tiles && ok; ++j) {
-            const tc_tile t = tiles[blockIdx.x + (int64_t)j * gridDim.x];
+            const tc_tile t = t_cur;
+            const tc_tile t_after = tile_at(j + 2);     // used two tiles from now
+            const int2 q_next = pair_of(t_next);        // used at the next tile
             asm volatile("bar.sync 1, %0;" ::"r"(NPROD));  // everyone is done with the previous srcv
-            for (int c = tp; c < NC; c += NPROD) {
-                long long v = -1;
-                if (c < t.npair) {
-                    int vi = t.pair0 + c;
-                    int pi = vi / mr, m = vi - pi * mr;
-                    v = pairs[pi].x / Tin + m * svstride;
-                }
-                srcv[c] = v;
-            }
+            if (tp < NC) srcv[tp] = v_cur;
             asm volatile("bar.sync 1, %0;" ::"r"(NPROD));
             const int nr = min(R, nrt - t.rt);  // row tiles of this tile
             const uint8_t *gA = opsA + (int64_t)t.op * op_bytes + (int64_t)t.rt * nkc * 2 * ABYTES;
@@ -272,6 +286,9 @@ __global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int
                 }
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fb));
             }
+            v_cur = col_src(t_next, q_next);
+            t_cur = t_next;
+            t_next = t_after;
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 4) {
