@@ -83,10 +83,10 @@ typedef struct {
                               every GMRES product) replays one captured CUDA graph on a library stream
                               joined to cuda_stream; 0: launch the kernels one by one (timing mode also
                               does) */
-    int autotune;          /* 1 (default): at setup, time each tensor-core translation batch with 32- and
-                              64-column tiles, one to three 64-row tiles per CTA tile and 2 to 4 ring stages,
-                              and keep the fastest (one right-hand side); 0: fixed rule (32 columns where an
-                              operator has few pairs, else 64; one row tile; 4 stages) */
+    int autotune;          /* 1 (default): at setup, time each tensor-core translation batch with 32-, 64-
+                              and 128-column tiles, one to three 64-row tiles per CTA tile and 2 to 4 ring
+                              stages, and keep the fastest (one right-hand side); 0: fixed rule (32, 64 or
+                              128 columns as operators have few or many pairs; one row tile) */
 } fda_config;
 
 typedef struct {

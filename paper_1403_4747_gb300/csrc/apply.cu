@@ -353,7 +353,8 @@ void fda_autotune_tc(fda_handle *h)
     FDA_CUDA(cudaEventCreate(&e1));
     lvl_ptrs<float> P = make_ptrs<float>(h, h->op32, h->q32, h->p32);
     // (columns, row tiles, stages)
-    static const int cand[7][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4}, {64, 2, 3}, {32, 3, 3}};
+    static const int cand[8][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4}, {64, 2, 3}, {32, 3, 3},
+                                   {128, 1, 3}};
     auto tune = [&](tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst, int64_t ds) {
         if (B.npairs == 0 || !T.A.p) return;
         float best = 1e30f;

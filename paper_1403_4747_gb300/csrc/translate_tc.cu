@@ -96,11 +96,11 @@ __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv
 
 // Persistent, warp-specialised form.  CTA c takes tiles c, c + grid,
 // c + 2 grid, ...; its warps split the work of every tile:
-//   warps 5-7 (producers): load stage g of the CTA into ring buffer g % ST:
+//   warps 5-8 (producers): load stage g of the CTA into ring buffer g % ST:
 //       the operator panels of the tile's row tiles by one bulk copy each,
 //       the tile's density columns (256 contiguous bytes each) by 16-byte
 //       cp.async copies (zero fill for columns with no pair); full[b]
-//       completes when all of them have landed (arrival count = 96 producer
+//       completes when all of them have landed (arrival count = 128 producer
 //       threads + 1 for the byte count);
 //   warp 4 (MMA): one thread issues the stage's MMAs into the tile's
 //       accumulator slot (R row tiles x [D1 D2]) and commits them to
@@ -114,8 +114,8 @@ __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv
 // once another role has recorded an error; the CTA then waits (bounded) for
 // its copies and MMAs in flight, frees its tensor memory and returns.
 constexpr int EPC = 16;          // epilogue chunk: accumulator columns staged per pass
-constexpr int WS_THREADS = 256;  // 8 warps
-constexpr int NPROD = 96;        // producer threads (warps 5-7)
+constexpr int WS_THREADS = 288;  // 9 warps
+constexpr int NPROD = 128;       // producer threads (warps 5-8)
 
 __device__ inline bool mbar_wait_ab(uint32_t bar, uint32_t parity, const volatile int *abort)
 {
@@ -162,7 +162,7 @@ __device__ inline bool bar_any(int id, int n, bool pred)
 }
 
 template <int NC, int R, int ST>
-__global__ void __launch_bounds__(WS_THREADS) k_btr_tc(const tc_tile *tiles, int ntiles, const int2 *pairs,
+__global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, int ntiles, const int2 *pairs,
                                                         const uint8_t *opsA, int64_t op_bytes, int nkc, int nrt,
                                                         int Tout, int Tin, const __nv_bfloat16 *qb, c32f *dst, int mr,
                                                         int64_t svstride, int64_t dstride, int *err)
@@ -550,7 +550,7 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     // tile shape (columns, row tiles, ring stages): the caller's, else the
     // tuned one (one right-hand side), else narrow tiles where an operator
     // has few columns, one row tile, four stages
-    int NC = avg_cols < 48.0 ? 32 : 64, R = 1, ST = 4;
+    int NC = avg_cols < 48.0 ? 32 : (avg_cols < 256.0 ? 64 : 128), R = 1, ST = NC == 128 ? 3 : 4;
     if (mr == 1 && P.nc_tuned) {
         NC = P.nc_tuned;
         R = P.r_tuned;
@@ -561,6 +561,7 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (st) ST = st;
     if (R > P.nrt) R = 1;
     if (R == 3) NC = 32;  // three row tiles fit tensor memory only with 32 columns
+    if (NC == 128) R = 1, ST = 3;
     const tile_set *ts = nullptr;
     for (const auto &t : P.tilesets)
         if (t.mr == mr && t.nc == NC && t.rows == R) ts = &t;
@@ -590,6 +591,8 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     } else if (R == 2) {
         if (NC == 32) launch_tc<32, 2, 4>(a, ts->n, h->stream);
         else launch_tc<64, 2, 3>(a, ts->n, h->stream);
+    } else if (NC == 128) {
+        launch_tc<128, 1, 3>(a, ts->n, h->stream);
     } else if (NC == 32) {
         if (ST == 2) launch_tc<32, 1, 2>(a, ts->n, h->stream);
         else launch_tc<32, 1, 4>(a, ts->n, h->stream);
