@@ -52,7 +52,7 @@ constexpr int NRG = 8;
 
 constexpr int NRW = 2;  // rows per warp in the near-field product
 
-template <typename R, int NR>
+template <typename R, int NR, bool XS>
 __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, const int32_t *bbeg,
                                                    const int32_t *bend, const int64_t *colptr, const int32_t *cols,
                                                    const int64_t *off, const cx<R> *A, const void *x, int x64,
@@ -62,18 +62,28 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
     // 8 NRW); the leaf's columns (its flattened near ranges, shared by all
     // its rows) are streamed four 32-wide slices at a time, the last ones
     // predicated, so every lane keeps 4 NRW independent matrix loads in
-    // flight and each column index and x value serves NRW rows.
+    // flight and each x value serves NRW rows.  With XS (one right-hand
+    // side) the CTA first gathers x over the leaf's columns into shared
+    // memory, so the warps read it from there instead of through the column
+    // list.
+    extern __shared__ unsigned char xs_raw[];
+    cx<R> *xsm = reinterpret_cast<cx<R> *>(xs_raw);
     int li = blockIdx.x;
     int B = leaf_box[li];
     int i0 = bbeg[B], nB = bend[B] - i0;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = blockIdx.y * (AT / 32) * NRW + warp;
-    if (r0 >= nB) return;
+    if (blockIdx.y * (AT / 32) * NRW >= nB) return;  // whole CTA
     const int m0 = blockIdx.z * NR;
     const int nm = min(NR, mr - m0);
     const int64_t c0 = colptr[li];
     const int nc = (int)(colptr[li + 1] - c0);
     const int32_t *cl = cols + c0;
+    if (XS) {
+        for (int c = threadIdx.x; c < nc; c += AT) xsm[c] = ldx<R>(x, __ldg(cl + c), x64);
+        __syncthreads();
+    }
+    if (r0 >= nB) return;
     const cx<R> *rowp[NRW];
     bool rv[NRW];
 #pragma unroll
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
             const int cc = cb + 32 * u + lane;
             j[u] = 0;
             if (cc < nc) {
-                j[u] = __ldg(cl + cc);
+                j[u] = XS ? cc : __ldg(cl + cc);
 #pragma unroll
                 for (int w = 0; w < NRW; ++w)
                     if (rv[w]) a[w][u] = rowp[w][cc];
@@ -102,7 +112,8 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
 #pragma unroll
             for (int mm = 0; mm < NR; ++mm)
                 if (mm < nm) {
-                    const cx<R> xv = ldx<R>(x, (int64_t)(m0 + mm) * xstr + j[u], x64);
+                    const cx<R> xv = XS ? (cb + 32 * u + lane < nc ? xsm[j[u]] : cx<R>())
+                                        : ldx<R>(x, (int64_t)(m0 + mm) * xstr + j[u], x64);
 #pragma unroll
                     for (int w = 0; w < NRW; ++w) cfma(acc[w][mm], a[w][u], xv);
                 }
@@ -217,18 +228,31 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     };
     mark(0);
     const int max_rows = h->max_leaf_rows;
-    if (mr == 1) {
+    const size_t xs_bytes = sizeof(cx<R>) * (size_t)h->max_near_cols;
+    if (mr == 1 && xs_bytes <= 160 * 1024) {
         dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
-        k_near_apply<R, 1><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
-                                             h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
-                                             h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                             ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+        static bool attr = false;
+        if (!attr) {
+            FDA_CUDA(cudaFuncSetAttribute(k_near_apply<R, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          160 * 1024));
+            attr = true;
+        }
+        k_near_apply<R, 1, true><<<gn, AT, xs_bytes, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+                                                          h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
+                                                          h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
+                                                          ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+    } else if (mr == 1) {
+        dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
+        k_near_apply<R, 1, false><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+                                                    h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
+                                                    h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
+                                                    ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
     } else {
         dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), (mr + NRG - 1) / NRG);
-        k_near_apply<R, NRG><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
-                                               h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
-                                               h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                               ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+        k_near_apply<R, NRG, false><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+                                                      h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
+                                                      h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
+                                                      ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
     }
     FDA_CHECK_LAUNCH();
     mark(1);

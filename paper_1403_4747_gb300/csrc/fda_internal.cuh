@@ -211,6 +211,7 @@ struct fda_handle {
     dbuf box_level;            // int32
     int nleaf = 0;
     int max_leaf_rows = 0;     // largest leaf (elements)
+    int64_t max_near_cols = 0; // widest near-field row of a leaf (columns)
     dbuf leaf_box;             // int32 [nleaf] global box index
     std::vector<int> h_leaf_level;  // leaf index -> level (host)
     dbuf leaf_of_box;          // int32 [nbox]: leaf index or -1

@@ -690,6 +690,15 @@ void fda_tree_build(fda_handle *h)
     }
     h->nf_colptr.alloc(sizeof(int64_t) * (NL + 1));
     fda_exclusive_scan_i64(ncols.as<int64_t>(), h->nf_colptr.as<int64_t>(), NL + 1, s, &h->ncols_total);
+    {
+        // widest leaf row (columns), for the near-field kernel's shared-memory staging
+        std::vector<int64_t> cp(NL + 1);
+        FDA_CUDA(cudaMemcpyAsync(cp.data(), h->nf_colptr.p, 8 * (size_t)(NL + 1), cudaMemcpyDeviceToHost, s));
+        FDA_CUDA(cudaStreamSynchronize(s));
+        int64_t mx = 0;
+        for (int li = 0; li < NL; ++li) mx = std::max(mx, cp[li + 1] - cp[li]);
+        h->max_near_cols = mx;
+    }
     h->nf_cols.alloc(sizeof(int32_t) * std::max<int64_t>(h->ncols_total, 1));
     k_near_cols<<<NL, 128, 0, s>>>(h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(), h->nr_end.as<int32_t>(),
                                    h->nf_colptr.as<int64_t>(), NL, h->nf_cols.as<int32_t>());
