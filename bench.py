@@ -41,6 +41,41 @@ def _dist():
     return ws, rank, local
 
 
+class RankGroup:
+    """One process per GPU (torchrun): barrier and max over ranks.  NCCL
+    between GPUs, gloo on CPU (the same code path the tests run)."""
+
+    def __init__(self, backend=None):
+        self.ws, self.rank, self.local = _dist()
+        self.dist = None
+        self.backend = backend
+        if self.ws > 1:
+            import torch
+            import torch.distributed as dist
+            if self.backend is None:
+                self.backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(self.backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, v):
+        if self.dist is None:
+            return v
+        import torch
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -157,27 +192,13 @@ def run_native(args):
     import torch
 
     ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    group = RankGroup()
     from paper_1403_4747_gb300 import build as lib_build
     lib_build.build()
     import paper_1403_4747_gb300 as F
     from inputs import icosphere, complex_normal
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def reduce_max(v):
-        if ws == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, reduce_max = group.barrier, group.max
 
     v, f = icosphere(args.level)
     n = len(f)
@@ -414,9 +435,7 @@ def run_native(args):
         print(json.dumps(line), flush=True)
     if P is not None:
         P.close()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    group.close()
     return 0
 
 
