@@ -478,6 +478,87 @@ def _m2l_flops(P):
     return int(sum(8.0 * st.level_rank[l] ** 2 * st.level_m2l_pairs[l] for l in range(st.n_levels)))
 
 
+def run_many_meshes(args):
+    """Eight meshes (sphere and ellipsoid icospheres, levels 5-7, kD 20-100)
+    times 64 plane-wave directions behind one batch apply per step: one CUDA
+    graph per step, one branch per mesh.  Reports (mesh x right-hand side)
+    matvecs per second.  Not the headline workload; run with
+    --workload many_meshes."""
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    group = RankGroup()
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import multi_mesh_set, complex_normal
+    mm = multi_mesh_set()
+    nrhs = args.batch
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    B = F.FDABatch([(v, f) for v, f, _ in mm], [k for _, _, k in mm], stream=stream,
+                   precision=F.FDA_CHOSEN_FP32, eps=args.eps, max_rhs=nrhs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    xs = [torch.from_numpy(complex_normal(len(f), seed=500 + i, nrhs=nrhs)).cuda() for i, (v, f, _) in enumerate(mm)]
+    ys = [torch.empty_like(x) for x in xs]
+    for _ in range(max(3, args.warmup)):
+        B.apply(xs, ys)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 20)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    group.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nl0 = F.fda_launch_count()
+    gr0 = B.stats().graph_replays
+    clocks.mark("t_begin")
+    e0.record(stream)
+    for _ in range(steps):
+        B.apply(xs, ys)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("t_end")
+    launches = F.fda_launch_count() - nl0
+    st = B.stats()
+    group.barrier()
+    clk = clocks.stop()
+    ms = group.max(e0.elapsed_time(e1) / steps)
+    # each mesh alone through its own handle, for comparison with the batch
+    alone_ms = []
+    for i in range(len(mm)):
+        h = B.mesh(i)
+        n = len(mm[i][1])
+        F.fda_apply(h, xs[i].data_ptr(), ys[i].data_ptr(), nrhs, n)
+        F.fda_apply(h, xs[i].data_ptr(), ys[i].data_ptr(), nrhs, n)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        F.fda_apply(h, xs[i].data_ptr(), ys[i].data_ptr(), nrhs, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        alone_ms.append(e0.elapsed_time(e1))
+    line = {"metric": "many-mesh batched FDA matvec (mesh x right-hand side)/s", "value": ws * len(mm) * nrhs * 1e3 / ms,
+            "unit": "matvec/s", "n_gpus": ws, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3/f64",
+            "data": "synthetic",
+            "config": {"workload": "8 meshes (sphere/ellipsoid icospheres L5-L7, 20,480-327,680 triangles, kD 20-100) "
+                                   "x %d right-hand sides, chosen form, eps %g" % (nrhs, args.eps),
+                       "meshes": [{"n": len(f), "k": k} for _, f, k in mm], "n_total": int(st.n_total),
+                       "l2": "inputs larger than L2 (%.1f GB of right-hand sides per step)"
+                             % (st.n_total * nrhs * 16 * 2 / 1e9)},
+            "setup_s": setup_s, "device_gb": st.device_bytes / 1e9, "gpu_launches": launches,
+            "cuda_graph_replays": st.graph_replays - gr0, "graph_fallback": st.graph_fallback,
+            "sequential_handles_ms": sum(alone_ms), "per_mesh_ms": alone_ms, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    B.close()
+    group.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,11 +579,15 @@ def main():
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes"],
+                    help="many_meshes: the eight-mesh batch instead of the headline line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "many_meshes":
+        return run_many_meshes(args)
     return run_native(args)
 
 

@@ -270,6 +270,55 @@ fda_status fda_sai_loss_grad(int64_t n, const double *centroids, const double *n
                              const fda_c128 *blocks, const double *weights, int precision, double *loss,
                              double *grad);
 
+/* ---- Several meshes behind one operator application ----
+ * A batch holds one handle per mesh, all created from one configuration, and
+ * applies the operator of Eq. eq_sum (Sec. 3.3 Steps 2-4) to every mesh's
+ * right-hand sides in one call.  With cfg.graphs = 1 the passes of all meshes
+ * form one CUDA graph per call (captured on the second call with the same
+ * right-hand-side count and per-mesh precision), one parallel branch per
+ * mesh, so small meshes share the GPU instead of running one after another.
+ * The paper treats one mesh; the batch is an execution arrangement of the
+ * same per-mesh operator, and each mesh's result equals fda_apply on its
+ * handle up to the rounding order of the float atomics.
+ *   - fda_create_batch: nmesh in [1, 64]; cfg as for fda_create (NULL =
+ *     defaults).  Every call on the batch or on a mesh's handle is ordered on
+ *     cfg.cuda_stream; fda_apply_batch forks one private stream per mesh from
+ *     it and joins them back before returning control of the stream.
+ *   - fda_build_batch: per mesh i, verts[i] (host double[nv[i]][3]),
+ *     tris[i] (host int32[nt[i]][3]) and wavenumber k[i], as fda_build_tree.
+ *   - fda_precompute_batch: fda_precompute_translations on every mesh.
+ *   - fda_apply_batch: y[i] = A_i x[i] for every mesh i: x[i], y[i] device
+ *     pointers (caller-owned, column-major, nrhs columns, leading dimension
+ *     ld[i] >= nt[i], x[i] and y[i] not overlapping); x, y, ld are host
+ *     arrays of nmesh entries.  Columns go max_rhs at a time.
+ *   - fda_batch_mesh: the handle of mesh i, owned by the batch (valid until
+ *     fda_destroy_batch; do not destroy it), for fda_solve, fda_get_stats,
+ *     fda_rhs_plane_wave, fda_set_precision ...; NULL if i is out of range.
+ * Errors: FDA_ERR_ARG for bad sizes or pointers, FDA_ERR_STATE out of order,
+ * a mesh's own status (its message prefixed by "mesh i: ") otherwise; the
+ * message is read with fda_batch_last_error. */
+typedef struct fda_batch fda_batch;
+
+typedef struct {
+    int nmesh;
+    int64_t n_total;          /* elements over all meshes */
+    int64_t graph_replays;    /* batch graph launches so far */
+    int graph_fallback;       /* 1 if capture failed and calls run the passes directly */
+    size_t device_bytes;      /* device memory held by all meshes */
+} fda_batch_stats;
+
+fda_status fda_create_batch(const fda_config *cfg, int nmesh, fda_batch **out);
+fda_status fda_build_batch(fda_batch *b, const double *const *verts, const int64_t *nv, const int32_t *const *tris,
+                           const int64_t *nt, const double *k);
+fda_status fda_precompute_batch(fda_batch *b);
+fda_status fda_apply_batch(fda_batch *b, const fda_c128 *const *x, fda_c128 *const *y, int nrhs,
+                           const int64_t *ld);
+fda_handle *fda_batch_mesh(fda_batch *b, int i);
+fda_status fda_get_batch_stats(fda_batch *b, fda_batch_stats *out);
+const char *fda_batch_last_error(const fda_batch *b);
+/* Release the batch and its meshes' handles (NULL is ignored). */
+void fda_destroy_batch(fda_batch *b);
+
 /* Symmetry table of the cone partition of a high-frequency level with
  * nc x nc cells per cube face (6 nc^2 cones, Sec. 3.1; cone index =
  * (2 axis + [sign > 0]) nc^2 + a nc + b, a and b the cell along the two other

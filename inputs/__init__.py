@@ -11,7 +11,7 @@ Sec. 5.3) are not available; the icosphere family stands in for the sphere
 meshes of Table tab_usphpls and the plane-wave sphere of Sec. 5.3.
 """
 from .meshes import (icosphere, ellipsoid_from_icosphere, fibonacci_directions,
-                     complex_normal, icosahedral_rotations, mesh_for_config)
+                     complex_normal, icosahedral_rotations, mesh_for_config, multi_mesh_set)
 
 __all__ = ["icosphere", "ellipsoid_from_icosphere", "fibonacci_directions",
-           "complex_normal", "icosahedral_rotations", "mesh_for_config"]
+           "complex_normal", "icosahedral_rotations", "mesh_for_config", "multi_mesh_set"]

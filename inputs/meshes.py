@@ -126,6 +126,19 @@ def icosahedral_rotations():
     return out
 
 
+def multi_mesh_set():
+    """Eight meshes for the many-mesh batch: (verts, tris, k) for sphere and
+    ellipsoid icospheres of levels 5-7 (20,480-327,680 triangles), kD 20-100,
+    at least 10 elements per wavelength."""
+    spec = [("s", 5, 10.0), ("e", 5, 15.0), ("s", 6, 25.0), ("e", 6, 30.0),
+            ("s", 6, 33.0), ("e", 7, 45.0), ("s", 7, 50.0), ("e", 7, 50.0)]
+    out = []
+    for kind, level, k in spec:
+        v, f = icosphere(level) if kind == "s" else ellipsoid_from_icosphere(level)
+        out.append((v, f, k))
+    return out
+
+
 def mesh_for_config(name: str):
     """Named synthetic workloads: returns (verts, tris, k, direction).
 

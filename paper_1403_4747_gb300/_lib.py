@@ -56,6 +56,11 @@ class fda_sai_report(ctypes.Structure):
     _fields_ = [("loss_init", ctypes.c_double), ("loss_final", ctypes.c_double), ("train_s", ctypes.c_double)]
 
 
+class fda_batch_stats(ctypes.Structure):
+    _fields_ = [("nmesh", ctypes.c_int), ("n_total", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("graph_fallback", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+
+
 _lib = None
 
 
@@ -97,6 +102,21 @@ def load(path: str = LIB_PATH):
     lib.fda_sai_loss_grad.argtypes = [i64, vp, vp, vp, dbl, cint, vp, vp, vp, vp, cint, vp, vp]
     for name in ("fda_sai_default_config", "fda_sai_init_weights", "fda_sai_train", "fda_sai_set",
                  "fda_sai_loss_grad"):
+        getattr(lib, name).restype = cint
+    B = ctypes.c_void_p
+    lib.fda_create_batch.argtypes = [ctypes.POINTER(fda_config), cint, ctypes.POINTER(B)]
+    lib.fda_build_batch.argtypes = [B, vp, vp, vp, vp, vp]
+    lib.fda_precompute_batch.argtypes = [B]
+    lib.fda_apply_batch.argtypes = [B, vp, vp, cint, vp]
+    lib.fda_batch_mesh.argtypes = [B, cint]
+    lib.fda_batch_mesh.restype = H
+    lib.fda_get_batch_stats.argtypes = [B, ctypes.POINTER(fda_batch_stats)]
+    lib.fda_batch_last_error.argtypes = [B]
+    lib.fda_batch_last_error.restype = ctypes.c_char_p
+    lib.fda_destroy_batch.argtypes = [B]
+    lib.fda_destroy_batch.restype = None
+    for name in ("fda_create_batch", "fda_build_batch", "fda_precompute_batch", "fda_apply_batch",
+                 "fda_get_batch_stats"):
         getattr(lib, name).restype = cint
     lib.fda_launch_count.argtypes = []
     lib.fda_launch_count.restype = ctypes.c_longlong
@@ -276,6 +296,72 @@ def fda_sai_loss_grad(cent, nrm, area, k, block_ptr, block_elems, blocks, weight
                                           len(bp) - 1, bp.ctypes.data, be.ctypes.data, A.ctypes.data, W.ctypes.data,
                                           precision, ctypes.byref(loss), grad.ctypes.data))
     return loss.value, grad
+
+
+def _bcheck(b, st):
+    if st != FDA_OK:
+        raise FDAError(st, load().fda_batch_last_error(b).decode() if b else "")
+
+
+def fda_create_batch(cfg: fda_config | None, nmesh: int):
+    b = ctypes.c_void_p()
+    st = load().fda_create_batch(ctypes.byref(cfg) if cfg is not None else None, int(nmesh), ctypes.byref(b))
+    if st != FDA_OK:
+        raise FDAError(st, "fda_create_batch failed")
+    return b
+
+
+def fda_build_batch(b, meshes, ks):
+    """meshes: list of (verts float64 [V,3], tris int32 [N,3]) host arrays; ks: wavenumbers."""
+    import numpy as np
+    vs = [np.ascontiguousarray(v, dtype=np.float64) for v, _ in meshes]
+    ts = [np.ascontiguousarray(t, dtype=np.int32) for _, t in meshes]
+    n = len(meshes)
+    vp = (ctypes.c_void_p * n)(*[v.ctypes.data for v in vs])
+    tp = (ctypes.c_void_p * n)(*[t.ctypes.data for t in ts])
+    nv = np.array([v.shape[0] for v in vs], dtype=np.int64)
+    nt = np.array([t.shape[0] for t in ts], dtype=np.int64)
+    k = np.ascontiguousarray(ks, dtype=np.float64)
+    _bcheck(b, load().fda_build_batch(b, ctypes.cast(vp, ctypes.c_void_p), nv.ctypes.data,
+                                      ctypes.cast(tp, ctypes.c_void_p), nt.ctypes.data, k.ctypes.data))
+
+
+def fda_precompute_batch(b):
+    _bcheck(b, load().fda_precompute_batch(b))
+
+
+def fda_apply_batch(b, x_ptrs, y_ptrs, nrhs, lds):
+    """x_ptrs, y_ptrs: per-mesh device addresses; lds: per-mesh leading dimensions."""
+    import numpy as np
+    n = len(x_ptrs)
+    xp = (ctypes.c_void_p * n)(*x_ptrs)
+    yp = (ctypes.c_void_p * n)(*y_ptrs)
+    ld = np.ascontiguousarray(lds, dtype=np.int64)
+    _bcheck(b, load().fda_apply_batch(b, ctypes.cast(xp, ctypes.c_void_p), ctypes.cast(yp, ctypes.c_void_p),
+                                      int(nrhs), ld.ctypes.data))
+
+
+def fda_batch_mesh(b, i: int):
+    """The handle of mesh i (owned by the batch)."""
+    h = load().fda_batch_mesh(b, int(i))
+    if not h:
+        raise FDAError(FDA_ERR_ARG, "no mesh %d in the batch" % i)
+    return ctypes.c_void_p(h)
+
+
+def fda_get_batch_stats(b) -> fda_batch_stats:
+    s = fda_batch_stats()
+    _bcheck(b, load().fda_get_batch_stats(b, ctypes.byref(s)))
+    return s
+
+
+def fda_batch_last_error(b) -> str:
+    return load().fda_batch_last_error(b).decode()
+
+
+def fda_destroy_batch(b):
+    if b:
+        load().fda_destroy_batch(b)
 
 
 def fda_launch_count() -> int:

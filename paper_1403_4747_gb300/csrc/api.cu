@@ -224,13 +224,11 @@ fda_status fda_apply(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrhs, in
         const int mr = std::max(1, h->cfg.max_rhs);
         for (int m0 = 0; m0 < nrhs; m0 += mr) {
             int nm = std::min(mr, nrhs - m0);
-            for (int m = 0; m < nm; ++m)
-                fda_gather_to_sorted(h, reinterpret_cast<const c64d *>(x) + (int64_t)(m0 + m) * ld,
-                                     h->xs.as<c64d>() + (int64_t)m * h->N);
+            fda_gather_cols(h, reinterpret_cast<const c64d *>(x) + (int64_t)m0 * ld, ld, h->xs.as<c64d>(), nm,
+                            h->stream);
             fda_apply_staged(h, h->cfg.precision, nm);
-            for (int m = 0; m < nm; ++m)
-                fda_scatter_from_sorted(h, h->ys.as<c64d>() + (int64_t)m * h->N,
-                                        reinterpret_cast<c64d *>(y) + (int64_t)(m0 + m) * ld);
+            fda_scatter_cols(h, h->ys.as<c64d>(), reinterpret_cast<c64d *>(y) + (int64_t)m0 * ld, ld, nm,
+                             h->stream);
         }
     });
 }

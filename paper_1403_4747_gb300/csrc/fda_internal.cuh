@@ -303,6 +303,8 @@ void fda_rhs_sorted(fda_handle *h, const double *dirs_dev, int nrhs, c64d *b_sor
 void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
+void fda_gather_cols(fda_handle *h, const c64d *x, int64_t ld, c64d *xs, int nrhs, cudaStream_t s);
+void fda_scatter_cols(fda_handle *h, const c64d *ys, c64d *y, int64_t ld, int nrhs, cudaStream_t s);
 fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda_info *info);
 void fda_precond_build(fda_handle *h);
 void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z);

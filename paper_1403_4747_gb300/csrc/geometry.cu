@@ -314,6 +314,23 @@ void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs)
     FDA_CHECK_LAUNCH();
 }
 
+// nrhs columns at once: x (caller order, leading dimension ld) -> xs (Morton
+// order, leading dimension N), on stream s
+void fda_gather_cols(fda_handle *h, const c64d *x, int64_t ld, c64d *xs, int nrhs, cudaStream_t s)
+{
+    dim3 g(fda_blocks(h->N, 256), nrhs);
+    k_permute_c<<<g, 256, 0, s>>>(x, xs, h->perm.as<int32_t>(), h->N, ld, h->N, nrhs, 1);
+    FDA_CHECK_LAUNCH();
+}
+
+// ys (Morton order, leading dimension N) -> y (caller order, leading dimension ld)
+void fda_scatter_cols(fda_handle *h, const c64d *ys, c64d *y, int64_t ld, int nrhs, cudaStream_t s)
+{
+    dim3 g(fda_blocks(h->N, 256), nrhs);
+    k_permute_c<<<g, 256, 0, s>>>(ys, y, h->perm.as<int32_t>(), h->N, h->N, ld, nrhs, 0);
+    FDA_CHECK_LAUNCH();
+}
+
 // ys (Morton order) -> y (caller order)
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y)
 {

@@ -61,3 +61,52 @@ class FDAProblem:
             self.close()
         except Exception:
             pass
+
+
+class FDABatch:
+    """Several meshes behind one operator application (one CUDA graph per
+    call, one branch per mesh).  meshes: list of (verts, tris); ks: one
+    wavenumber per mesh."""
+
+    def __init__(self, meshes, ks, stream=None, **cfg):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("FDABatch needs a CUDA device; there is no CPU path")
+        c = _lib.fda_default_config(**cfg)
+        if stream is not None:
+            c.cuda_stream = stream.cuda_stream
+        self.b = _lib.fda_create_batch(c, len(meshes))
+        self.ns = [int(len(t)) for _, t in meshes]
+        self.ks = [float(k) for k in ks]
+        _lib.fda_build_batch(self.b, meshes, self.ks)
+        _lib.fda_precompute_batch(self.b)
+
+    def apply(self, xs, ys=None):
+        """xs: per mesh a complex128 CUDA tensor [nrhs, n_i] (or [n_i]); same nrhs for all."""
+        import torch
+        if ys is None:
+            ys = [torch.empty_like(x) for x in xs]
+        for t in list(xs) + list(ys):
+            if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+                raise TypeError("expected contiguous complex128 CUDA tensors")
+        nrhs = 1 if xs[0].dim() == 1 else xs[0].shape[0]
+        _lib.fda_apply_batch(self.b, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys], nrhs, self.ns)
+        return ys
+
+    def mesh(self, i):
+        """The handle of mesh i (owned by the batch)."""
+        return _lib.fda_batch_mesh(self.b, i)
+
+    def stats(self):
+        return _lib.fda_get_batch_stats(self.b)
+
+    def close(self):
+        if self.b:
+            _lib.fda_destroy_batch(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

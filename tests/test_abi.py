@@ -56,3 +56,18 @@ def test_null_handle_calls(lib):
     assert lib.fda_apply(None, None, None, 1, 1) == 1
     assert lib.fda_last_error(None) == b"null handle"
     lib.fda_destroy(None)
+
+
+def test_batch_arguments_rejected_without_gpu(lib):
+    import ctypes
+    from paper_1403_4747_gb300 import fda_default_config, fda_create_batch, FDAError, FDA_ERR_ARG
+    out = ctypes.c_void_p()
+    assert lib.fda_create_batch(None, 0, ctypes.byref(out)) == FDA_ERR_ARG and not out.value
+    assert lib.fda_create_batch(None, 65, ctypes.byref(out)) == FDA_ERR_ARG and not out.value
+    with pytest.raises(FDAError) as e:
+        fda_create_batch(fda_default_config(eps=0.0), 2)
+    assert e.value.status == FDA_ERR_ARG
+    assert lib.fda_apply_batch(None, None, None, 1, None) == FDA_ERR_ARG
+    assert lib.fda_batch_mesh(None, 0) is None
+    assert lib.fda_batch_last_error(None) == b"null batch"
+    lib.fda_destroy_batch(None)
