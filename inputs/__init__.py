@@ -10,8 +10,8 @@ The paper's own meshes (sphere families of Sec. 5, the Su-27 and submarine of
 Sec. 5.3) are not available; the icosphere family stands in for the sphere
 meshes of Table tab_usphpls and the plane-wave sphere of Sec. 5.3.
 """
-from .meshes import (icosphere, ellipsoid_from_icosphere, fibonacci_directions,
+from .meshes import (icosphere, octasphere, ellipsoid_from_icosphere, fibonacci_directions,
                      complex_normal, icosahedral_rotations, mesh_for_config, multi_mesh_set)
 
-__all__ = ["icosphere", "ellipsoid_from_icosphere", "fibonacci_directions",
+__all__ = ["icosphere", "octasphere", "ellipsoid_from_icosphere", "fibonacci_directions",
            "complex_normal", "icosahedral_rotations", "mesh_for_config", "multi_mesh_set"]

@@ -47,10 +47,10 @@ def _icosahedron():
     return v, f
 
 
-@functools.lru_cache(maxsize=8)
-def _icosphere_cached(level: int):
-    v, f = _icosahedron()
-    for _ in range(level):
+def _subdivide(v, f, levels):
+    """`levels` rounds of midpoint subdivision (each triangle into four) with
+    the new vertices projected onto the unit sphere; orientation kept."""
+    for _ in range(levels):
         nv = v.shape[0]
         e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]], axis=0)
         e.sort(axis=1)
@@ -72,6 +72,39 @@ def _icosphere_cached(level: int):
             np.stack([m01, m12, m20], axis=1),
         ], axis=0)
     return v, f.astype(np.int32)
+
+
+@functools.lru_cache(maxsize=8)
+def _icosphere_cached(level: int):
+    v, f = _icosahedron()
+    return _subdivide(v, f, level)
+
+
+def _octahedron():
+    """Regular octahedron (+-e_x, +-e_y, +-e_z), faces oriented outward."""
+    v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=np.float64)
+    faces = []
+    for i in (0, 1):
+        for j in (2, 3):
+            for k in (4, 5):
+                n = np.cross(v[j] - v[i], v[k] - v[i])
+                faces.append((i, j, k) if np.dot(n, v[i] + v[j] + v[k]) > 0 else (i, k, j))
+    return v, np.array(faces, dtype=np.int64)
+
+
+@functools.lru_cache(maxsize=8)
+def _octasphere_cached(level: int):
+    v, f = _octahedron()
+    return _subdivide(v, f, level)
+
+
+def octasphere(level: int):
+    """Unit sphere from the octahedron after `level` rounds of midpoint
+    subdivision with re-projection: 8 * 4**level flat triangles (level 3:
+    512, the coarsest sphere of the paper's pulsating-sphere family
+    N = 512 * 4**m)."""
+    v, f = _octasphere_cached(int(level))
+    return v.copy(), f.copy()
 
 
 def icosphere(level: int):

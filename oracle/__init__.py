@@ -16,13 +16,22 @@ Parity status per function:
       and with the Mie series).
   mie_surface_field / sphere_eigenvalues      : pinned (mpmath evaluation,
       Rayleigh limit, mutual consistency).
+  rhs_layers_matvec / rhs_layers_assemble /
+  self_single_layer                           : pinned (self integral by a
+      Duffy-transformed brute force and the equilateral closed form, operator
+      by the sphere eigenvalues beta_n and the k -> 0 potential of a uniform
+      layer, pulsating-sphere solution converging to 1/(1 - ik)).
 """
 from .api import (load, geometry, kernels, integrate_triangle, self_hypersingular, entry,
                   is_near_pair, matvec, assemble, rhs_plane_wave, num_threads, gauss_legendre,
-                  rule6, layer_rowsum)
+                  rule6, layer_rowsum, rhs_layers_matvec, rhs_layers_assemble, rhs_layers_entry,
+                  self_single_layer)
 from .solve import gmres, lu_solve
-from .closed_forms import mie_surface_field, sphere_eigenvalue, legendre_on_mesh
+from .closed_forms import (mie_surface_field, sphere_eigenvalue, legendre_on_mesh, sphere_rhs_eigenvalue,
+                           pulsating_sphere_potential)
 
 __all__ = ["load", "geometry", "kernels", "integrate_triangle", "self_hypersingular", "entry",
            "is_near_pair", "matvec", "assemble", "rhs_plane_wave", "num_threads", "gauss_legendre",
-           "rule6", "layer_rowsum", "gmres", "lu_solve", "mie_surface_field", "sphere_eigenvalue", "legendre_on_mesh"]
+           "rule6", "layer_rowsum", "gmres", "lu_solve", "mie_surface_field", "sphere_eigenvalue", "legendre_on_mesh",
+           "rhs_layers_matvec", "rhs_layers_assemble", "rhs_layers_entry", "self_single_layer",
+           "sphere_rhs_eigenvalue", "pulsating_sphere_potential"]

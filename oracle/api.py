@@ -36,6 +36,8 @@ def load():
         lib.orc_rule6.argtypes = [_dp, _dp]
         lib.orc_set_alpha_sign.argtypes = [dbl]
         lib.orc_layer_rowsum.argtypes = [_dp, _ip, i64, dbl, cint, _dp, cint]
+        lib.orc_set_side.argtypes = [cint]
+        lib.orc_self_single.argtypes = [_dp, _ip, i64, dbl, _dp]
         _lib = lib
     return _lib
 
@@ -163,3 +165,36 @@ def layer_rowsum(verts, tris, k, part, nthreads=0):
     out = np.empty(2 * n)
     load().orc_layer_rowsum(_d(v), t.ctypes.data_as(_ip), n, float(k), int(part), _d(out), int(nthreads))
     return out[0::2] + 1j * out[1::2]
+
+
+# ---- right-hand side's layers of Eq. eq_bm acting on Neumann data q = du/dn
+def _with_side(fn):
+    load().orc_set_side(1)
+    try:
+        return fn()
+    finally:
+        load().orc_set_side(0)
+
+
+def rhs_layers_matvec(verts, tris, k, q, rows=None, nthreads=0, alpha_sign=1.0):
+    """b = B q: b_i = -alpha q_i / 2 + sum_j int_{tri_j} [G + alpha dG/dn_x](x_i, y) dy q_j
+    (all rows or the listed rows; q complex [N] or [nrhs, N])."""
+    return _with_side(lambda: matvec(verts, tris, k, q, rows=rows, nthreads=nthreads, alpha_sign=alpha_sign))
+
+
+def rhs_layers_assemble(verts, tris, k, nthreads=0, alpha_sign=1.0):
+    """Dense B (row-major [N, N], small meshes only)."""
+    return _with_side(lambda: assemble(verts, tris, k, nthreads=nthreads, alpha_sign=alpha_sign))
+
+
+def rhs_layers_entry(verts, tris, k, i, j, alpha_sign=1.0):
+    load().orc_set_alpha_sign(float(alpha_sign))
+    return _with_side(lambda: entry(verts, tris, k, i, j, alpha_sign=alpha_sign))
+
+
+def self_single_layer(verts, tris, t, k):
+    """int over triangle t of G(x_t, y) dy, x_t its centroid."""
+    v, tr = _mesh(verts, tris)
+    out = np.empty(2)
+    load().orc_self_single(_d(v), tr.ctypes.data_as(_ip), int(t), float(k), _d(out))
+    return out[0] + 1j * out[1]

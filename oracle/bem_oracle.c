@@ -36,6 +36,17 @@
  *         angular integral is split per edge into its closed-form static
  *         part and a smooth remainder integrated by Gauss-Legendre.
  *
+ * The right-hand side's layers of Eq. eq_bm, acting on given Neumann data
+ * q = du/dn (a radiating body, u_inc = 0), discretised the same way:
+ *
+ *   (B q)_i = -alpha c q_i + sum_j B_ij q_j,
+ *   B_ij    = int_{tri_j} [ G + alpha dG/dn_x ](x_i, y) dy                 (i != j)
+ *   B_ii    = int_{tri_i} G(x_i, y) dy       (dG/dn_x vanishes: r.n_x = 0 on a flat triangle)
+ *
+ * with the same element rules; the weakly singular self integral is taken in
+ * polar coordinates about x_i, where the radial integral is closed:
+ *   int_tri G dA = (1/(4 pi)) int_0^{2 pi} (e^{ik rho(t)} - 1)/(ik) dt.
+ *
  * Kernels (r = x - y, R = |r|, derived from G; pinned by finite differences):
  *   G           = e^{ikR}/(4 pi R)
  *   dG/dn_y     = e^{ikR}(1 - ikR)(r.n_y)/(4 pi R^3)
@@ -135,14 +146,23 @@ void orc_set_alpha_sign(double s) { g_alpha_sign = s; }
  * alone.  Set once per exported call, before any parallel region. */
 static int g_part = 0;
 
-/* Burton-Miller layer kernel of Eq. eq_sum: dG/dn_y + alpha d2G/dn_x dn_y */
+/* Which side of Eq. eq_bm the integrals take: 0 the left-hand side (acting
+ * on u), 1 the right-hand side's layers (acting on q = du/dn).  Set once per
+ * exported call, before any parallel region. */
+static int g_side = 0;
+
+void orc_set_side(int side) { g_side = side; }
+
+/* Layer kernel: left-hand side of Eq. eq_sum, dG/dn_y + alpha d2G/dn_x dn_y;
+ * right-hand side, G + alpha dG/dn_x */
 static cplx kernel_bm(const double *x, const double *nx, const double *y, const double *ny, double k)
 {
     cplx o[4];
     kernels_all(x, nx, y, ny, k, o);
+    cplx alpha = g_alpha_sign * I / k;
+    if (g_side == 1) return o[0] + alpha * o[2];
     if (g_part == 1) return o[1];
     if (g_part == 2) return o[3];
-    cplx alpha = g_alpha_sign * I / k;
     return o[1] + alpha * o[3];
 }
 
@@ -255,9 +275,42 @@ static cplx self_hypersingular(const tri_t *T, double k)
     return I * k / 2.0 - acc / (4.0 * ORC_PI);
 }
 
-/* one matrix entry A_ij */
+/* int_tri G(x, y) dA about the interior point x (the centroid), in polar
+ * coordinates about x: per edge, with d the distance from x to the edge line
+ * and phi the angle from the perpendicular, rho(phi) = d/cos(phi) and
+ *   int_0^rho e^{ikr}/(4 pi r) r dr = (e^{ik rho} - 1)/(4 pi ik),
+ * integrated over phi by Gauss-Legendre. */
+static cplx self_single(const tri_t *T, double k)
+{
+    double gx[GL_SELF], gw[GL_SELF];
+    gauss_legendre(GL_SELF, gx, gw);
+    cplx acc = 0.0;
+    for (int e = 0; e < 3; ++e) {
+        const double *a = T->v[e], *b = T->v[(e + 1) % 3];
+        double t[3], xa[3];
+        sub3(b, a, t);
+        double L = sqrt(dot3(t, t));
+        for (int d = 0; d < 3; ++d) t[d] /= L;
+        sub3(T->c, a, xa);
+        double s = dot3(xa, t);
+        double foot[3], dv[3];
+        for (int d = 0; d < 3; ++d) foot[d] = a[d] + s * t[d];
+        sub3(T->c, foot, dv);
+        double dist = sqrt(dot3(dv, dv));
+        double pa = atan2(-s, dist), pb = atan2(L - s, dist);
+        double half = 0.5 * (pb - pa), mid = 0.5 * (pb + pa);
+        for (int g = 0; g < GL_SELF; ++g) {
+            double rho = dist / cos(mid + half * gx[g]);
+            acc += half * gw[g] * (cexp(I * k * rho) - 1.0) / (I * k);
+        }
+    }
+    return acc / (4.0 * ORC_PI);
+}
+
+/* one matrix entry A_ij (left-hand side) or B_ij (right-hand side) */
 static cplx entry(const tri_t *Ti, const tri_t *Tj, int same, double k)
 {
+    if (same && g_side == 1) return -0.5 * (g_alpha_sign * I / k) + self_single(Ti, k);
     if (same) {
         if (g_part == 1) return 0.5;
         if (g_part == 2) return self_hypersingular(Ti, k);
@@ -389,6 +442,16 @@ void orc_layer_rowsum(const double *verts, const int32_t *tris, int64_t nt, doub
     }
     g_part = 0;
     free(T);
+}
+
+/* int_tri G(x_t, y) dy over triangle t from its own centroid (interleaved complex) */
+void orc_self_single(const double *verts, const int32_t *tris, int64_t t, double k, double *out)
+{
+    tri_t T;
+    make_tri(verts, tris, t, &T);
+    cplx v = self_single(&T, k);
+    out[0] = creal(v);
+    out[1] = cimag(v);
 }
 
 /* single entry A_ij (interleaved complex) */

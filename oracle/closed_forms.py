@@ -16,6 +16,18 @@ A = 1/2 + D + alpha H (D double layer with n, H hypersingular):
     lambda_n = 1/2 - (i k^2/2)(j_n' h_n + j_n h_n') - k^2 j_n' h_n',
 from the addition theorem (the double layer's principal value is the mean
 of its two one-sided limits; H is continuous across the sphere).
+
+Right-hand side's layers of Eq. eq_bm acting on q = du/dn,
+B = -alpha/2 + S + alpha K' (S single layer, K' its normal derivative in n,
+direct value): B[P_n] = beta_n P_n,
+    beta_n = -alpha/2 + i k j_n h_n - alpha (i k^2/2)(j_n h_n' + j_n' h_n),
+since S[Y_n] = i k j_n h_n Y_n on the unit sphere and the radial derivative
+of the single-layer potential is i k^2 j_n h_n' outside and i k^2 j_n' h_n
+inside (their mean is the direct value in nu; n = -nu flips its sign).
+
+Pulsating unit sphere (Sec. 5.1), du/dn = 1 with n into the body: the
+radiating solution u = A e^{ikr}/r gives u = 1/(1 - ik) on the surface
+(beta_0 / lambda_0 equals it for either sign of alpha).
 """
 from __future__ import annotations
 
@@ -59,3 +71,18 @@ def legendre_on_mesh(centroids, n: int, axis=(0.0, 0.0, 1.0)):
     c = np.asarray(centroids, dtype=np.float64)
     u = c / np.linalg.norm(c, axis=1, keepdims=True)
     return special.eval_legendre(n, u @ np.asarray(axis, dtype=np.float64))
+
+
+def sphere_rhs_eigenvalue(n: int, k: float, alpha_sign: float = 1.0) -> complex:
+    """beta_n for alpha = alpha_sign i/k: -alpha/2 + S + alpha K' on P_n."""
+    jn = special.spherical_jn(n, k)
+    jd = special.spherical_jn(n, k, derivative=True)
+    hn = _h1(n, k)
+    hd = _h1(n, k, derivative=True)
+    alpha = alpha_sign * 1j / k
+    return -0.5 * alpha + 1j * k * jn * hn - alpha * 0.5j * k * k * (jn * hd + jd * hn)
+
+
+def pulsating_sphere_potential(k: float) -> complex:
+    """Surface potential of the unit sphere pulsating with du/dn = 1 (n into the body)."""
+    return 1.0 / (1.0 - 1j * k)
