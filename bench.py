@@ -559,6 +559,57 @@ def run_many_meshes(args):
     return 0
 
 
+def run_pulsating(args):
+    """The pulsating unit sphere of Sec. 5.1 over the paper's sphere family
+    N = 512 * 4^m, k = pi 2^m (octahedral spheres, m = 0..6): right-hand side
+    of the Burton-Miller equation for du/dn = 1 by the fast directional
+    algorithm, GMRES to tol = eps, error against 1/(1 - ik); eps = 1e-3 and
+    1e-4, chosen form.  The shape of Table tab_usphpls; not the headline
+    workload (--workload pulsating)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import octasphere
+    rows = []
+    max_level = min(9, args.pulsating_max_level)
+    for eps in (1e-3, 1e-4):
+        for level in range(3, max_level + 1):
+            m = level - 3
+            k = math.pi * 2 ** m
+            v, f = octasphere(level)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P = F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, eps=eps, alpha_sign=args.alpha_sign)
+            q = torch.ones(len(f), dtype=torch.complex128, device="cuda")
+            b = P.rhs_neumann(q)
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
+            u, info = P.solve(b, eps, raise_on_not_converged=False)
+            ue = 1.0 / (1.0 - 1j * k)
+            un = u.cpu().numpy()
+            err = float(np.linalg.norm(un - ue) / (abs(ue) * math.sqrt(len(f))))
+            st = P.stats()
+            rows.append({"N": len(f), "k_over_pi": 2 ** m, "eps": eps, "alpha_sign": args.alpha_sign,
+                         "setup_s": round(setup_s, 3),
+                         "solve_s": round(info.solve_s, 4), "iters": info.iters,
+                         "matvec_ms": round(info.matvec_s * 1e3, 3), "rel_resid": info.rel_resid_fp64,
+                         "l2_error": err, "device_gb": round(st.device_bytes / 1e9, 2)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            P.close()
+            del P, q, b, u
+            torch.cuda.empty_cache()
+    line = {"metric": "pulsating unit sphere: solve time and L2 error vs N (Table tab_usphpls shape)",
+            "value": rows[-1]["solve_s"] if rows else None, "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f32+bf16x3/f64", "data": "synthetic",
+            "config": {"workload": "octahedral unit spheres N = 512 4^m, k = pi 2^m, du/dn = 1, chosen form"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -579,8 +630,11 @@ def main():
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes"],
-                    help="many_meshes: the eight-mesh batch instead of the headline line")
+    ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes", "pulsating"],
+                    help="many_meshes: the eight-mesh batch; pulsating: the pulsating-sphere study")
+    ap.add_argument("--pulsating-max-level", type=int, default=9)
+    ap.add_argument("--alpha-sign", type=float, default=-1.0, choices=[-1.0, 1.0],
+                    help="coupling alpha = sign * i/k of the pulsating study (-1: the paper's time convention)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -588,6 +642,8 @@ def main():
         return run_reference(args)
     if args.workload == "many_meshes":
         return run_many_meshes(args)
+    if args.workload == "pulsating":
+        return run_pulsating(args)
     return run_native(args)
 
 

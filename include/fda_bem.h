@@ -160,6 +160,21 @@ fda_status fda_apply_host(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrh
  * dirs: host double[nrhs][3] unit vectors; b: device, ld = nt. */
 fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b);
 
+/* Right-hand side of Eq. eq_bm for a radiating body with given Neumann data
+ * q = du/dn (no incident field), the layers of the equation's right-hand
+ * side evaluated by the same fast directional algorithm (Sec. 3.3 Steps 2-4
+ * with single-layer sources):
+ *   b_i = -alpha q_i / 2 + sum_j int_{tri_j} [ G + alpha dG/dn_x ](x_i, y) dy q_j
+ * (c = 1/2 at a centroid; the adjoint double layer vanishes on the element
+ * itself).  q, b: device, nrhs columns with leading dimension ld >= nt, not
+ * overlapping; the handle's precision applies (chosen: FP32 near field and
+ * split-bf16 translations).  The first call builds this side's near field
+ * and single-layer S2M operators (FP64 quadrature; about the cost and memory
+ * of the operator's own near field) and synchronises; later calls are
+ * stream-ordered.  For a body that also scatters an incident wave, add
+ * fda_rhs_plane_wave's result. */
+fda_status fda_rhs_neumann(fda_handle *h, const fda_c128 *q, fda_c128 *b, int nrhs, int64_t ld);
+
 /* Allocation-free variant of fda_rhs_plane_wave, for callers that must not
  * have the library allocate device memory during the call: real-time loops
  * that forbid allocator calls (cudaMalloc / cudaFree can synchronise the

@@ -14,7 +14,6 @@
 #include "fda_internal.cuh"
 
 void fda_alloc_densities(fda_handle *h, int want32);
-void fda_near_convert_f32(fda_handle *h);
 void fda_far_convert_f32(fda_handle *h);
 
 static std::atomic<long long> g_launches{0};
@@ -85,6 +84,7 @@ size_t handle_bytes(const fda_handle *h)
                           &h->leaf_of_box, &h->il_ptr, &h->il_src, &h->il_op, &h->il_cone, &h->nr_ptr,
                           &h->nr_begin, &h->nr_end, &h->nf_colptr, &h->nf_cols, &h->nf_off, &h->leaf_op_off,
                           &h->op64.St, &h->op64.Tt, &h->op64.near, &h->op32.St, &h->op32.Tt, &h->op32.near,
+                          &h->op64.St1, &h->op64.near1, &h->op32.St1, &h->op32.near1,
                           &h->xs, &h->ys, &h->xs32};
     for (const dbuf *b : bufs) s += b->bytes;
     for (int l = 0; l < FDA_MAX_LEVELS; ++l) {
@@ -260,6 +260,31 @@ fda_status fda_apply_host(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrh
                                      h->stream));
         }
         FDA_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+fda_status fda_rhs_neumann(fda_handle *h, const fda_c128 *q, fda_c128 *b, int nrhs, int64_t ld)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = "fda_rhs_neumann before fda_precompute_translations";
+        return FDA_ERR_STATE;
+    }
+    if (!q || !b || nrhs < 1 || ld < h->N) {
+        h->err = "invalid fda_rhs_neumann arguments";
+        return FDA_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        fda_rhs_layers_prepare(h);
+        const int mr = std::max(1, h->cfg.max_rhs);
+        for (int m0 = 0; m0 < nrhs; m0 += mr) {
+            int nm = std::min(mr, nrhs - m0);
+            fda_gather_cols(h, reinterpret_cast<const c64d *>(q) + (int64_t)m0 * ld, ld, h->xs.as<c64d>(), nm,
+                            h->stream);
+            fda_apply_sorted(h, h->xs.as<c64d>(), h->ys.as<c64d>(), h->cfg.precision, nm, 1);
+            fda_scatter_cols(h, h->ys.as<c64d>(), reinterpret_cast<c64d *>(b) + (int64_t)m0 * ld, ld, nm,
+                             h->stream);
+        }
     });
 }
 

@@ -217,9 +217,15 @@ lvl_ptrs<R> make_ptrs(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p)
     return P;
 }
 
+// side 0: the Burton-Miller operator of Eq. eq_sum applied to u; side 1: the
+// right-hand side's layers of Eq. eq_bm applied to q = du/dn (its own near
+// field and single-layer S2M; every translation and the L2T are shared)
 template <typename R>
-void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x, int x64, c64d *y, int mr)
+void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x, int x64, c64d *y, int mr,
+                int side)
 {
+    const dbuf &near = side ? ops.near1 : ops.near;
+    const dbuf &St = side ? ops.St1 : ops.St;
     const int64_t N = h->N;
     cudaStream_t s = h->stream;
     const int NL = h->nleaf;
@@ -240,19 +246,19 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         k_near_apply<R, 1, true><<<gn, AT, xs_bytes, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                           h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
                                                           h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                                          ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+                                                          near.template as<cx<R>>(), x, x64, N, mr, y, N);
     } else if (mr == 1) {
         dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
         k_near_apply<R, 1, false><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                     h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
                                                     h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                                    ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+                                                    near.template as<cx<R>>(), x, x64, N, mr, y, N);
     } else {
         dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), (mr + NRG - 1) / NRG);
         k_near_apply<R, NRG, false><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                       h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
                                                       h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                                      ops.near.template as<cx<R>>(), x, x64, N, mr, y, N);
+                                                      near.template as<cx<R>>(), x, x64, N, mr, y, N);
     }
     FDA_CHECK_LAUNCH();
     mark(1);
@@ -269,7 +275,7 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     }
     k_s2m<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
                                h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(),
-                               ops.St.template as<cx<R>>(), x, x64, N, mr);
+                               St.template as<cx<R>>(), x, x64, N, mr);
     FDA_CHECK_LAUNCH();
     mark(2);
     // tensor cores (chosen precision): every translation reads bf16 hi/lo
@@ -336,7 +342,7 @@ void fda_alloc_densities(fda_handle *h, int want32)
 }
 
 // ys = A xs, both complex double in Morton order
-void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, int mr)
+void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, int mr, int side)
 {
     if (mr < 1 || mr > std::max(1, h->cfg.max_rhs)) fda_fail(FDA_ERR_ARG, "more right-hand sides than max_rhs");
     if (precision == FDA_CHOSEN_FP32) {
@@ -344,9 +350,9 @@ void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, in
         if (!h->xs32.p) h->xs32.alloc(sizeof(c32f) * h->N * std::max(1, h->cfg.max_rhs));
         k_c64_to_c32<<<fda_blocks(h->N * mr, 256), 256, 0, h->stream>>>(xs, h->xs32.as<c32f>(), h->N * mr);
         FDA_CHECK_LAUNCH();
-        apply_impl<float>(h, h->op32, h->q32, h->p32, h->xs32.p, 0, ys, mr);
+        apply_impl<float>(h, h->op32, h->q32, h->p32, h->xs32.p, 0, ys, mr, side);
     } else {
-        apply_impl<double>(h, h->op64, h->q64, h->p64, xs, 1, ys, mr);
+        apply_impl<double>(h, h->op64, h->q64, h->p64, xs, 1, ys, mr, side);
     }
     if (h->timing) {
         FDA_CUDA(cudaEventSynchronize(h->ev[6]));

@@ -170,8 +170,10 @@ struct far_ops {
     dbuf Mt[FDA_MAX_LEVELS];     // parent level: [8 * ncones][T_child][T] column-major
     dbuf Lt[FDA_MAX_LEVELS];     // parent level: [8 * ncones][T][T_child] column-major (rows = child rank)
     dbuf St;                     // per leaf: [n_B][T] (S~ transposed)
+    dbuf St1;                    // the same for single-layer sources (right-hand side's layers; built on demand)
     dbuf Tt;                     // per leaf: [T][n_B] (T~ column-major)
     dbuf near;                   // near-field blocks, row-major per leaf
+    dbuf near1;                  // right-hand side's layers on the same pattern (built on demand)
 };
 
 struct fda_handle {
@@ -239,6 +241,7 @@ struct fda_handle {
     far_ops<double> op64;
     far_ops<float> op32;
     int have32 = 0;
+    int rhs_layers = 0;  // near field and S2M of the right-hand side's layers built
 
     // tensor-core M2L (chosen precision)
     tc_ops tc_m2l[FDA_MAX_LEVELS], tc_m2m[FDA_MAX_LEVELS], tc_l2l[FDA_MAX_LEVELS];
@@ -293,9 +296,16 @@ struct fda_handle {
 // ---------------------------------------------------------------------------
 void fda_geometry_build(fda_handle *h, const double *verts, int64_t nv, const int32_t *tris, int64_t nt);
 void fda_tree_build(fda_handle *h);
-void fda_near_build(fda_handle *h);
+void fda_near_build(fda_handle *h, int side = 0);
+void fda_near_convert_f32(fda_handle *h, int side = 0);
+// S~ of the right-hand side's layers (single-layer sources) for every leaf
+void fda_far_rhs_s2m(fda_handle *h);
+void fda_far_rhs_convert_f32(fda_handle *h);
 void fda_far_precompute(fda_handle *h);
-void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, int mr = 1);
+// side 0: the Burton-Miller operator (unknown u); side 1: the right-hand
+// side's layers acting on q = du/dn (needs fda_rhs_layers_prepare)
+void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, int mr = 1, int side = 0);
+void fda_rhs_layers_prepare(fda_handle *h);
 // h->ys = A h->xs (sorted order, mr right-hand sides) through the graph cache
 void fda_apply_staged(fda_handle *h, int precision, int mr);
 void fda_graphs_release(fda_handle *h);

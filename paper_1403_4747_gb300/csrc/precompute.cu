@@ -173,8 +173,11 @@ __global__ void k_kmat(const kmat_job *jobs, double k)
     }
 }
 
-// S2M sources: E[c][j] = sum_q w_jq dG/dn_y(x_c, y_jq), x_c = check points of
-// the leaf, j < n_B (padded to 64 columns)
+// S2M sources: E[c][j] = sum_q w_jq dG/dn_y(x_c, y_jq) (SIDE 0, the double
+// layer of the unknown u) or sum_q w_jq G(x_c, y_jq) (SIDE 1, the single
+// layer of given Neumann data), x_c = check points of the leaf, j < n_B
+// (padded to 64 columns)
+template <int SIDE>
 __global__ void k_emat_s2m(const double *chk, int nchk, const double *centers, const int32_t *leaf_list,
                            const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend, const double *qpt,
                            const double *qw, const double *nrm, double k, c64d *out)
@@ -198,6 +201,12 @@ __global__ void k_emat_s2m(const double *chk, int nchk, const double *centers, c
                 double R2 = r0 * r0 + r1 * r1 + r2 * r2, R = sqrt(R2);
                 double s, cc;
                 sincos(k * R, &s, &cc);
+                if (SIDE == 1) {
+                    double g = qw[6 * (int64_t)j + q] / (4.0 * FDA_PI * R);
+                    acc.re += g * cc;
+                    acc.im += g * s;
+                    continue;
+                }
                 double f = qw[6 * (int64_t)j + q] * (r0 * ny[0] + r1 * ny[1] + r2 * ny[2]) / (4.0 * FDA_PI * R2 * R);
                 // e^{ikR}(1 - ikR) f
                 acc.re += f * (cc + k * R * s);
@@ -565,6 +574,94 @@ int fda_child_cone(const fda_handle *h, int l, int u)
     return face * ncc * ncc + (a / f) * ncc + (b / f);
 }
 
+// Per-leaf S~ (and, for side 0, T~) at the active levels (leaves are low
+// frequency).  side 0: S~ of the double-layer sources and T~; side 1: S~ of
+// the single-layer sources of the right-hand side's layers (same check
+// points, pseudo-inverse and layout).
+static void leaf_operators(fda_handle *h, int side)
+{
+    cudaStream_t s = h->stream;
+    const int nlev = h->nlev;
+    std::vector<int32_t> hbox_coord(3 * (size_t)h->nbox_total), hleaf_box(h->nleaf);
+    std::vector<int32_t> hbeg(h->nbox_total), hend(h->nbox_total);
+    FDA_CUDA(cudaMemcpy(hbox_coord.data(), h->box_coord.p, 12 * (size_t)h->nbox_total, cudaMemcpyDeviceToHost));
+    FDA_CUDA(cudaMemcpy(hleaf_box.data(), h->leaf_box.p, 4 * (size_t)h->nleaf, cudaMemcpyDeviceToHost));
+    FDA_CUDA(cudaMemcpy(hbeg.data(), h->box_begin.p, 4 * (size_t)h->nbox_total, cudaMemcpyDeviceToHost));
+    FDA_CUDA(cudaMemcpy(hend.data(), h->box_end.p, 4 * (size_t)h->nbox_total, cudaMemcpyDeviceToHost));
+    std::vector<int64_t> off(h->nleaf + 1, 0);
+    for (int li = 0; li < h->nleaf; ++li) {
+        int l = h->h_leaf_level[li];
+        int T = h->lev[l].active ? h->lev[l].T : 0;
+        off[li + 1] = off[li] + (int64_t)64 * T;
+    }
+    dbuf &St = side ? h->op64.St1 : h->op64.St;
+    if (side == 0) {
+        h->leaf_T_off.assign(off.begin(), off.end() - 1);
+        h->leaf_op_off.alloc(sizeof(int64_t) * (h->nleaf + 1));
+        FDA_CUDA(cudaMemcpy(h->leaf_op_off.p, off.data(), sizeof(int64_t) * (h->nleaf + 1), cudaMemcpyHostToDevice));
+        h->op64.Tt.alloc(sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1));
+        FDA_CUDA(cudaMemset(h->op64.Tt.p, 0, sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1)));
+    }
+    St.alloc(sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1));
+    FDA_CUDA(cudaMemset(St.p, 0, sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1)));
+    for (int l = h->lev_lo; l < nlev; ++l) {
+        level_info &L = h->lev[l];
+        std::vector<int32_t> lv;
+        for (int li = 0; li < h->nleaf; ++li)
+            if (h->h_leaf_level[li] == l) lv.push_back(li);
+        if (lv.empty()) continue;
+        const int T = L.T, nchk = L.n_chk, neq = L.n_eq;
+        const int chunk = std::max(1, (int)std::min<int64_t>(4096, (int64_t)(768ll << 20) / (16ll * 64 * nchk)));
+        dbuf dlist, dctr, E, R;
+        dlist.alloc(sizeof(int32_t) * chunk);
+        dctr.alloc(sizeof(double) * 3 * chunk);
+        E.alloc(sizeof(c64d) * (size_t)chunk * 64 * std::max(nchk, neq));
+        R.alloc(sizeof(c64d) * (size_t)chunk * 64 * T);
+        for (size_t c0 = 0; c0 < lv.size(); c0 += chunk) {
+            int nb = (int)std::min<size_t>(chunk, lv.size() - c0);
+            std::vector<double> ctr(3 * nb);
+            for (int b = 0; b < nb; ++b) box_center_host(h, &hbox_coord[3 * (size_t)hleaf_box[lv[c0 + b]]], l, &ctr[3 * b]);
+            FDA_CUDA(cudaMemcpy(dlist.p, &lv[c0], 4 * nb, cudaMemcpyHostToDevice));
+            FDA_CUDA(cudaMemcpy(dctr.p, ctr.data(), 8 * 3 * nb, cudaMemcpyHostToDevice));
+            // S2M: E_s (nchk x 64) then S~ = S^-1 U^H E_s  (T x 64), stored as [64][T]
+            auto emat = side ? k_emat_s2m<1> : k_emat_s2m<0>;
+            emat<<<dim3(32, nb), 256, 0, s>>>(h->chk_up[l].as<double>(), nchk, dctr.as<double>(),
+                                                   dlist.as<int32_t>(), h->leaf_box.as<int32_t>(),
+                                                   h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
+                                                   h->qpt.as<double>(), h->qw.as<double>(), h->nrm.as<double>(),
+                                                   h->k, E.as<c64d>());
+            FDA_CHECK_LAUNCH();
+            std::vector<gemm_job> gj(nb);
+            for (int b = 0; b < nb; ++b)
+                gj[b] = gemm_job{h->Uup[l].as<c64d>(), E.as<c64d>() + (size_t)b * nchk * 64,
+                                 St.as<c64d>() + off[lv[c0 + b]]};
+            run_gemm(h, gj, T, 64, nchk, nchk, nchk, T, 2, 0);
+            for (int b = 0; b < nb; ++b) {
+                k_scale_inv<<<dim3(16, 1), 256, 0, s>>>(St.as<c64d>() + off[lv[c0 + b]], T, 64, T, 0,
+                                                        h->sig[l].as<double>(), 1);
+            }
+            FDA_CHECK_LAUNCH();
+            if (side) continue;
+            // L2T: E_t (64 x n_eq_dn = nchk) then T~ = E_t conj(U) S^-1 (64 x T)
+            k_emat_l2t<<<dim3(32, nb), 256, 0, s>>>(h->chk_up[l].as<double>(), nchk, dctr.as<double>(),
+                                                   dlist.as<int32_t>(), h->leaf_box.as<int32_t>(),
+                                                   h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
+                                                   h->cent.as<double>(), h->nrm.as<double>(), h->k,
+                                                   h->cfg.alpha_sign, E.as<c64d>());
+            FDA_CHECK_LAUNCH();
+            for (int b = 0; b < nb; ++b)
+                gj[b] = gemm_job{E.as<c64d>() + (size_t)b * 64 * nchk, h->Uup[l].as<c64d>(),
+                                 h->op64.Tt.as<c64d>() + off[lv[c0 + b]]};
+            run_gemm(h, gj, 64, T, nchk, 64, nchk, 64, 0, 1);
+            for (int b = 0; b < nb; ++b) {
+                k_scale_inv<<<dim3(16, 1), 256, 0, s>>>(h->op64.Tt.as<c64d>() + off[lv[c0 + b]], 64, T, 64, 0,
+                                                        h->sig[l].as<double>(), 0);
+            }
+            FDA_CHECK_LAUNCH();
+        }
+    }
+}
+
 void fda_far_precompute(fda_handle *h)
 {
     cudaStream_t s = h->stream;
@@ -729,81 +826,39 @@ void fda_far_precompute(fda_handle *h)
         }
     }
 
-    // ---- per-leaf S~ and T~ (leaves at active levels; leaves are low frequency)
-    std::vector<int32_t> hbox_coord(3 * (size_t)h->nbox_total), hleaf_box(h->nleaf);
-    std::vector<int32_t> hbeg(h->nbox_total), hend(h->nbox_total);
-    FDA_CUDA(cudaMemcpy(hbox_coord.data(), h->box_coord.p, 12 * (size_t)h->nbox_total, cudaMemcpyDeviceToHost));
-    FDA_CUDA(cudaMemcpy(hleaf_box.data(), h->leaf_box.p, 4 * (size_t)h->nleaf, cudaMemcpyDeviceToHost));
-    FDA_CUDA(cudaMemcpy(hbeg.data(), h->box_begin.p, 4 * (size_t)h->nbox_total, cudaMemcpyDeviceToHost));
-    FDA_CUDA(cudaMemcpy(hend.data(), h->box_end.p, 4 * (size_t)h->nbox_total, cudaMemcpyDeviceToHost));
-    std::vector<int64_t> off(h->nleaf + 1, 0);
-    for (int li = 0; li < h->nleaf; ++li) {
-        int l = h->h_leaf_level[li];
-        int T = h->lev[l].active ? h->lev[l].T : 0;
-        off[li + 1] = off[li] + (int64_t)64 * T;
-    }
-    h->leaf_T_off.assign(off.begin(), off.end() - 1);
-    h->leaf_op_off.alloc(sizeof(int64_t) * (h->nleaf + 1));
-    FDA_CUDA(cudaMemcpy(h->leaf_op_off.p, off.data(), sizeof(int64_t) * (h->nleaf + 1), cudaMemcpyHostToDevice));
-    h->op64.St.alloc(sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1));
-    h->op64.Tt.alloc(sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1));
-    FDA_CUDA(cudaMemset(h->op64.St.p, 0, sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1)));
-    FDA_CUDA(cudaMemset(h->op64.Tt.p, 0, sizeof(c64d) * std::max<int64_t>(off[h->nleaf], 1)));
-    for (int l = h->lev_lo; l < nlev; ++l) {
-        level_info &L = h->lev[l];
-        std::vector<int32_t> lv;
-        for (int li = 0; li < h->nleaf; ++li)
-            if (h->h_leaf_level[li] == l) lv.push_back(li);
-        if (lv.empty()) continue;
-        const int T = L.T, nchk = L.n_chk, neq = L.n_eq;
-        const int chunk = std::max(1, (int)std::min<int64_t>(4096, (int64_t)(768ll << 20) / (16ll * 64 * nchk)));
-        dbuf dlist, dctr, E, R;
-        dlist.alloc(sizeof(int32_t) * chunk);
-        dctr.alloc(sizeof(double) * 3 * chunk);
-        E.alloc(sizeof(c64d) * (size_t)chunk * 64 * std::max(nchk, neq));
-        R.alloc(sizeof(c64d) * (size_t)chunk * 64 * T);
-        for (size_t c0 = 0; c0 < lv.size(); c0 += chunk) {
-            int nb = (int)std::min<size_t>(chunk, lv.size() - c0);
-            std::vector<double> ctr(3 * nb);
-            for (int b = 0; b < nb; ++b) box_center_host(h, &hbox_coord[3 * (size_t)hleaf_box[lv[c0 + b]]], l, &ctr[3 * b]);
-            FDA_CUDA(cudaMemcpy(dlist.p, &lv[c0], 4 * nb, cudaMemcpyHostToDevice));
-            FDA_CUDA(cudaMemcpy(dctr.p, ctr.data(), 8 * 3 * nb, cudaMemcpyHostToDevice));
-            // S2M: E_s (nchk x 64) then S~ = S^-1 U^H E_s  (T x 64), stored as [64][T]
-            k_emat_s2m<<<dim3(32, nb), 256, 0, s>>>(h->chk_up[l].as<double>(), nchk, dctr.as<double>(),
-                                                   dlist.as<int32_t>(), h->leaf_box.as<int32_t>(),
-                                                   h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
-                                                   h->qpt.as<double>(), h->qw.as<double>(), h->nrm.as<double>(),
-                                                   h->k, E.as<c64d>());
-            FDA_CHECK_LAUNCH();
-            std::vector<gemm_job> gj(nb);
-            for (int b = 0; b < nb; ++b)
-                gj[b] = gemm_job{h->Uup[l].as<c64d>(), E.as<c64d>() + (size_t)b * nchk * 64,
-                                 h->op64.St.as<c64d>() + off[lv[c0 + b]]};
-            run_gemm(h, gj, T, 64, nchk, nchk, nchk, T, 2, 0);
-            for (int b = 0; b < nb; ++b) {
-                k_scale_inv<<<dim3(16, 1), 256, 0, s>>>(h->op64.St.as<c64d>() + off[lv[c0 + b]], T, 64, T, 0,
-                                                        h->sig[l].as<double>(), 1);
-            }
-            FDA_CHECK_LAUNCH();
-            // L2T: E_t (64 x n_eq_dn = nchk) then T~ = E_t conj(U) S^-1 (64 x T)
-            k_emat_l2t<<<dim3(32, nb), 256, 0, s>>>(h->chk_up[l].as<double>(), nchk, dctr.as<double>(),
-                                                   dlist.as<int32_t>(), h->leaf_box.as<int32_t>(),
-                                                   h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
-                                                   h->cent.as<double>(), h->nrm.as<double>(), h->k,
-                                                   h->cfg.alpha_sign, E.as<c64d>());
-            FDA_CHECK_LAUNCH();
-            for (int b = 0; b < nb; ++b)
-                gj[b] = gemm_job{E.as<c64d>() + (size_t)b * 64 * nchk, h->Uup[l].as<c64d>(),
-                                 h->op64.Tt.as<c64d>() + off[lv[c0 + b]]};
-            run_gemm(h, gj, 64, T, nchk, 64, nchk, 64, 0, 1);
-            for (int b = 0; b < nb; ++b) {
-                k_scale_inv<<<dim3(16, 1), 256, 0, s>>>(h->op64.Tt.as<c64d>() + off[lv[c0 + b]], 64, T, 64, 0,
-                                                        h->sig[l].as<double>(), 0);
-            }
-            FDA_CHECK_LAUNCH();
-        }
-    }
+    leaf_operators(h, 0);
     FDA_CUDA(cudaStreamSynchronize(s));
+}
+
+void fda_far_rhs_s2m(fda_handle *h)
+{
+    if (h->lev_lo < 0) return;
+    leaf_operators(h, 1);
+    FDA_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void fda_far_rhs_convert_f32(fda_handle *h)
+{
+    if (!h->op64.St1.p) return;
+    int64_t n = (int64_t)(h->op64.St1.bytes / sizeof(c64d));
+    h->op32.St1.alloc(sizeof(c32f) * n);
+    k_f64_to_f32<<<1024, 256, 0, h->stream>>>(h->op64.St1.as<c64d>(), h->op32.St1.as<c32f>(), n);
+    FDA_CHECK_LAUNCH();
+    FDA_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// near field and single-layer S2M of the right-hand side's layers, once
+void fda_rhs_layers_prepare(fda_handle *h)
+{
+    if (h->rhs_layers) return;
+    fda_near_build(h, 1);
+    fda_far_rhs_s2m(h);
+    if (h->have32) {
+        fda_near_convert_f32(h, 1);
+        fda_far_rhs_convert_f32(h);
+    }
+    FDA_CUDA(cudaStreamSynchronize(h->stream));
+    h->rhs_layers = 1;
 }
 
 // FP32 copies of every far-field operator (chosen precision)

@@ -15,6 +15,15 @@
 //     for the smooth remainder (e^{ik rho} - 1)/rho.
 // All of it in FP64: these are the singular and near-singular integrals the
 // method keeps in double precision.
+//
+// The same rules also build the near field of the right-hand side's layers
+// of Eq. eq_bm for given Neumann data q = du/dn (side 1):
+//   B_ij = int_{tri_j} [ G + alpha dG/dn_x ](x_i, y) dy,
+//   B_ii = -alpha/2 + int_{tri_i} G(x_i, y) dy   (dG/dn_x vanishes in the plane),
+// the weakly singular self integral in polar coordinates about x_i, whose
+// radial part is closed: per edge int (e^{ik rho} - 1)/(4 pi ik) dphi,
+// written as rho e^{ik rho/2} sin(k rho/2)/(k rho/2) (no cancellation at
+// small k rho), by the 16-point Gauss-Legendre rule.
 #include <math.h>
 
 #include <vector>
@@ -55,6 +64,32 @@ __device__ inline c64d bm_kernel(const double *x, const double *nx, const double
     return c64d(dl.re - as * hs.im / k, dl.im + as * hs.re / k);
 }
 
+// right-hand side's layer kernel: G + alpha dG/dn_x, r = x - y
+__device__ inline c64d rhs_kernel(const double *x, const double *nx, const double *y, double k, double as)
+{
+    double r0 = x[0] - y[0], r1 = x[1] - y[1], r2 = x[2] - y[2];
+    double R2 = r0 * r0 + r1 * r1 + r2 * r2;
+    double R = sqrt(R2);
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    double g = 1.0 / (4.0 * FDA_PI * R);
+    double rnx = r0 * nx[0] + r1 * nx[1] + r2 * nx[2];
+    // dG/dn_x = -e^{ikR}(1 - ikR) rnx/(4 pi R^3)
+    double f = -rnx * g / R2;
+    double dre = f * (cs + k * R * sn), dim = f * (sn - k * R * cs);
+    // G + as (i/k) dG/dn_x
+    return c64d(cs * g - as * dim / k, sn * g + as * dre / k);
+}
+
+template <int SIDE>
+__device__ inline c64d layer_kernel(const double *x, const double *nx, const double *y, const double *ny, double k,
+                                    double as)
+{
+    if (SIDE == 1) return rhs_kernel(x, nx, y, k, as);
+    return bm_kernel(x, nx, y, ny, k, as);
+}
+
+template <int SIDE>
 __device__ inline c64d rule6(const double *x, const double *nx, const double *p0, const double *p1,
                              const double *p2, const double *ny, double area, double k, double as)
 {
@@ -66,7 +101,7 @@ __device__ inline c64d rule6(const double *x, const double *nx, const double *p0
         for (int r = 0; r < 3; ++r) {
             double y[3];
             for (int d = 0; d < 3; ++d) y[d] = bc[r][0] * p0[d] + bc[r][1] * p1[d] + bc[r][2] * p2[d];
-            c64d v = bm_kernel(x, nx, y, ny, k, as);
+            c64d v = layer_kernel<SIDE>(x, nx, y, ny, k, as);
             s.re += wa * v.re;
             s.im += wa * v.im;
         }
@@ -81,6 +116,7 @@ __device__ inline bool near_pair(const double *ci, const double *cj, double h2j)
 }
 
 // regular entries; near and self entries are left for the special kernels
+template <int SIDE>
 __global__ void k_near_regular(const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend,
                                const int64_t *colptr, const int32_t *cols, const int64_t *off, const double *cent,
                                const double *nrm, const double *v9, const double *area, const double *h2, double k,
@@ -98,7 +134,7 @@ __global__ void k_near_regular(const int32_t *leaf_box, const int32_t *bbeg, con
         int j = cl[c];
         if (j == i || near_pair(x, cent + 3 * j, h2[j])) continue;
         const double *p = v9 + 9 * (int64_t)j;
-        row[c] = rule6(x, nx, p, p + 3, p + 6, nrm + 3 * j, area[j], k, as);
+        row[c] = rule6<SIDE>(x, nx, p, p + 3, p + 6, nrm + 3 * j, area[j], k, as);
     }
 }
 
@@ -130,6 +166,7 @@ __global__ void k_near_special_list(const int32_t *leaf_box, const int32_t *bbeg
 }
 
 // one warp per near entry: 64 sub-triangles, two per lane
+template <int SIDE>
 __global__ void k_near_subdiv(const special_entry *list, int64_t n, const double *cent, const double *nrm,
                               const double *v9, const double *area, double k, double as, c64d *A)
 {
@@ -167,7 +204,7 @@ __global__ void k_near_subdiv(const special_entry *list, int64_t n, const double
                 a[d] = na; b[d] = nb; c[d] = ncc;
             }
         }
-        c64d v = rule6(x, nx, a, b, c, ny, sub_area, k, as);
+        c64d v = rule6<SIDE>(x, nx, a, b, c, ny, sub_area, k, as);
         acc.re += v.re;
         acc.im += v.im;
     }
@@ -215,6 +252,41 @@ __global__ void k_near_self(const special_entry *list, int64_t n, const double *
     A[e.idx] = c64d(0.5 - as * Him / k, as * Hre / k);
 }
 
+// right-hand side's self entries: -alpha/2 + int G (one thread each)
+__global__ void k_near_self_rhs(const special_entry *list, int64_t n, const double *cent, const double *v9, double k,
+                                double as, c64d *A)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    special_entry e = list[t];
+    if (e.i != e.j) return;
+    const double *x = cent + 3 * (int64_t)e.i;
+    const double *P = v9 + 9 * (int64_t)e.i;
+    double sre = 0.0, sim = 0.0;
+    for (int ed = 0; ed < 3; ++ed) {
+        const double *a = P + 3 * ed, *b = P + 3 * ((ed + 1) % 3);
+        double tv[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        double L = sqrt(tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]);
+        for (int d = 0; d < 3; ++d) tv[d] /= L;
+        double s = (x[0] - a[0]) * tv[0] + (x[1] - a[1]) * tv[1] + (x[2] - a[2]) * tv[2];
+        double f[3] = {x[0] - (a[0] + s * tv[0]), x[1] - (a[1] + s * tv[1]), x[2] - (a[2] + s * tv[2])};
+        double dist = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        double pa = atan2(-s, dist), pb = atan2(L - s, dist);
+        double half = 0.5 * (pb - pa), mid = 0.5 * (pb + pa);
+        for (int g = 0; g < GL_N; ++g) {
+            double rho = dist / cos(mid + half * c_gl_x[g]);
+            double th = 0.5 * k * rho;
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            double m = rho * (sn / th);  // (e^{ik rho} - 1)/(ik) = rho e^{i th} sin(th)/th
+            sre += half * c_gl_w[g] * m * cs;
+            sim += half * c_gl_w[g] * m * sn;
+        }
+    }
+    // -as (i/k)/2 + (sre + i sim)/(4 pi)
+    A[e.idx] = c64d(sre / (4.0 * FDA_PI), sim / (4.0 * FDA_PI) - 0.5 * as / k);
+}
+
 __global__ void k_to_f32(const c64d *a, c32f *b, int64_t n)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -253,15 +325,17 @@ void gauss_legendre_host(int n, double *x, double *w)
 
 }  // namespace
 
-void fda_near_convert_f32(fda_handle *h)
+void fda_near_convert_f32(fda_handle *h, int side)
 {
-    h->op32.near.alloc(sizeof(c32f) * std::max<int64_t>(h->nnz_near, 1));
-    k_to_f32<<<fda_blocks(h->nnz_near, 256), 256, 0, h->stream>>>(h->op64.near.as<c64d>(), h->op32.near.as<c32f>(),
-                                                                  h->nnz_near);
+    dbuf &src = side ? h->op64.near1 : h->op64.near, &dst = side ? h->op32.near1 : h->op32.near;
+    dst.alloc(sizeof(c32f) * std::max<int64_t>(h->nnz_near, 1));
+    k_to_f32<<<fda_blocks(h->nnz_near, 256), 256, 0, h->stream>>>(src.as<c64d>(), dst.as<c32f>(), h->nnz_near);
     FDA_CHECK_LAUNCH();
 }
 
-void fda_near_build(fda_handle *h)
+// side 0: the Burton-Miller operator's near field; side 1: the right-hand
+// side's layers (same pattern)
+void fda_near_build(fda_handle *h, int side)
 {
     cudaStream_t s = h->stream;
     double gx[GL_N], gw[GL_N];
@@ -269,7 +343,8 @@ void fda_near_build(fda_handle *h)
     FDA_CUDA(cudaMemcpyToSymbolAsync(c_gl_x, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, s));
     FDA_CUDA(cudaMemcpyToSymbolAsync(c_gl_w, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, s));
     const int NL = h->nleaf;
-    h->op64.near.alloc(sizeof(c64d) * std::max<int64_t>(h->nnz_near, 1));
+    dbuf &dst = side ? h->op64.near1 : h->op64.near;
+    dst.alloc(sizeof(c64d) * std::max<int64_t>(h->nnz_near, 1));
     dim3 g(NL, h->max_leaf_rows);
     // near/self entries first (cheap geometry test), then the regular rule
     dbuf counter;
@@ -292,21 +367,22 @@ void fda_near_build(fda_handle *h)
                                           h->h2.as<double>(), 1, counter.as<unsigned long long>(),
                                           list.as<special_entry>());
     FDA_CHECK_LAUNCH();
-    k_near_regular<<<g, 128, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
-                                     h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                     h->cent.as<double>(), h->nrm.as<double>(), h->verts9.as<double>(),
-                                     h->area.as<double>(), h->h2.as<double>(), h->k, h->cfg.alpha_sign,
-                                     h->op64.near.as<c64d>());
+    auto regular = side ? k_near_regular<1> : k_near_regular<0>;
+    regular<<<g, 128, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
+                              h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
+                              h->cent.as<double>(), h->nrm.as<double>(), h->verts9.as<double>(), h->area.as<double>(),
+                              h->h2.as<double>(), h->k, h->cfg.alpha_sign, dst.as<c64d>());
     FDA_CHECK_LAUNCH();
     if (nspec > 0) {
-        k_near_subdiv<<<fda_blocks((int64_t)nspec * 32, 256), 256, 0, s>>>(
+        auto subdiv = side ? k_near_subdiv<1> : k_near_subdiv<0>;
+        subdiv<<<fda_blocks((int64_t)nspec * 32, 256), 256, 0, s>>>(
             list.as<special_entry>(), (int64_t)nspec, h->cent.as<double>(), h->nrm.as<double>(),
-            h->verts9.as<double>(), h->area.as<double>(), h->k, h->cfg.alpha_sign, h->op64.near.as<c64d>());
+            h->verts9.as<double>(), h->area.as<double>(), h->k, h->cfg.alpha_sign, dst.as<c64d>());
         FDA_CHECK_LAUNCH();
-        k_near_self<<<fda_blocks((int64_t)nspec, 128), 128, 0, s>>>(list.as<special_entry>(), (int64_t)nspec,
-                                                                     h->cent.as<double>(), h->verts9.as<double>(),
-                                                                     h->k, h->cfg.alpha_sign,
-                                                                     h->op64.near.as<c64d>());
+        auto self = side ? k_near_self_rhs : k_near_self;
+        self<<<fda_blocks((int64_t)nspec, 128), 128, 0, s>>>(list.as<special_entry>(), (int64_t)nspec,
+                                                              h->cent.as<double>(), h->verts9.as<double>(), h->k,
+                                                              h->cfg.alpha_sign, dst.as<c64d>());
         FDA_CHECK_LAUNCH();
     }
     FDA_CUDA(cudaStreamSynchronize(s));

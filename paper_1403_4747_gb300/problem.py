@@ -41,6 +41,15 @@ class FDAProblem:
         _lib.fda_rhs_plane_wave(self.h, d, self._c(b))
         return b[0] if np.ndim(dirs) == 1 else b
 
+    def rhs_neumann(self, q, b=None):
+        """Right-hand side of the Burton-Miller equation for Neumann data q = du/dn."""
+        import torch
+        if b is None:
+            b = torch.empty_like(q)
+        nrhs = 1 if q.dim() == 1 else q.shape[0]
+        _lib.fda_rhs_neumann(self.h, self._c(q), self._c(b), nrhs, self.n)
+        return b
+
     def solve(self, b, tol, x0=None, raise_on_not_converged=True):
         import torch
         x = torch.zeros_like(b) if x0 is None else x0.clone()
