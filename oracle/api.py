@@ -37,6 +37,7 @@ def load():
         lib.orc_set_alpha_sign.argtypes = [dbl]
         lib.orc_layer_rowsum.argtypes = [_dp, _ip, i64, dbl, cint, _dp, cint]
         lib.orc_set_side.argtypes = [cint]
+        lib.orc_rhs_point_source.argtypes = [_dp, _ip, i64, dbl, _dp, cint, _dp]
         lib.orc_self_single.argtypes = [_dp, _ip, i64, dbl, _dp]
         _lib = lib
     return _lib
@@ -198,3 +199,16 @@ def self_single_layer(verts, tris, t, k):
     out = np.empty(2)
     load().orc_self_single(_d(v), tr.ctypes.data_as(_ip), int(t), float(k), _d(out))
     return out[0] + 1j * out[1]
+
+
+def rhs_point_source(verts, tris, k, sources, alpha_sign=1.0):
+    """b = u_inc + alpha du_inc/dn at centroids for u_inc = G(x, x_s);
+    sources [nrhs, 3] -> [nrhs, N]"""
+    v, t = _mesh(verts, tris)
+    load().orc_set_alpha_sign(float(alpha_sign))
+    src = np.ascontiguousarray(np.atleast_2d(sources), dtype=np.float64)
+    n = t.shape[0]
+    b = np.empty((src.shape[0], n), dtype=np.complex128)
+    load().orc_rhs_point_source(_d(v), t.ctypes.data_as(_ip), n, float(k), _d(src), src.shape[0],
+                                b.ctypes.data_as(_dp))
+    return b

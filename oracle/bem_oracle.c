@@ -539,3 +539,21 @@ void orc_rhs_plane_wave(const double *verts, const int32_t *tris, int64_t nt, do
             bc[(int64_t)m * nt + t] = uinc + alpha * dudn;
         }
 }
+
+/* point-source right-hand side of Eq. eq_bm for a sound-hard body
+ * (du/dn = 0) and u_inc = G(x, x_s): b_i = G(x_i, x_s) + alpha dG/dn_x(x_i, x_s)
+ * for nrhs sources src[nrhs, 3] off the surface; b column-major [nrhs][nt] */
+void orc_rhs_point_source(const double *verts, const int32_t *tris, int64_t nt, double k, const double *src,
+                          int nrhs, double *b)
+{
+    cplx *bc = (cplx *)b;
+    cplx alpha = g_alpha_sign * I / k;
+    for (int m = 0; m < nrhs; ++m)
+        for (int64_t t = 0; t < nt; ++t) {
+            tri_t T;
+            make_tri(verts, tris, t, &T);
+            cplx o[4];
+            kernels_all(T.c, T.n, src + 3 * m, T.n, k, o);
+            bc[(int64_t)m * nt + t] = o[0] + alpha * o[2];
+        }
+}

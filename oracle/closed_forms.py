@@ -25,6 +25,14 @@ since S[Y_n] = i k j_n h_n Y_n on the unit sphere and the radial derivative
 of the single-layer potential is i k^2 j_n h_n' outside and i k^2 j_n' h_n
 inside (their mean is the direct value in nu; n = -nu flips its sign).
 
+Point source at x_s, |x_s| = r_s > 1, outside the rigid unit sphere (the
+comparison of Sec. 5.2): with the addition theorem
+G(x, x_s) = (ik/4pi) sum_n (2n+1) j_n(k r) h_n(k r_s) P_n(cos gamma), a
+scattered field sum_n a_n h_n(k r) P_n with zero total radial derivative at
+r = 1 and the Wronskian leave on the surface
+    u(gamma) = -(1/(4 pi k)) sum_n (2n+1) h_n(k r_s) P_n(cos gamma) / h_n'(k),
+gamma the angle between x and x_s.
+
 Pulsating unit sphere (Sec. 5.1), du/dn = 1 with n into the body: the
 radiating solution u = A e^{ikr}/r gives u = 1/(1 - ik) on the surface
 (beta_0 / lambda_0 equals it for either sign of alpha).
@@ -86,3 +94,14 @@ def sphere_rhs_eigenvalue(n: int, k: float, alpha_sign: float = 1.0) -> complex:
 def pulsating_sphere_potential(k: float) -> complex:
     """Surface potential of the unit sphere pulsating with du/dn = 1 (n into the body)."""
     return 1.0 / (1.0 - 1j * k)
+
+
+def point_source_surface_field(k: float, rs: float, cos_gamma, nmax: int | None = None):
+    """Total surface field of the rigid unit sphere for u_inc = G(x, x_s), |x_s| = rs."""
+    ct = np.asarray(cos_gamma, dtype=np.float64)
+    nmax = mie_nmax(k) + int(np.ceil(10.0 / np.log(rs))) if nmax is None else nmax
+    u = np.zeros(ct.shape, dtype=np.complex128)
+    for n in range(nmax + 1):
+        u += (-(2 * n + 1) / (4 * np.pi * k)) * _h1(n, k * rs) / _h1(n, k, derivative=True) * \
+            special.eval_legendre(n, ct)
+    return u
