@@ -610,6 +610,62 @@ def run_pulsating(args):
     return 0
 
 
+def run_point_source(args):
+    """Rigid unit sphere, point source at (-2, 0, 0) (the comparison of Sec.
+    5.2): k = 5 and 50 on spheres of about the paper's size (N = 131,072)
+    and the headline sphere (N = 327,680); GMRES to eps = 1e-3 as there,
+    error against the closed form.  Not the headline workload
+    (--workload point_source)."""
+    import numpy as np
+    import torch
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import octasphere, icosphere
+    from scipy import special
+    src = np.array([-2.0, 0.0, 0.0])
+
+    def exact(k, cg):
+        # -(1/(4 pi k)) sum (2n+1) h_n(2k) P_n(cos g) / h_n'(k)
+        u = np.zeros(cg.shape, dtype=np.complex128)
+        for n in range(int(k + 10 * k ** (1 / 3) + 40)):
+            h = special.spherical_jn(n, 2 * k) + 1j * special.spherical_yn(n, 2 * k)
+            hd = special.spherical_jn(n, k, True) + 1j * special.spherical_yn(n, k, True)
+            u += -(2 * n + 1) / (4 * np.pi * k) * h / hd * special.eval_legendre(n, cg)
+        return u
+
+    rows = []
+    for name, mesh in (("octasphere L7", lambda: octasphere(7)), ("icosphere L7", lambda: icosphere(7))):
+        v, f = mesh()
+        for k in (5.0, 50.0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P = F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, eps=1e-3, alpha_sign=args.alpha_sign)
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
+            b = P.rhs_point_source(src)
+            u, info = P.solve(b, 1e-3, raise_on_not_converged=False)
+            c = np.mean(v[f], axis=1)
+            cg = (c / np.linalg.norm(c, axis=1, keepdims=True)) @ (src / 2.0)
+            ue = exact(k, cg)
+            err = float(np.linalg.norm(u.cpu().numpy() - ue) / np.linalg.norm(ue))
+            rows.append({"mesh": name, "N": len(f), "k": k, "alpha_sign": args.alpha_sign,
+                         "setup_s": round(setup_s, 3), "solve_s": round(info.solve_s, 4), "iters": info.iters,
+                         "T_it_ms": round(info.solve_s / max(1, info.iters) * 1e3, 3),
+                         "rel_resid": info.rel_resid_fp64, "l2_error": err})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            P.close()
+            del P, b, u
+            torch.cuda.empty_cache()
+    line = {"metric": "point-source sphere scattering: time per GMRES iteration and error (Sec. 5.2)",
+            "value": rows[1]["T_it_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32+bf16x3/f64", "data": "synthetic",
+            "config": {"workload": "rigid unit sphere, point source (-2, 0, 0), k = 5 and 50, eps = tol = 1e-3"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -630,11 +686,12 @@ def main():
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes", "pulsating"],
+    ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes", "pulsating", "point_source"],
                     help="many_meshes: the eight-mesh batch; pulsating: the pulsating-sphere study")
     ap.add_argument("--pulsating-max-level", type=int, default=9)
     ap.add_argument("--alpha-sign", type=float, default=-1.0, choices=[-1.0, 1.0],
-                    help="coupling alpha = sign * i/k of the pulsating study (-1: the paper's time convention)")
+                    help="coupling alpha = sign * i/k of the pulsating and point-source studies "
+                         "(-1: the paper's time convention)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -644,6 +701,8 @@ def main():
         return run_many_meshes(args)
     if args.workload == "pulsating":
         return run_pulsating(args)
+    if args.workload == "point_source":
+        return run_point_source(args)
     return run_native(args)
 
 

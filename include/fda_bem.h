@@ -160,6 +160,14 @@ fda_status fda_apply_host(fda_handle *h, const fda_c128 *x, fda_c128 *y, int nrh
  * dirs: host double[nrhs][3] unit vectors; b: device, ld = nt. */
 fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b);
 
+/* Right-hand side of Eq. eq_bm for a sound-hard body and point sources
+ * u_inc = G(x, x_s) (the sphere comparison of Sec. 5.2):
+ * b = u_inc + alpha du_inc/dn at the centroids.  src: host double[nrhs][3]
+ * source positions (finite, off the surface: a source on a centroid gives a
+ * non-finite b, which fda_solve reports as FDA_ERR_NUMERIC); b: device,
+ * ld = nt.  Synchronises the stream. */
+fda_status fda_rhs_point_source(fda_handle *h, const double *src, int nrhs, fda_c128 *b);
+
 /* Right-hand side of Eq. eq_bm for a radiating body with given Neumann data
  * q = du/dn (no incident field), the layers of the equation's right-hand
  * side evaluated by the same fast directional algorithm (Sec. 3.3 Steps 2-4

@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
     lib.fda_rhs_plane_wave.argtypes = [H, vp, cint, vp]
     lib.fda_rhs_plane_wave_noalloc.argtypes = [H, vp, cint, vp]
     lib.fda_rhs_neumann.argtypes = [H, vp, vp, cint, i64]
+    lib.fda_rhs_point_source.argtypes = [H, vp, cint, vp]
     lib.fda_solve.argtypes = [H, vp, vp, cint, dbl, ctypes.POINTER(fda_info)]
     lib.fda_get_stats.argtypes = [H, ctypes.POINTER(fda_stats)]
     lib.fda_set_timing.argtypes = [H, cint]
@@ -126,7 +127,7 @@ def load(path: str = LIB_PATH):
     lib.fda_destroy.argtypes = [H]
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
-                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
+                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
                  "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores"):
         getattr(lib, name).restype = cint
     _lib = lib
@@ -185,6 +186,13 @@ def fda_rhs_plane_wave(h, dirs, b_ptr):
     import numpy as np
     d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
     _check(h, load().fda_rhs_plane_wave(h, d.ctypes.data, d.shape[0], b_ptr))
+
+
+def fda_rhs_point_source(h, sources, b_ptr):
+    """sources: host [nrhs, 3] positions; b_ptr: device address (ld = nt)."""
+    import numpy as np
+    s = np.ascontiguousarray(np.atleast_2d(sources), dtype=np.float64)
+    _check(h, load().fda_rhs_point_source(h, s.ctypes.data, s.shape[0], b_ptr))
 
 
 def fda_rhs_neumann(h, q_ptr, b_ptr, nrhs, ld):

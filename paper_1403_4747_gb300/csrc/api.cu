@@ -318,6 +318,31 @@ fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c
     });
 }
 
+fda_status fda_rhs_point_source(fda_handle *h, const double *src, int nrhs, fda_c128 *b)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state < 1) {
+        h->err = "fda_rhs_point_source before fda_build_tree";
+        return FDA_ERR_STATE;
+    }
+    if (!src || !b || nrhs < 1) {
+        h->err = "invalid right-hand-side arguments";
+        return FDA_ERR_ARG;
+    }
+    for (int i = 0; i < 3 * nrhs; ++i)
+        if (!std::isfinite(src[i])) {
+            h->err = "non-finite source position";
+            return FDA_ERR_ARG;
+        }
+    return guarded(h, [&] {
+        dbuf ds;
+        ds.alloc(sizeof(double) * 3 * nrhs);
+        FDA_CUDA(cudaMemcpyAsync(ds.p, src, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, h->stream));
+        fda_rhs_point(h, ds.as<double>(), nrhs, reinterpret_cast<c64d *>(b));
+        FDA_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
 fda_status fda_rhs_plane_wave_noalloc(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b)
 {
     if (!h) return FDA_ERR_ARG;

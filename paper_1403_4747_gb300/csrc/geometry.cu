@@ -185,7 +185,34 @@ __global__ void k_rhs_direct(const double *cent, const double *nrm, const int32_
     b[(int64_t)m * n + perm[i]] = c64d(c * (1.0 - as * dn), s * (1.0 - as * dn));
 }
 
+// Point-source incidence u_inc = G(x, x_s) on a sound-hard body:
+// b[m][perm[i]] = G(x_i, x_s) + alpha dG/dn_x(x_i, x_s), r = x_i - x_s.
+__global__ void k_rhs_point(const double *cent, const double *nrm, const int32_t *perm, int64_t n,
+                            const double *src, int nrhs, double k, double as, c64d *b)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int m = blockIdx.y;
+    if (i >= n || m >= nrhs) return;
+    const double *xs = src + 3 * m, *x = cent + 3 * i, *nx = nrm + 3 * i;
+    double r0 = x[0] - xs[0], r1 = x[1] - xs[1], r2 = x[2] - xs[2];
+    double R2 = r0 * r0 + r1 * r1 + r2 * r2, R = sqrt(R2);
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    double g = 1.0 / (4.0 * FDA_PI * R);
+    double f = -(r0 * nx[0] + r1 * nx[1] + r2 * nx[2]) * g / R2;
+    double dre = f * (cs + k * R * sn), dim = f * (sn - k * R * cs);
+    b[(int64_t)m * n + perm[i]] = c64d(cs * g - as * dim / k, sn * g + as * dre / k);
+}
+
 }  // namespace
+
+void fda_rhs_point(fda_handle *h, const double *src_dev, int nrhs, c64d *b)
+{
+    dim3 g(fda_blocks(h->N, 256), nrhs);
+    k_rhs_point<<<g, 256, 0, h->stream>>>(h->cent.as<double>(), h->nrm.as<double>(), h->perm.as<int32_t>(), h->N,
+                                           src_dev, nrhs, h->k, h->cfg.alpha_sign, b);
+    FDA_CHECK_LAUNCH();
+}
 
 // Device-resident staging area for the incidence directions of
 // fda_rhs_plane_wave_noalloc: FDA_NOALLOC_MAX_DIRS unit vectors (6 KB), held

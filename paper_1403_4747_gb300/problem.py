@@ -41,6 +41,15 @@ class FDAProblem:
         _lib.fda_rhs_plane_wave(self.h, d, self._c(b))
         return b[0] if np.ndim(dirs) == 1 else b
 
+    def rhs_point_source(self, sources):
+        """Right-hand side for point sources u_inc = G(x, x_s) (host positions [nrhs, 3] or [3])."""
+        import numpy as np
+        import torch
+        src = np.atleast_2d(np.asarray(sources, dtype=np.float64))
+        b = torch.empty((src.shape[0], self.n), dtype=torch.complex128, device="cuda")
+        _lib.fda_rhs_point_source(self.h, src, b.data_ptr())
+        return b[0] if np.ndim(sources) == 1 else b
+
     def rhs_neumann(self, q, b=None):
         """Right-hand side of the Burton-Miller equation for Neumann data q = du/dn."""
         import torch
