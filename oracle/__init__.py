@@ -25,14 +25,15 @@ Parity status per function:
 from .api import (load, geometry, kernels, integrate_triangle, self_hypersingular, entry,
                   is_near_pair, matvec, assemble, rhs_plane_wave, num_threads, gauss_legendre,
                   rule6, layer_rowsum, rhs_layers_matvec, rhs_layers_assemble, rhs_layers_entry,
-                  self_single_layer, rhs_point_source)
+                  self_single_layer, rhs_point_source, scattered_field, far_field)
 from .solve import gmres, lu_solve
 from .closed_forms import (mie_surface_field, sphere_eigenvalue, legendre_on_mesh, sphere_rhs_eigenvalue,
-                           pulsating_sphere_potential, point_source_surface_field)
+                           pulsating_sphere_potential, point_source_surface_field, mie_scattered_field,
+                           mie_far_field)
 
 __all__ = ["load", "geometry", "kernels", "integrate_triangle", "self_hypersingular", "entry",
            "is_near_pair", "matvec", "assemble", "rhs_plane_wave", "num_threads", "gauss_legendre",
            "rule6", "layer_rowsum", "gmres", "lu_solve", "mie_surface_field", "sphere_eigenvalue", "legendre_on_mesh",
            "rhs_layers_matvec", "rhs_layers_assemble", "rhs_layers_entry", "self_single_layer",
            "sphere_rhs_eigenvalue", "pulsating_sphere_potential", "rhs_point_source",
-           "point_source_surface_field"]
+           "point_source_surface_field", "scattered_field", "far_field", "mie_scattered_field", "mie_far_field"]

@@ -38,6 +38,8 @@ def load():
         lib.orc_layer_rowsum.argtypes = [_dp, _ip, i64, dbl, cint, _dp, cint]
         lib.orc_set_side.argtypes = [cint]
         lib.orc_rhs_point_source.argtypes = [_dp, _ip, i64, dbl, _dp, cint, _dp]
+        lib.orc_scattered_field.argtypes = [_dp, _ip, i64, dbl, _dp, _dp, _dp, i64, _dp, cint]
+        lib.orc_far_field.argtypes = [_dp, _ip, i64, dbl, _dp, _dp, _dp, i64, _dp, cint]
         lib.orc_self_single.argtypes = [_dp, _ip, i64, dbl, _dp]
         _lib = lib
     return _lib
@@ -212,3 +214,35 @@ def rhs_point_source(verts, tris, k, sources, alpha_sign=1.0):
     load().orc_rhs_point_source(_d(v), t.ctypes.data_as(_ip), n, float(k), _d(src), src.shape[0],
                                 b.ctypes.data_as(_dp))
     return b
+
+
+def _surface_data(u, q, n):
+    uc = np.ascontiguousarray(u, dtype=np.complex128).reshape(n)
+    qc = None if q is None else np.ascontiguousarray(q, dtype=np.complex128).reshape(n)
+    return uc, qc
+
+
+def scattered_field(verts, tris, k, u, points, q=None, nthreads=0):
+    """u_sc(x) = int G q - int dG/dn_y u at points [M, 3] off the surface (q None = 0)."""
+    v, t = _mesh(verts, tris)
+    n = t.shape[0]
+    uc, qc = _surface_data(u, q, n)
+    p = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    out = np.empty(p.shape[0], dtype=np.complex128)
+    load().orc_scattered_field(_d(v), t.ctypes.data_as(_ip), n, float(k), uc.ctypes.data_as(_dp),
+                               qc.ctypes.data_as(_dp) if qc is not None else None, _d(p), p.shape[0],
+                               out.ctypes.data_as(_dp), int(nthreads))
+    return out
+
+
+def far_field(verts, tris, k, u, dirs, q=None, nthreads=0):
+    """Far-field pattern F(xh) for unit directions [M, 3] (q None = 0)."""
+    v, t = _mesh(verts, tris)
+    n = t.shape[0]
+    uc, qc = _surface_data(u, q, n)
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    out = np.empty(d.shape[0], dtype=np.complex128)
+    load().orc_far_field(_d(v), t.ctypes.data_as(_ip), n, float(k), uc.ctypes.data_as(_dp),
+                         qc.ctypes.data_as(_dp) if qc is not None else None, _d(d), d.shape[0],
+                         out.ctypes.data_as(_dp), int(nthreads))
+    return out

@@ -557,3 +557,77 @@ void orc_rhs_point_source(const double *verts, const int32_t *tris, int64_t nt, 
             bc[(int64_t)m * nt + t] = o[0] + alpha * o[2];
         }
 }
+
+/* ------------------------------------------------------------------ */
+/* fields off the surface                                              */
+/* ------------------------------------------------------------------ */
+/* Green's representation in the acoustic domain (Eq. cbie with c = 1, n
+ * into the body): u(x) = u_inc(x) + int G(x, y) q(y) dy - int dG/dn_y(x, y) u(y) dy.
+ * Scattered part at npts points pts[npts, 3] (off the surface) from the
+ * element values u (and q, NULL = 0), six-point rule per element. */
+void orc_scattered_field(const double *verts, const int32_t *tris, int64_t nt, double k, const double *u,
+                         const double *q, const double *pts, int64_t npts, double *out, int nthreads)
+{
+    tri_t *T = build_all(verts, tris, nt);
+    set_threads(nthreads);
+    const cplx *uc = (const cplx *)u, *qc = (const cplx *)q;
+    cplx *oc = (cplx *)out;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < npts; ++p) {
+        const double *x = pts + 3 * p;
+        cplx acc = 0.0;
+        for (int64_t j = 0; j < nt; ++j) {
+            cplx sg = 0.0, sd = 0.0;
+            for (int g = 0; g < 2; ++g) {
+                double a = R6_A[g], b = 1.0 - 2.0 * R6_A[g];
+                double bary[3][3] = {{b, a, a}, {a, b, a}, {a, a, b}};
+                for (int r = 0; r < 3; ++r) {
+                    double y[3];
+                    for (int d = 0; d < 3; ++d)
+                        y[d] = bary[r][0] * T[j].v[0][d] + bary[r][1] * T[j].v[1][d] + bary[r][2] * T[j].v[2][d];
+                    cplx o[4];
+                    kernels_all(x, T[j].n, y, T[j].n, k, o);
+                    sg += R6_W[g] * T[j].area * o[0];
+                    sd += R6_W[g] * T[j].area * o[1];
+                }
+            }
+            acc += (qc ? sg * qc[j] : 0.0) - sd * uc[j];
+        }
+        oc[p] = acc;
+    }
+    free(T);
+}
+
+/* Far-field pattern F of the scattered field, u_sc ~ e^{ik|x|}/|x| F(xh):
+ *   F(xh) = (1/(4 pi)) int [ q(y) + ik (xh . n_y) u(y) ] e^{-ik xh . y} dy
+ * (the large-|x| limit of the representation above), for ndir unit
+ * directions dirs[ndir, 3]; six-point rule per element. */
+void orc_far_field(const double *verts, const int32_t *tris, int64_t nt, double k, const double *u,
+                   const double *q, const double *dirs, int64_t ndir, double *out, int nthreads)
+{
+    tri_t *T = build_all(verts, tris, nt);
+    set_threads(nthreads);
+    const cplx *uc = (const cplx *)u, *qc = (const cplx *)q;
+    cplx *oc = (cplx *)out;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t m = 0; m < ndir; ++m) {
+        const double *xh = dirs + 3 * m;
+        cplx acc = 0.0;
+        for (int64_t j = 0; j < nt; ++j) {
+            cplx se = 0.0;
+            for (int g = 0; g < 2; ++g) {
+                double a = R6_A[g], b = 1.0 - 2.0 * R6_A[g];
+                double bary[3][3] = {{b, a, a}, {a, b, a}, {a, a, b}};
+                for (int r = 0; r < 3; ++r) {
+                    double y[3];
+                    for (int d = 0; d < 3; ++d)
+                        y[d] = bary[r][0] * T[j].v[0][d] + bary[r][1] * T[j].v[1][d] + bary[r][2] * T[j].v[2][d];
+                    se += R6_W[g] * T[j].area * cexp(-I * k * dot3(xh, y));
+                }
+            }
+            acc += se * ((qc ? qc[j] : 0.0) + I * k * dot3(xh, T[j].n) * uc[j]);
+        }
+        oc[m] = acc / (4.0 * ORC_PI);
+    }
+    free(T);
+}

@@ -105,3 +105,28 @@ def point_source_surface_field(k: float, rs: float, cos_gamma, nmax: int | None 
         u += (-(2 * n + 1) / (4 * np.pi * k)) * _h1(n, k * rs) / _h1(n, k, derivative=True) * \
             special.eval_legendre(n, ct)
     return u
+
+
+def mie_scattered_field(k: float, r, cos_theta, nmax: int | None = None):
+    """Scattered field of the rigid unit sphere for e^{ik d.x} at radius r >= 1:
+    sum_n a_n h_n(k r) P_n(cos theta), a_n = -(2n+1) i^n j_n'(k)/h_n'(k)."""
+    ct = np.asarray(cos_theta, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    nmax = mie_nmax(k) if nmax is None else nmax
+    u = np.zeros(np.broadcast(ct, r).shape, dtype=np.complex128)
+    for n in range(nmax + 1):
+        an = -(2 * n + 1) * (1j ** n) * special.spherical_jn(n, k, derivative=True) / _h1(n, k, derivative=True)
+        u += an * _h1(n, k * r) * special.eval_legendre(n, ct)
+    return u
+
+
+def mie_far_field(k: float, cos_theta, nmax: int | None = None):
+    """Far-field pattern of the rigid unit sphere, u_sc ~ e^{ikr}/r F:
+    F = (i/k) sum_n (2n+1) j_n'(k)/h_n'(k) P_n(cos theta) (h_n(x) ~ (-i)^{n+1} e^{ix}/x)."""
+    ct = np.asarray(cos_theta, dtype=np.float64)
+    nmax = mie_nmax(k) if nmax is None else nmax
+    f = np.zeros(ct.shape, dtype=np.complex128)
+    for n in range(nmax + 1):
+        f += (2 * n + 1) * special.spherical_jn(n, k, derivative=True) / _h1(n, k, derivative=True) * \
+            special.eval_legendre(n, ct)
+    return (1j / k) * f
