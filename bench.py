@@ -666,6 +666,120 @@ def run_point_source(args):
     return 0
 
 
+def run_p0_sweep(args):
+    """The p0 study of Table tab_varp0: points per direction p = ceil(ln(1/eps))
+    + p0 for the low-frequency cubes (and two more for the high-frequency cone
+    grids), p0 = 0..3, on the pulsating sphere with eps = 1e-3 (N = 524,288,
+    k = 32 pi here; the paper uses N = 2,097,152).  Not the headline workload
+    (--workload p0_sweep)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import octasphere
+    level = args.p0_level
+    v, f = octasphere(level)
+    k = math.pi * 2 ** (level - 3)
+    eps = 1e-3
+    rows = []
+    for p0 in range(4):
+        p_lf = int(math.ceil(math.log(1.0 / eps))) + p0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P = F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, eps=eps, p_lf=p_lf, p_hf=p_lf + 2,
+                         alpha_sign=args.alpha_sign)
+        b = P.rhs_neumann(torch.ones(len(f), dtype=torch.complex128, device="cuda"))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        u, info = P.solve(b, eps, raise_on_not_converged=False)
+        ue = 1.0 / (1.0 - 1j * k)
+        err = float(np.linalg.norm(u.cpu().numpy() - ue) / (abs(ue) * math.sqrt(len(f))))
+        x = torch.ones(len(f), dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            P.apply(x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            P.apply(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        st = P.stats()
+        rows.append({"p0": p0, "p_lf": p_lf, "p_hf": p_lf + 2, "setup_s": round(setup_s, 3),
+                     "solve_s": round(info.solve_s, 4), "iters": info.iters,
+                     "matvec_ms": round(e0.elapsed_time(e1) / 10, 3), "l2_error": err,
+                     "device_gb": round(st.device_bytes / 1e9, 2),
+                     "ranks": [int(st.level_rank[l]) for l in range(st.n_levels)]})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        P.close()
+        del P, b, u, x, y
+        torch.cuda.empty_cache()
+    line = {"metric": "p0 study (Table tab_varp0 shape): error, time and memory vs points per direction",
+            "value": rows[1]["matvec_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32+bf16x3/f64", "data": "synthetic",
+            "config": {"workload": "pulsating octahedral sphere N = %d, k = %g pi, eps = 1e-3" % (len(f), k / math.pi)},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_far_field(args):
+    """Far-field pattern of the headline sphere (level 7, N = 327,680,
+    k = 50, plane wave along +z, chosen form, tol 1e-4) on 720 directions in
+    the xz-plane against the Mie series, and reciprocity on the ellipsoid of
+    the same level.  Not the headline workload (--workload far_field)."""
+    import numpy as np
+    import torch
+    from scipy import special
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import icosphere, ellipsoid_from_icosphere
+    k = 50.0
+    th = np.arange(720) * (2 * np.pi / 720)
+    dirs = np.stack([np.sin(th), np.zeros_like(th), np.cos(th)], axis=1)
+    nmax = int(np.ceil(k + 10 * k ** (1 / 3) + 10))
+    mie = np.zeros(len(th), dtype=np.complex128)
+    for n in range(nmax + 1):
+        jd = special.spherical_jn(n, k, True)
+        hd = jd + 1j * special.spherical_yn(n, k, True)
+        mie += (2 * n + 1) * jd / hd * special.eval_legendre(n, np.cos(th))
+    mie *= 1j / k
+    v, f = icosphere(7)
+    P = F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, alpha_sign=args.alpha_sign)
+    u, info = P.solve(P.rhs_plane_wave([0.0, 0.0, 1.0]), 1e-4)
+    P.far_field(u, dirs[:8])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Fp = P.far_field(u, dirs)
+    torch.cuda.synchronize()
+    t_pat = time.perf_counter() - t0
+    Fp = Fp.cpu().numpy()
+    err = float(np.linalg.norm(Fp - mie) / np.linalg.norm(mie))
+    P.close()
+    ve, fe = ellipsoid_from_icosphere(7)
+    Q = F.FDAProblem(ve, fe, k, precision=F.FDA_CHOSEN_FP32, alpha_sign=args.alpha_sign)
+    d = np.array([0.0, 0.0, 1.0])
+    a = np.array([0.6, 0.0, 0.8])
+    u1, _ = Q.solve(Q.rhs_plane_wave(d), 1e-5)
+    u2, _ = Q.solve(Q.rhs_plane_wave(-a), 1e-5)
+    f1 = complex(Q.far_field(u1, [a]).cpu().numpy()[0])
+    f2 = complex(Q.far_field(u2, [-d]).cpu().numpy()[0])
+    Q.close()
+    line = {"metric": "far-field pattern: 720 directions, error vs Mie, evaluation time", "value": t_pat * 1e3,
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "icosphere level 7 (N = 327,680), k = 50, plane wave +z; ellipsoid level 7 "
+                                   "reciprocity", "alpha_sign": args.alpha_sign},
+            "pattern_rel_l2_error_vs_mie": err, "solve_iters": info.iters, "solve_s": info.solve_s,
+            "reciprocity": {"F(a;d)": [f1.real, f1.imag], "F(-d;-a)": [f2.real, f2.imag],
+                            "rel_gap": abs(f1 - f2) / abs(f1)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -686,9 +800,11 @@ def main():
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes", "pulsating", "point_source"],
+    ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes", "pulsating", "point_source", "far_field",
+                             "p0_sweep"],
                     help="many_meshes: the eight-mesh batch; pulsating: the pulsating-sphere study")
     ap.add_argument("--pulsating-max-level", type=int, default=9)
+    ap.add_argument("--p0-level", type=int, default=8, help="octahedral sphere level of the p0 study")
     ap.add_argument("--alpha-sign", type=float, default=-1.0, choices=[-1.0, 1.0],
                     help="coupling alpha = sign * i/k of the pulsating and point-source studies "
                          "(-1: the paper's time convention)")
@@ -703,6 +819,10 @@ def main():
         return run_pulsating(args)
     if args.workload == "point_source":
         return run_point_source(args)
+    if args.workload == "far_field":
+        return run_far_field(args)
+    if args.workload == "p0_sweep":
+        return run_p0_sweep(args)
     return run_native(args)
 
 

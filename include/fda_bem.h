@@ -168,6 +168,25 @@ fda_status fda_rhs_plane_wave(fda_handle *h, const double *dirs, int nrhs, fda_c
  * ld = nt.  Synchronises the stream. */
 fda_status fda_rhs_point_source(fda_handle *h, const double *src, int nrhs, fda_c128 *b);
 
+/* Fields off the surface from a solution u (device, nt values in the
+ * caller's order, e.g. fda_solve's x) and its Neumann data q = du/dn (device,
+ * NULL = 0, the sound-hard case): Green's representation of Eq. cbie in the
+ * acoustic domain (c = 1),
+ *   u_sc(x) = int G(x, y) q(y) dy - int dG/dn_y(x, y) u(y) dy
+ * (add u_inc for the total field), and its far-field pattern, u_sc ~
+ * e^{ik|x|}/|x| F(xh) with
+ *   F(xh) = (1/(4 pi)) int [ q(y) + ik (xh . n_y) u(y) ] e^{-ik xh . y} dy.
+ * Every element by the six-point rule, summed directly over all elements
+ * for each target (N x M x 6 FP64 evaluations; no fast algorithm), so
+ * points closer to the surface than about two element sizes lose accuracy.
+ * dirs: host double[ndir][3] unit vectors; pts: host double[npts][3];
+ * F, out: device, caller-owned, overwritten.  Needs fda_precompute_translations
+ * (FDA_ERR_STATE before); synchronises the stream. */
+fda_status fda_far_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *dirs, int ndir,
+                         fda_c128 *F);
+fda_status fda_scattered_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *pts, int64_t npts,
+                               fda_c128 *out);
+
 /* Right-hand side of Eq. eq_bm for a radiating body with given Neumann data
  * q = du/dn (no incident field), the layers of the equation's right-hand
  * side evaluated by the same fast directional algorithm (Sec. 3.3 Steps 2-4

@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
     lib.fda_rhs_plane_wave_noalloc.argtypes = [H, vp, cint, vp]
     lib.fda_rhs_neumann.argtypes = [H, vp, vp, cint, i64]
     lib.fda_rhs_point_source.argtypes = [H, vp, cint, vp]
+    lib.fda_far_field.argtypes = [H, vp, vp, vp, cint, vp]
+    lib.fda_scattered_field.argtypes = [H, vp, vp, vp, i64, vp]
     lib.fda_solve.argtypes = [H, vp, vp, cint, dbl, ctypes.POINTER(fda_info)]
     lib.fda_get_stats.argtypes = [H, ctypes.POINTER(fda_stats)]
     lib.fda_set_timing.argtypes = [H, cint]
@@ -127,7 +129,7 @@ def load(path: str = LIB_PATH):
     lib.fda_destroy.argtypes = [H]
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
-                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
+                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_far_field", "fda_scattered_field", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
                  "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores"):
         getattr(lib, name).restype = cint
     _lib = lib
@@ -193,6 +195,20 @@ def fda_rhs_point_source(h, sources, b_ptr):
     import numpy as np
     s = np.ascontiguousarray(np.atleast_2d(sources), dtype=np.float64)
     _check(h, load().fda_rhs_point_source(h, s.ctypes.data, s.shape[0], b_ptr))
+
+
+def fda_far_field(h, u_ptr, q_ptr, dirs, F_ptr):
+    """Far-field pattern at host unit directions [M, 3] into device F (q_ptr 0 / None = sound-hard)."""
+    import numpy as np
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    _check(h, load().fda_far_field(h, u_ptr, q_ptr or None, d.ctypes.data, d.shape[0], F_ptr))
+
+
+def fda_scattered_field(h, u_ptr, q_ptr, points, out_ptr):
+    """Scattered field at host points [M, 3] into device out (q_ptr 0 / None = sound-hard)."""
+    import numpy as np
+    p = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    _check(h, load().fda_scattered_field(h, u_ptr, q_ptr or None, p.ctypes.data, p.shape[0], out_ptr))
 
 
 def fda_rhs_neumann(h, q_ptr, b_ptr, nrhs, ld):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfdabem.so")
 SOURCES = ["sort.cu", "geometry.cu", "tree.cu", "quadrature.cu", "precompute.cu", "translate.cu", "translate_tc.cu",
-           "precond.cu", "sai.cu", "apply.cu", "gmres.cu", "api.cu", "batch.cu"]
+           "precond.cu", "sai.cu", "apply.cu", "gmres.cu", "api.cu", "batch.cu", "field.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include"), "-diag-suppress", "20054"]

@@ -343,6 +343,50 @@ fda_status fda_rhs_point_source(fda_handle *h, const double *src, int nrhs, fda_
     });
 }
 
+namespace {
+fda_status field_call(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *tgt, int64_t ntgt,
+                      int far, fda_c128 *out, const char *name)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = std::string(name) + " before fda_precompute_translations";
+        return FDA_ERR_STATE;
+    }
+    if (!u || !tgt || !out || ntgt < 1) {
+        h->err = std::string("invalid ") + name + " arguments";
+        return FDA_ERR_ARG;
+    }
+    for (int64_t i = 0; i < ntgt; ++i) {
+        const double *t = tgt + 3 * i;
+        if (!std::isfinite(t[0]) || !std::isfinite(t[1]) || !std::isfinite(t[2]) ||
+            (far && !(fabs(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] - 1.0) < 1e-6))) {
+            h->err = far ? "far-field directions must be unit vectors" : "non-finite field point";
+            return FDA_ERR_ARG;
+        }
+    }
+    return guarded(h, [&] {
+        dbuf dt;
+        dt.alloc(sizeof(double) * 3 * ntgt);
+        FDA_CUDA(cudaMemcpyAsync(dt.p, tgt, sizeof(double) * 3 * ntgt, cudaMemcpyHostToDevice, h->stream));
+        fda_field(h, reinterpret_cast<const c64d *>(u), reinterpret_cast<const c64d *>(q), dt.as<double>(), ntgt,
+                  far, reinterpret_cast<c64d *>(out));
+        FDA_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+}  // namespace
+
+fda_status fda_far_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *dirs, int ndir,
+                         fda_c128 *F)
+{
+    return field_call(h, u, q, dirs, ndir, 1, F, "fda_far_field");
+}
+
+fda_status fda_scattered_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *pts, int64_t npts,
+                               fda_c128 *out)
+{
+    return field_call(h, u, q, pts, npts, 0, out, "fda_scattered_field");
+}
+
 fda_status fda_rhs_plane_wave_noalloc(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b)
 {
     if (!h) return FDA_ERR_ARG;

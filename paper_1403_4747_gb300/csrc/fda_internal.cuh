@@ -313,6 +313,8 @@ void fda_rhs_sorted(fda_handle *h, const double *dirs_dev, int nrhs, c64d *b_sor
 void fda_rhs_noalloc(fda_handle *h, const double *dirs_host, int nrhs, c64d *b);
 // point sources (device [nrhs][3]) -> b in the caller's element order, ld = N
 void fda_rhs_point(fda_handle *h, const double *src_dev, int nrhs, c64d *b);
+// far = 1: far-field pattern at unit directions; far = 0: scattered field at points
+void fda_field(fda_handle *h, const c64d *u, const c64d *q, const double *tgt_dev, int64_t ntgt, int far, c64d *out);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
 void fda_gather_cols(fda_handle *h, const c64d *x, int64_t ld, c64d *xs, int nrhs, cudaStream_t s);

@@ -50,6 +50,24 @@ class FDAProblem:
         _lib.fda_rhs_point_source(self.h, src, b.data_ptr())
         return b[0] if np.ndim(sources) == 1 else b
 
+    def far_field(self, u, dirs, q=None):
+        """Far-field pattern of the scattered field at unit directions (host [M, 3])."""
+        import numpy as np
+        import torch
+        d = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        F = torch.empty(d.shape[0], dtype=torch.complex128, device="cuda")
+        _lib.fda_far_field(self.h, self._c(u), self._c(q) if q is not None else None, d, F.data_ptr())
+        return F
+
+    def scattered_field(self, u, points, q=None):
+        """Scattered field at host points [M, 3] off the surface."""
+        import numpy as np
+        import torch
+        p = np.atleast_2d(np.asarray(points, dtype=np.float64))
+        out = torch.empty(p.shape[0], dtype=torch.complex128, device="cuda")
+        _lib.fda_scattered_field(self.h, self._c(u), self._c(q) if q is not None else None, p, out.data_ptr())
+        return out
+
     def rhs_neumann(self, q, b=None):
         """Right-hand side of the Burton-Miller equation for Neumann data q = du/dn."""
         import torch

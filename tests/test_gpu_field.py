@@ -1,0 +1,76 @@
+"""Fields off the surface (fda_scattered_field) and far-field pattern
+(fda_far_field) against the FP64 oracle on the same surface data (only the
+summation order differs: <= 1e-12), and end to end from a GPU solution
+against the Mie series and reciprocity."""
+import numpy as np
+import pytest
+
+import oracle
+from inputs import icosphere, ellipsoid_from_icosphere, complex_normal, fibonacci_directions
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_4747_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def test_field_kernels_match_oracle():
+    from paper_1403_4747_gb300 import FDAProblem
+    v, f = ellipsoid_from_icosphere(3)
+    k = 7.0
+    P = FDAProblem(v, f, k)
+    u = complex_normal(len(f), seed=31)
+    q = complex_normal(len(f), seed=32)
+    dirs = fibonacci_directions(37)  # not a multiple of the block's four targets
+    pts = np.random.default_rng(3).normal(size=(23, 3))
+    pts *= (1.5 + np.random.default_rng(4).random(23))[:, None] / np.linalg.norm(pts, axis=1, keepdims=True)
+    for qq in (None, q):
+        F = P.far_field(_dev(u), dirs, None if qq is None else _dev(qq)).cpu().numpy()
+        assert _rel(F, oracle.far_field(v, f, k, u, dirs, q=qq)) < 1e-12
+        us = P.scattered_field(_dev(u), pts, None if qq is None else _dev(qq)).cpu().numpy()
+        assert _rel(us, oracle.scattered_field(v, f, k, u, pts, q=qq)) < 1e-12
+    P.close()
+
+
+def test_far_field_of_gpu_solution_against_mie():
+    from paper_1403_4747_gb300 import FDAProblem
+    k = 5.0
+    v, f = icosphere(5)
+    P = FDAProblem(v, f, k, precision=1)
+    u, info = P.solve(P.rhs_plane_wave([0.0, 0.0, 1.0]), 1e-6)
+    dirs = fibonacci_directions(60)
+    F = P.far_field(u, dirs).cpu().numpy()
+    assert _rel(F, oracle.mie_far_field(k, dirs[:, 2])) < 3e-3
+    pts = dirs[:10] * 2.0
+    us = P.scattered_field(u, pts).cpu().numpy()
+    assert _rel(us, oracle.mie_scattered_field(k, 2.0, dirs[:10, 2])) < 2e-3
+    P.close()
+
+
+def test_reciprocity_from_gpu_solutions():
+    from paper_1403_4747_gb300 import FDAProblem
+    v, f = ellipsoid_from_icosphere(5)
+    P = FDAProblem(v, f, 3.0, precision=1)
+    d = np.array([0.0, 0.0, 1.0])
+    a = np.array([0.6, 0.0, 0.8])
+    u1, _ = P.solve(P.rhs_plane_wave(d), 1e-7)
+    u2, _ = P.solve(P.rhs_plane_wave(-a), 1e-7)
+    f1 = P.far_field(u1, [a]).cpu().numpy()[0]
+    f2 = P.far_field(u2, [-d]).cpu().numpy()[0]
+    assert abs(f1 - f2) < 7e-3 * abs(f1)  # oracle at level 4: 9.0e-3, first order in h
+    P.close()
