@@ -334,6 +334,9 @@ __global__ void k_jacobi(c64d *A, c64d *V, int n, int npad, int max_sweeps, doub
     for (int e = tid; e < n * n; e += nthreads) V[e] = c64d((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
     grid.sync();
     int sweep = 0;
+    double hist[3] = {0.0, 0.0, 0.0};  // off-diagonal mass of the last three sweeps
+    // round-off floor of the off-diagonal mass after rotations of an n x n matrix
+    const double floor_rel = (8.0 * n * 1.1102230246251565e-16) * (8.0 * n * 1.1102230246251565e-16);
     for (; sweep < max_sweeps; ++sweep) {
         // convergence measure
         if (tid == 0) {
@@ -356,8 +359,15 @@ __global__ void k_jacobi(c64d *A, c64d *V, int n, int npad, int max_sweeps, doub
             atomicAdd(&off[1], sd);
         }
         grid.sync();
-        // stop when the off-diagonal part is at FP64 round-off of the diagonal
-        if (off[0] <= 1e-26 * off[1]) break;
+        // stop when the off-diagonal part is at FP64 round-off of the diagonal,
+        // or when it has stalled for three sweeps at the round-off floor of
+        // an n x n rotation sequence (large n)
+        const double o0 = off[0], d0 = off[1];
+        if (o0 <= 1e-26 * d0) break;
+        if (sweep >= 3 && o0 > 0.5 * hist[0] && o0 <= floor_rel * d0) break;
+        hist[0] = hist[1];
+        hist[1] = hist[2];
+        hist[2] = o0;
         for (int r = 0; r < npad - 1; ++r) {
             // pairs of this round and their rotations
             for (int q = tid; q < half; q += nthreads) {
