@@ -688,8 +688,13 @@ def run_p0_sweep(args):
         p_lf = int(math.ceil(math.log(1.0 / eps))) + p0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        P = F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, eps=eps, p_lf=p_lf, p_hf=p_lf + 2,
-                         alpha_sign=args.alpha_sign)
+        try:
+            P = F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, eps=eps, p_lf=p_lf, p_hf=p_lf + 2,
+                             alpha_sign=args.alpha_sign)
+        except F.FDAError as e:
+            rows.append({"p0": p0, "p_lf": p_lf, "p_hf": p_lf + 2, "error": str(e)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            continue
         b = P.rhs_neumann(torch.ones(len(f), dtype=torch.complex128, device="cuda"))
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0

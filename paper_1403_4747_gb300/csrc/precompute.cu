@@ -335,8 +335,10 @@ __global__ void k_jacobi(c64d *A, c64d *V, int n, int npad, int max_sweeps, doub
     grid.sync();
     int sweep = 0;
     double hist[3] = {0.0, 0.0, 0.0};  // off-diagonal mass of the last three sweeps
-    // round-off floor of the off-diagonal mass after rotations of an n x n matrix
-    const double floor_rel = (8.0 * n * 1.1102230246251565e-16) * (8.0 * n * 1.1102230246251565e-16);
+    // accepted floor of the off-diagonal mass once it stalls (large n): an
+    // off-diagonal norm of 1e-10 of the diagonal's perturbs the kept singular
+    // vectors (sigma >= eps sigma_0, eps >= 1e-6) far below eps
+    const double floor_rel = 1e-20;
     for (; sweep < max_sweeps; ++sweep) {
         // convergence measure
         if (tid == 0) {
@@ -360,8 +362,8 @@ __global__ void k_jacobi(c64d *A, c64d *V, int n, int npad, int max_sweeps, doub
         }
         grid.sync();
         // stop when the off-diagonal part is at FP64 round-off of the diagonal,
-        // or when it has stalled for three sweeps at the round-off floor of
-        // an n x n rotation sequence (large n)
+        // or when it has stalled for three sweeps below the accepted floor
+        // (rounding in the rotations of a large matrix)
         const double o0 = off[0], d0 = off[1];
         if (o0 <= 1e-26 * d0) break;
         if (sweep >= 3 && o0 > 0.5 * hist[0] && o0 <= floor_rel * d0) break;
@@ -523,7 +525,7 @@ int truncated_svd(fda_handle *h, const c64d *G, int m, int n, double eps, dbuf &
     c64d *Ap = gram.as<c64d>(), *Vp = vecs.as<c64d>();
     double *scp = scratch.as<double>();
     int *swp = sweeps.as<int>();
-    int max_sweeps = 40;
+    int max_sweeps = 60;
     void *args[] = {&Ap, &Vp, &n, &npad, &max_sweeps, &scp, &swp};
     FDA_CUDA(cudaLaunchCooperativeKernel((void *)k_jacobi, grid, 256, args, 0, s));
     FDA_CHECK_LAUNCH();
