@@ -731,6 +731,65 @@ def run_p0_sweep(args):
     return 0
 
 
+def run_precond_study(args):
+    """Preconditioners at the large size (icosphere level 9, N = 5,242,880,
+    k = 200): the learned network trained on the leaf blocks of level 6-8
+    spheres and ellipsoids with kD in {50, 100, 200, 300} (weights seed 0),
+    then GMRES to 1e-4 with none, the leaf block-diagonal inverse and the
+    learned preconditioner (chosen form).  Not the headline workload
+    (--workload precond)."""
+    import numpy as np
+    import torch
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import icosphere, ellipsoid_from_icosphere
+    train = [("sphere L6", icosphere(6), 25.0), ("ellipsoid L7", ellipsoid_from_icosphere(7), 50.0),
+             ("sphere L8", icosphere(8), 100.0), ("ellipsoid L8", ellipsoid_from_icosphere(8), 150.0)]
+    hs = []
+    t0 = time.perf_counter()
+    for name, (v, f), k in train:
+        hs.append(F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, alpha_sign=args.alpha_sign))
+    w = F.fda_sai_init_weights(0)
+    rep = F.fda_sai_train([P.h for P in hs], F.fda_sai_default_config(epochs=400, seed=0), w)
+    train_setup_s = time.perf_counter() - t0
+    for P in hs:
+        P.close()
+    del hs
+    torch.cuda.empty_cache()
+    v, f = icosphere(args.precond_level)
+    k = args.precond_k
+    t0 = time.perf_counter()
+    P = F.FDAProblem(v, f, k, precision=F.FDA_CHOSEN_FP32, precond=1, alpha_sign=args.alpha_sign, maxit=600)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    set_loss = F.fda_sai_set(P.h, w)
+    b = P.rhs_plane_wave([0.0, 0.0, 1.0])
+    res = {}
+    x_ref = None
+    for name, pc in (("none", 0), ("blockdiag", 1), ("learned", 2)):
+        F.fda_set_precond(P.h, pc)
+        x, info = P.solve(b, 1e-4, raise_on_not_converged=False)
+        if x_ref is None:
+            x_ref = x.clone()
+        res[name] = {"iters": info.iters, "solve_s": round(info.solve_s, 3), "rel_resid": info.rel_resid_fp64,
+                     "diff_vs_none": float((x - x_ref).norm() / x_ref.norm())}
+        print(json.dumps({name: res[name]}), file=sys.stderr, flush=True)
+    st = P.stats()
+    P.close()
+    line = {"metric": "GMRES iterations and solve time at 1e-4: none vs block-diagonal vs learned",
+            "value": res["learned"]["solve_s"], "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32+bf16x3/f64", "data": "synthetic",
+            "config": {"workload": "icosphere level %d (N = %d), k = %g, plane wave +z, chosen form"
+                                   % (args.precond_level, len(f), k), "alpha_sign": args.alpha_sign,
+                       "training": [{"mesh": n, "N": len(m[1]), "k": kk} for n, m, kk in train]},
+            "train": {"loss_init": rep.loss_init, "loss_final": rep.loss_final, "train_s": rep.train_s,
+                      "setup_and_train_s": train_setup_s},
+            "target_loss": set_loss, "setup_s": setup_s, "device_gb": st.device_bytes / 1e9, "solves": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_far_field(args):
     """Far-field pattern of the headline sphere (level 7, N = 327,680,
     k = 50, plane wave along +z, chosen form, tol 1e-4) on 720 directions in
@@ -806,10 +865,12 @@ def main():
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes", "pulsating", "point_source", "far_field",
-                             "p0_sweep"],
+                             "p0_sweep", "precond"],
                     help="many_meshes: the eight-mesh batch; pulsating: the pulsating-sphere study")
     ap.add_argument("--pulsating-max-level", type=int, default=9)
     ap.add_argument("--p0-level", type=int, default=8, help="octahedral sphere level of the p0 study")
+    ap.add_argument("--precond-level", type=int, default=9, help="icosphere level of the preconditioner study")
+    ap.add_argument("--precond-k", type=float, default=200.0)
     ap.add_argument("--alpha-sign", type=float, default=-1.0, choices=[-1.0, 1.0],
                     help="coupling alpha = sign * i/k of the pulsating and point-source studies "
                          "(-1: the paper's time convention)")
@@ -828,6 +889,8 @@ def main():
         return run_far_field(args)
     if args.workload == "p0_sweep":
         return run_p0_sweep(args)
+    if args.workload == "precond":
+        return run_precond_study(args)
     return run_native(args)
 
 
