@@ -87,6 +87,12 @@ typedef struct {
                               and 128-column tiles, one to three 64-row tiles per CTA tile and 2 to 4 ring
                               stages, and keep the fastest (one right-hand side); 0: fixed rule (32, 64 or
                               128 columns as operators have few or many pairs; one row tile) */
+    const char *autotune_cache; /* NULL (default) or a file path: the autotuner first looks each batch up
+                              there (key: GPU name and SM count, pass, level, ranks, operator and pair
+                              counts) and times only the batches it does not find, appending their choice
+                              as one text line "key columns row_tiles stages" each.  A missing file is
+                              created; an unreadable or unwritable one only disables the cache.  The
+                              string is read during fda_precompute_translations only. */
 } fda_config;
 
 typedef struct {
@@ -116,6 +122,8 @@ typedef struct {
     int32_t level_m2l_ops[32];    /* per level: distinct M2L operators (after the cone symmetry) */
     int64_t graph_replays;        /* operator applications replayed from captured CUDA graphs so far */
     int32_t graph_fallback;       /* 1 if a capture failed and the handle launches kernels one by one */
+    int32_t autotune_cached;      /* tensor-core batches whose tile shape came from the autotune cache */
+    int32_t autotune_timed;       /* tensor-core batches timed by the autotuner at setup */
 } fda_stats;
 
 typedef struct fda_handle fda_handle;

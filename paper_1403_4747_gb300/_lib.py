@@ -27,7 +27,7 @@ class fda_config(ctypes.Structure):
                 ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("precond", ctypes.c_int),
                 ("alpha_sign", ctypes.c_double), ("max_rhs", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p)]
 
 
 class fda_info(ctypes.Structure):
@@ -45,7 +45,8 @@ class fda_stats(ctypes.Structure):
                 ("precompute_s", ctypes.c_double), ("tree_s", ctypes.c_double), ("near_s", ctypes.c_double),
                 ("level_m2l_pairs", ctypes.c_int64 * 32),
                 ("level_m2l_ops", ctypes.c_int32 * 32), ("graph_replays", ctypes.c_int64),
-                ("graph_fallback", ctypes.c_int32)]
+                ("graph_fallback", ctypes.c_int32), ("autotune_cached", ctypes.c_int32),
+                ("autotune_timed", ctypes.c_int32)]
 
 
 class fda_sai_config(ctypes.Structure):
@@ -151,7 +152,7 @@ def fda_default_config(**overrides) -> fda_config:
     c = fda_config()
     load().fda_default_config(ctypes.byref(c))
     for k, v in overrides.items():
-        setattr(c, k, v)
+        setattr(c, k, v.encode() if isinstance(v, str) else v)
     return c
 
 

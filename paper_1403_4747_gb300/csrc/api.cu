@@ -124,6 +124,7 @@ void fda_default_config(fda_config *c)
     c->cuda_stream = nullptr;
     c->graphs = 1;
     c->autotune = 1;
+    c->autotune_cache = nullptr;
 }
 
 fda_status fda_create(const fda_config *cfg, fda_handle **out)
@@ -142,6 +143,8 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
     fda_handle *h = new (std::nothrow) fda_handle();
     if (!h) return FDA_ERR_OOM;
     h->cfg = c;
+    if (c.autotune_cache) h->autotune_cache = c.autotune_cache;
+    h->cfg.autotune_cache = nullptr;  // the handle keeps its own copy
     h->stream = (cudaStream_t)c.cuda_stream;
     fda_status st = guarded(h, [&] {
         for (int i = 0; i < 8; ++i) FDA_CUDA(cudaEventCreate(&h->ev[i]));
@@ -463,6 +466,8 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
         out->n_m2l_ops = ops;
         out->graph_replays = h->graph_replays;
         out->graph_fallback = h->graphs_broken;
+        out->autotune_cached = h->autotune_cached;
+        out->autotune_timed = h->autotune_timed;
         int rb = h->cfg.precision == FDA_CHOSEN_FP32 ? 8 : 16;
         out->bytes_near = h->nnz_near * rb;
         // far-field flop count (real flops, 8 per complex multiply-add)

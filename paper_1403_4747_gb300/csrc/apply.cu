@@ -11,7 +11,12 @@
 // per box and cone; p~ = U_dn^H p).  Every pass is templated on the real
 // type: double (plain FP64 form) or float (chosen form: FP32 operators and
 // densities, FP32 accumulation, the result added into the FP64 output).
+#include <stdio.h>
+
 #include <algorithm>
+#include <array>
+#include <map>
+#include <string>
 
 #include "fda_internal.cuh"
 
@@ -374,6 +379,9 @@ void fda_apply_sorted(fda_handle *h, const c64d *xs, c64d *ys, int precision, in
 // values do not change the work) and timed with CUDA events on the library
 // stream; the faster candidate of the second runs is kept for one right-hand
 // side.  Runs once, at the end of fda_precompute_translations.
+// With an autotune cache file, batches found there (same GPU model, pass,
+// level, ranks, operator and pair counts) take the stored shape untimed;
+// the shapes of the batches timed here are appended to it.
 void fda_autotune_tc(fda_handle *h)
 {
     if (!h->have_tc || h->lev_lo < 0) return;
@@ -385,8 +393,46 @@ void fda_autotune_tc(fda_handle *h)
     // (columns, row tiles, stages)
     static const int cand[8][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4}, {64, 2, 3}, {32, 3, 3},
                                    {128, 1, 3}};
-    auto tune = [&](tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst, int64_t ds) {
+    std::map<std::string, std::array<int, 3>> cache;
+    std::string added;
+    std::string gpu;
+    if (!h->autotune_cache.empty()) {
+        int dev = 0;
+        cudaDeviceProp prop;
+        FDA_CUDA(cudaGetDevice(&dev));
+        FDA_CUDA(cudaGetDeviceProperties(&prop, dev));
+        for (const char *c = prop.name; *c; ++c) gpu += (*c == ' ' || *c == '|') ? '_' : *c;
+        gpu += "|" + std::to_string(prop.multiProcessorCount);
+        if (FILE *f = fopen(h->autotune_cache.c_str(), "r")) {
+            char key[512];
+            int a, b, c;
+            while (fscanf(f, "%511s %d %d %d", key, &a, &b, &c) == 4) cache[key] = {a, b, c};
+            fclose(f);
+        }
+    }
+    auto tune = [&](const char *pass, int l, tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst,
+                    int64_t ds) {
         if (B.npairs == 0 || !T.A.p) return;
+        std::string key;
+        if (!gpu.empty()) {
+            key = gpu + "|" + pass + "|" + std::to_string(l) + "|" + std::to_string(T.Tout) + "|" +
+                  std::to_string(T.Tin) + "|" + std::to_string(B.op_start.empty() ? 0 : B.op_start.size() - 1) +
+                  "|" + std::to_string(B.npairs);
+            auto it = cache.find(key);
+            if (it != cache.end()) {
+                const auto &c = it->second;
+                bool known = false;
+                for (const auto &k : cand) known |= k[0] == c[0] && k[1] == c[1] && k[2] == c[2];
+                if (known && c[1] <= T.nrt) {
+                    T.nc_tuned = c[0];
+                    T.r_tuned = c[1];
+                    T.st_tuned = c[2];
+                    ++h->autotune_cached;
+                    return;
+                }
+            }
+        }
+        ++h->autotune_timed;
         float best = 1e30f;
         for (const auto &c : cand) {
             if (c[1] > T.nrt) continue;
@@ -405,18 +451,29 @@ void fda_autotune_tc(fda_handle *h)
                 T.st_tuned = c[2];
             }
         }
+        if (!key.empty())
+            added += key + " " + std::to_string(T.nc_tuned) + " " + std::to_string(T.r_tuned) + " " +
+                     std::to_string(T.st_tuned) + "\n";
     };
     auto sv = [&](int l) { return P.stride[l] / std::max(1, h->lev[l].T); };
     for (int l = h->lev_lo; l < h->nlev; ++l) {
         if (h->lev[l].T == 0) continue;
-        tune(h->b_m2l[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<float *>(P.p[l]), P.stride[l]);
+        tune("m2l", l, h->b_m2l[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<float *>(P.p[l]), P.stride[l]);
         if (l + 1 < h->nlev && h->lev[l + 1].T > 0) {
-            tune(h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], sv(l + 1), reinterpret_cast<float *>(P.q[l]), P.stride[l]);
-            tune(h->b_l2l[l], h->tc_l2l[l], h->ps[l], sv(l), reinterpret_cast<float *>(P.p[l + 1]), P.stride[l + 1]);
+            tune("m2m", l, h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], sv(l + 1), reinterpret_cast<float *>(P.q[l]),
+                 P.stride[l]);
+            tune("l2l", l, h->b_l2l[l], h->tc_l2l[l], h->ps[l], sv(l), reinterpret_cast<float *>(P.p[l + 1]),
+                 P.stride[l + 1]);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (!added.empty()) {
+        if (FILE *f = fopen(h->autotune_cache.c_str(), "a")) {
+            fputs(added.c_str(), f);
+            fclose(f);
+        }
+    }
     if (fda_tc_error(h)) fda_fail(FDA_ERR_TIMEOUT, "a tensor-core translation gave up waiting on its copies");
 }
 

@@ -242,6 +242,8 @@ struct fda_handle {
     far_ops<float> op32;
     int have32 = 0;
     int rhs_layers = 0;  // near field and S2M of the right-hand side's layers built
+    int autotune_cached = 0, autotune_timed = 0;  // tensor-core batches from the cache / timed at setup
+    std::string autotune_cache;                   // cfg.autotune_cache copied at fda_create ("" = none)
 
     // tensor-core M2L (chosen precision)
     tc_ops tc_m2l[FDA_MAX_LEVELS], tc_m2m[FDA_MAX_LEVELS], tc_l2l[FDA_MAX_LEVELS];

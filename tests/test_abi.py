@@ -71,3 +71,32 @@ def test_batch_arguments_rejected_without_gpu(lib):
     assert lib.fda_batch_mesh(None, 0) is None
     assert lib.fda_batch_last_error(None) == b"null batch"
     lib.fda_destroy_batch(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of fda_config, fda_stats, fda_info and
+    fda_batch_stats have the C structs' sizes and field offsets (gcc)."""
+    import shutil
+    import subprocess
+    from paper_1403_4747_gb300 import _lib
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"fda_config": _lib.fda_config, "fda_stats": _lib.fda_stats, "fda_info": _lib.fda_info,
+               "fda_batch_stats": _lib.fda_batch_stats, "fda_sai_config": _lib.fda_sai_config,
+               "fda_sai_report": _lib.fda_sai_report}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fda_bem.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, fname, name, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(out[name + "." + fname]) == getattr(cls, fname).offset, (name, fname)
