@@ -404,6 +404,10 @@ def run_native(args):
         cpu = {"value": rate, "unit": "matvec/s", "cores": cores, "kind": "oracle",
                "sample": "%d random rows of the dense FP64 oracle matvec (of %d), %.1f s" % (args.cpu_rows, n, dt)}
 
+    if cpu is not None and solve and "plain" in solve:
+        # the oracle's matrix-free GMRES at this size, from its matvec rate and
+        # the FP64 solve's iteration count (too long to run: days)
+        cpu["solve_s_extrapolated"] = solve["plain"]["iters"] / cpu["value"]
     line = {"metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
