@@ -355,7 +355,6 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
         // stages (D1, D2) column-major; then thread (row, half) combines the
         // two lanes of its row for EPC / 2 columns and adds them to the target.
         const int row = (warp & 1) * 32 + lane, half = warp >> 1;
-        const bool even_rank = (Tout & 1) == 0;
         for (int j = 0; j < my_tiles; ++j) {
             const int slot = j & 1;
             const tc_tile t = tiles[blockIdx.x + (int64_t)j * gridDim.x];
@@ -388,36 +387,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
                     for (int jj = 0; jj < EPC; ++jj)
                         stg[jj * 128 + tid] = make_float2(__uint_as_float(v1[jj]), __uint_as_float(v2[jj]));
                     asm volatile("bar.sync 2, 128;");
-                    if (even_rank) {
-                        // lanes 2i and 2i + 1 hold rows rowg and rowg + 1 (rowg even for even
-                        // lanes): each pair of columns becomes two 16-byte atomics, the even lane
-                        // adding both rows of the first column, the odd lane both rows of the
-                        // second.  With an even rank every target offset is even, so the
-                        // address is 16-byte aligned; it is checked anyway.
-                        const bool odd = lane & 1;
-#pragma unroll
-                        for (int jj = half * (EPC / 2); jj < (half + 1) * (EPC / 2); jj += 2) {
-                            const float2 t0 = stg[jj * 128 + row], b0 = stg[jj * 128 + 64 + row];
-                            const float2 t1 = stg[(jj + 1) * 128 + row], b1 = stg[(jj + 1) * 128 + 64 + row];
-                            const float2 a0 = make_float2(t0.x - b0.y, t0.y + b0.x);
-                            const float2 a1 = make_float2(t1.x - b1.y, t1.y + b1.x);
-                            const float2 snd = odd ? a0 : a1;
-                            const float2 rcv = make_float2(__shfl_xor_sync(0xffffffffu, snd.x, 1),
-                                                           __shfl_xor_sync(0xffffffffu, snd.y, 1));
-                            const int n = c0 + jj + (odd ? 1 : 0);
-                            const int r0 = odd ? rowg - 1 : rowg;
-                            if (n < t.npair && r0 < Tout) {
-                                const float2 lo = odd ? rcv : a0, hi = odd ? a1 : rcv;
-                                const long long off = tgt[n] + r0;
-                                if ((off & 1) == 0) {
-                                    atomicAdd(reinterpret_cast<float4 *>(dst + off), make_float4(lo.x, lo.y, hi.x, hi.y));
-                                } else {
-                                    atomicAdd(reinterpret_cast<float2 *>(dst + off), lo);
-                                    if (r0 + 1 < Tout) atomicAdd(reinterpret_cast<float2 *>(dst + off + 1), hi);
-                                }
-                            }
-                        }
-                    } else if (rowg < Tout) {
+                    if (rowg < Tout) {
 #pragma unroll
                         for (int jj = half * (EPC / 2); jj < (half + 1) * (EPC / 2); ++jj) {
                             const int n = c0 + jj;
