@@ -100,3 +100,11 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[name]) == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(out[name + "." + fname]) == getattr(cls, fname).offset, (name, fname)
+
+
+def test_null_handle_calls_of_the_right_hand_sides_and_fields(lib):
+    from paper_1403_4747_gb300 import FDA_ERR_ARG
+    assert lib.fda_rhs_neumann(None, None, None, 1, 1) == FDA_ERR_ARG
+    assert lib.fda_rhs_point_source(None, None, 1, None) == FDA_ERR_ARG
+    assert lib.fda_far_field(None, None, None, None, 1, None) == FDA_ERR_ARG
+    assert lib.fda_scattered_field(None, None, None, None, 1, None) == FDA_ERR_ARG
