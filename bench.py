@@ -544,6 +544,29 @@ def run_many_meshes(args):
         e1.record(stream)
         torch.cuda.synchronize()
         alone_ms.append(e0.elapsed_time(e1))
+    # one right-hand side per mesh: the batch's graph branches against the
+    # meshes' own graph replays one after another
+    x1 = [x[:1].contiguous() for x in xs]
+    y1 = [torch.empty_like(x) for x in x1]
+    for _ in range(3):
+        B.apply(x1, y1)
+        for i in range(len(mm)):
+            F.fda_apply(B.mesh(i), x1[i].data_ptr(), y1[i].data_ptr(), 1, len(mm[i][1]))
+    torch.cuda.synchronize()
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        B.apply(x1, y1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    one_batch_ms = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        for i in range(len(mm)):
+            F.fda_apply(B.mesh(i), x1[i].data_ptr(), y1[i].data_ptr(), 1, len(mm[i][1]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    one_seq_ms = e0.elapsed_time(e1) / reps
     line = {"metric": "many-mesh batched FDA matvec (mesh x right-hand side)/s", "value": ws * len(mm) * nrhs * 1e3 / ms,
             "unit": "matvec/s", "n_gpus": ws, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3/f64",
@@ -555,7 +578,10 @@ def run_many_meshes(args):
                              % (st.n_total * nrhs * 16 * 2 / 1e9)},
             "setup_s": setup_s, "device_gb": st.device_bytes / 1e9, "gpu_launches": launches,
             "cuda_graph_replays": st.graph_replays - gr0, "graph_fallback": st.graph_fallback,
-            "sequential_handles_ms": sum(alone_ms), "per_mesh_ms": alone_ms, "clocks": clk}
+            "sequential_handles_ms": sum(alone_ms), "per_mesh_ms": alone_ms,
+            "one_rhs": {"batch_ms": one_batch_ms, "sequential_handles_ms": one_seq_ms,
+                        "batch_matvec_per_s": len(mm) * 1e3 / one_batch_ms},
+            "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     B.close()
