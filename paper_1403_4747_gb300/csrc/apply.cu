@@ -25,6 +25,7 @@ namespace {
 constexpr int AT = 256;    // threads per CTA
 constexpr int MAXR = 4;    // rows per thread (rank <= 1024)
 constexpr int MAXT = AT * MAXR;
+static_assert(AT % 64 == 0, "the L2T groups split the CTA into 64-row slices");
 
 template <typename R>
 struct lvl_ptrs {
@@ -141,12 +142,16 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
 }
 
 // ---- Step 2: S2M at leaves, q~ = S~ x_B
+// One CTA per leaf.  With T < blockDim the CTA splits the sum over the
+// leaf's elements into blockDim / T interleaved groups (every thread has a
+// share of the loads) and adds the groups' partial sums in shared memory.
 template <typename R>
 __global__ void k_s2m(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *blev, const int32_t *bbeg,
                       const int32_t *bend, const int64_t *loff, const cx<R> *St, const void *x, int x64,
                       int64_t xstr, int mr)
 {
     __shared__ cx<R> xs[64];
+    __shared__ cx<R> part[AT];
     int li = blockIdx.x;
     int B = leaf_box[li];
     int l = blev[B];
@@ -154,25 +159,50 @@ __global__ void k_s2m(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
     if (T == 0) return;
     int j0 = bbeg[B], nB = bend[B] - j0;
     const cx<R> *S = St + loff[li];
+    const int G = T < (int)blockDim.x ? (int)blockDim.x / T : 1;
     for (int m = 0; m < mr; ++m) {
         __syncthreads();
         for (int j = threadIdx.x; j < nB; j += blockDim.x) xs[j] = ldx<R>(x, (int64_t)m * xstr + j0 + j, x64);
         __syncthreads();
         cx<R> *q = P.q[l] + m * P.stride[l] + (int64_t)(B - P.box0[l]) * T;
-        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        if (G == 1) {
+            for (int t = threadIdx.x; t < T; t += blockDim.x) {
+                cx<R> acc;
+#pragma unroll 4
+                for (int j = 0; j < nB; ++j) cfma(acc, S[(int64_t)j * T + t], xs[j]);
+                q[t] = acc;
+            }
+        } else {
+            const int g = threadIdx.x / T, t = threadIdx.x - g * T;
             cx<R> acc;
-            for (int j = 0; j < nB; ++j) cfma(acc, S[(int64_t)j * T + t], xs[j]);
-            q[t] = acc;
+            if (g < G) {
+#pragma unroll 4
+                for (int j = g; j < nB; j += G) cfma(acc, S[(int64_t)j * T + t], xs[j]);
+            }
+            part[threadIdx.x] = acc;
+            __syncthreads();
+            if ((int)threadIdx.x < T) {
+                cx<R> sum = part[threadIdx.x];
+                for (int gg = 1; gg < G; ++gg) {
+                    const cx<R> v = part[gg * T + threadIdx.x];
+                    sum.re += v.re;
+                    sum.im += v.im;
+                }
+                q[threadIdx.x] = sum;
+            }
         }
     }
 }
 
 // ---- Step 3: L2T at leaves, y += T~ p~
+// One CTA per leaf; blockDim / 64 groups split the sum over the rank and add
+// their partial sums in shared memory.
 template <typename R>
 __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *blev, const int32_t *bbeg,
                       const int32_t *bend, const int64_t *loff, const cx<R> *Tt, c64d *y, int64_t ldy, int mr)
 {
     __shared__ cx<R> pp[MAXT];
+    __shared__ cx<R> part[AT];
     int li = blockIdx.x;
     int B = leaf_box[li];
     int l = blev[B];
@@ -180,17 +210,29 @@ __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
     if (T == 0) return;
     int i0 = bbeg[B], nB = bend[B] - i0;
     const cx<R> *Tm = Tt + loff[li];
+    const int G = (int)blockDim.x / 64, g = threadIdx.x / 64, i = threadIdx.x - g * 64;
     for (int m = 0; m < mr; ++m) {
         const cx<R> *src = P.p[l] + m * P.stride[l] + (int64_t)(B - P.box0[l]) * T;
         __syncthreads();
         for (int j = threadIdx.x; j < T; j += blockDim.x) pp[j] = src[j];
         __syncthreads();
-        for (int i = threadIdx.x; i < nB; i += blockDim.x) {
-            cx<R> acc;
-            for (int t = 0; t < T; ++t) cfma(acc, Tm[(int64_t)t * 64 + i], pp[t]);
-            c64d *yp = y + (int64_t)m * ldy + i0 + i;
+        cx<R> acc;
+        if (i < nB) {
+#pragma unroll 4
+            for (int t = g; t < T; t += G) cfma(acc, Tm[(int64_t)t * 64 + i], pp[t]);
+        }
+        part[threadIdx.x] = acc;
+        __syncthreads();
+        if ((int)threadIdx.x < nB) {
+            cx<R> sum = part[threadIdx.x];
+            for (int gg = 1; gg < G; ++gg) {
+                const cx<R> v = part[gg * 64 + threadIdx.x];
+                sum.re += v.re;
+                sum.im += v.im;
+            }
+            c64d *yp = y + (int64_t)m * ldy + i0 + threadIdx.x;
             c64d v = *yp;
-            *yp = c64d(v.re + (double)acc.re, v.im + (double)acc.im);
+            *yp = c64d(v.re + (double)sum.re, v.im + (double)sum.im);
         }
     }
 }
