@@ -25,7 +25,6 @@ namespace {
 constexpr int AT = 256;    // threads per CTA
 constexpr int MAXR = 4;    // rows per thread (rank <= 1024)
 constexpr int MAXT = AT * MAXR;
-static_assert(AT % 64 == 0, "the L2T groups split the CTA into 64-row slices");
 
 template <typename R>
 struct lvl_ptrs {
@@ -195,14 +194,11 @@ __global__ void k_s2m(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
 }
 
 // ---- Step 3: L2T at leaves, y += T~ p~
-// One CTA per leaf; blockDim / 64 groups split the sum over the rank and add
-// their partial sums in shared memory.
 template <typename R>
 __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *blev, const int32_t *bbeg,
                       const int32_t *bend, const int64_t *loff, const cx<R> *Tt, c64d *y, int64_t ldy, int mr)
 {
     __shared__ cx<R> pp[MAXT];
-    __shared__ cx<R> part[AT];
     int li = blockIdx.x;
     int B = leaf_box[li];
     int l = blev[B];
@@ -210,29 +206,17 @@ __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
     if (T == 0) return;
     int i0 = bbeg[B], nB = bend[B] - i0;
     const cx<R> *Tm = Tt + loff[li];
-    const int G = (int)blockDim.x / 64, g = threadIdx.x / 64, i = threadIdx.x - g * 64;
     for (int m = 0; m < mr; ++m) {
         const cx<R> *src = P.p[l] + m * P.stride[l] + (int64_t)(B - P.box0[l]) * T;
         __syncthreads();
         for (int j = threadIdx.x; j < T; j += blockDim.x) pp[j] = src[j];
         __syncthreads();
-        cx<R> acc;
-        if (i < nB) {
-#pragma unroll 4
-            for (int t = g; t < T; t += G) cfma(acc, Tm[(int64_t)t * 64 + i], pp[t]);
-        }
-        part[threadIdx.x] = acc;
-        __syncthreads();
-        if ((int)threadIdx.x < nB) {
-            cx<R> sum = part[threadIdx.x];
-            for (int gg = 1; gg < G; ++gg) {
-                const cx<R> v = part[gg * 64 + threadIdx.x];
-                sum.re += v.re;
-                sum.im += v.im;
-            }
-            c64d *yp = y + (int64_t)m * ldy + i0 + threadIdx.x;
+        for (int i = threadIdx.x; i < nB; i += blockDim.x) {
+            cx<R> acc;
+            for (int t = 0; t < T; ++t) cfma(acc, Tm[(int64_t)t * 64 + i], pp[t]);
+            c64d *yp = y + (int64_t)m * ldy + i0 + i;
             c64d v = *yp;
-            *yp = c64d(v.re + (double)sum.re, v.im + (double)sum.im);
+            *yp = c64d(v.re + (double)acc.re, v.im + (double)acc.im);
         }
     }
 }
