@@ -164,3 +164,43 @@ def test_pulsating_sphere_matches_paper_table():
         errs.append(err)
         assert abs(err - paper[(len(f), kp)]) < 0.1 * paper[(len(f), kp)], (len(f), err)
     assert 1.6 < errs[0] / errs[1] < 2.4
+
+
+def _brute_single_layer(x, nx, p, k):
+    """adaptive 2-D quadrature of G + alpha dG/dn_x over triangle p"""
+    p = np.asarray(p)
+    e1, e2 = p[1] - p[0], p[2] - p[0]
+    jac = np.linalg.norm(np.cross(e1, e2))
+    alpha = 1j / k
+
+    def f(t, s, part):
+        y = p[0] + s * e1 + t * e2
+        g = oracle.kernels(x, nx, y, nx, k)
+        v = (g[0] + alpha * g[2]) * jac
+        return v.real if part == 0 else v.imag
+
+    re = integrate.dblquad(f, 0, 1, 0, lambda s: 1 - s, args=(0,), epsabs=1e-12, epsrel=1e-11)[0]
+    im = integrate.dblquad(f, 0, 1, 0, lambda s: 1 - s, args=(1,), epsabs=1e-12, epsrel=1e-11)[0]
+    return re + 1j * im
+
+
+@pytest.mark.parametrize("case", ["edge_neighbour", "vertex_neighbour", "far"])
+def test_rhs_element_rules_against_brute_force(case):
+    """The right-hand side's layers through the same element rules: near
+    pairs (subdivided rule) and far pairs (six-point rule) against adaptive
+    quadrature of G + alpha dG/dn_x."""
+    v, f = icosphere(2)
+    c, n, a, h2 = oracle.geometry(v, f)
+    i = 0
+    shared = [len(set(f[i]) & set(f[j])) for j in range(len(f))]
+    if case == "edge_neighbour":
+        j = next(j for j in range(len(f)) if shared[j] == 2)
+    elif case == "vertex_neighbour":
+        j = next(j for j in range(len(f)) if shared[j] == 1)
+    else:
+        j = int(np.argmax(np.linalg.norm(c - c[i], axis=1)))
+    k = 5.0
+    got = oracle.rhs_layers_entry(v, f, k, i, j)
+    ref = _brute_single_layer(c[i], n[i], v[f[j]], k)
+    tol = 1e-4 if case != "far" else 1e-6
+    assert abs(got - ref) < tol * abs(ref), (got, ref)
