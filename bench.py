@@ -142,13 +142,20 @@ class ClockSampler:
 
 
 def _cpu_oracle_rate(v, f, k, x, rows_n, seed=7):
+    """Oracle matvec rate on sampled rows (matvec/s equivalent); also returns
+    the rows and the oracle's values there, for the GPU results' error."""
     import numpy as np
     import oracle
     rows = np.random.default_rng(seed).choice(len(f), rows_n, replace=False)
     t0 = time.perf_counter()
-    oracle.matvec(v, f, k, x, rows=rows)
+    ref = oracle.matvec(v, f, k, x, rows=rows)
     dt = time.perf_counter() - t0
-    return (rows_n / len(f)) / dt, dt, oracle.num_threads()
+    return (rows_n / len(f)) / dt, dt, oracle.num_threads(), rows, ref
+
+
+def _rel(a, b):
+    import numpy as np
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def run_reference(args):
@@ -239,6 +246,7 @@ def run_native(args):
     ms = e0.elapsed_time(e1) / args.steps
     ms = reduce_max(ms)
     value = ws * 1e3 / ms
+    y_chosen = y.cpu().numpy()
 
     # end to end through the C ABI with host buffers (pinned)
     xh = torch.from_numpy(complex_normal(n, seed=99)).pin_memory()
@@ -274,6 +282,7 @@ def run_native(args):
         P.apply(x, y)
     torch.cuda.synchronize()
     plain_ms = (time.perf_counter() - tp) / nplain * 1e3
+    y_plain = y.cpu().numpy()
     pt64 = pass_times(1)
     F.fda_set_precision(P.h, F.FDA_CHOSEN_FP32)
 
@@ -349,8 +358,10 @@ def run_native(args):
                  "frac": near_gbs / hbm_peak, "ms_per_apply": pt32[5], "algorithmic_bytes_per_apply": near_bytes}
 
     solve = {}
+    u_chosen = b_host = None
     if not args.no_solve:
         b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+        b_host = b.cpu().numpy()
         runs = [("chosen", F.FDA_CHOSEN_FP32, 0)]
         if args.blockdiag:
             runs.append(("chosen_blockdiag", F.FDA_CHOSEN_FP32, 1))
@@ -363,6 +374,8 @@ def run_native(args):
             ts = time.perf_counter()
             xs, info = P.solve(b, args.tol, raise_on_not_converged=False)
             torch.cuda.synchronize()
+            if name == "chosen":
+                u_chosen = xs.cpu().numpy()
             solve[name] = {"solve_s": time.perf_counter() - ts, "iters": info.iters,
                            "refinements": info.refinements, "rel_resid_fp64": info.rel_resid_fp64,
                            "matvec_s": info.matvec_s, "precond": ["none", "blockdiag"][pc]}
@@ -372,18 +385,20 @@ def run_native(args):
             solve["speedup_chosen_over_plain"] = solve["plain"]["solve_s"] / solve["chosen"]["solve_s"]
         solve["setup_s"] = setup_s
         solve["restart"] = args.restart
-        solve["coupling"] = "alpha = +i/k (normal into the body)"
+        solve["coupling"] = "alpha = -i/k with the normal into the body (library default; the paper's operator)"
         if not args.no_alt_coupling:
-            # the conjugate coupling alpha = -i/k: same scattering problem, eigenvalues in the right half-plane
+            # the coupling as printed, alpha = +i/k: same scattering problem,
+            # sphere eigenvalues around 0, many more iterations
             P.close()
             t0 = time.perf_counter()
-            Q = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps, alpha_sign=-1.0,
+            Q = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps, alpha_sign=1.0,
                              restart=args.restart)
             torch.cuda.synchronize()
             setup_q = time.perf_counter() - t0
             bq = Q.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
             alt = {}
-            for name, prec in (("chosen", F.FDA_CHOSEN_FP32), ("plain", F.FDA_PLAIN_FP64)):
+            forms = [("chosen", F.FDA_CHOSEN_FP32)] + ([("plain", F.FDA_PLAIN_FP64)] if args.alt_plain else [])
+            for name, prec in forms:
                 F.fda_set_precision(Q.h, prec)
                 torch.cuda.synchronize()
                 ts = time.perf_counter()
@@ -392,17 +407,30 @@ def run_native(args):
                 alt[name] = {"solve_s": time.perf_counter() - ts, "iters": info.iters,
                              "refinements": info.refinements, "rel_resid_fp64": info.rel_resid_fp64}
             alt["setup_s"] = setup_q
-            alt["speedup_chosen_over_plain"] = alt["plain"]["solve_s"] / max(alt["chosen"]["solve_s"], 1e-9)
-            solve["conjugate_coupling"] = alt
+            if "plain" in alt:
+                alt["speedup_chosen_over_plain"] = alt["plain"]["solve_s"] / max(alt["chosen"]["solve_s"], 1e-9)
+            solve["printed_coupling_plus_i_over_k"] = alt
             Q.close()
             P = None
 
     cpu = None
+    err = None
     if rank == 0 and not args.no_cpu:
+        import oracle
         xc = complex_normal(n, seed=1234)
-        rate, dt, cores = _cpu_oracle_rate(v, f, k, xc, args.cpu_rows)
+        rate, dt, cores, rows, ref = _cpu_oracle_rate(v, f, k, xc, args.cpu_rows)
         cpu = {"value": rate, "unit": "matvec/s", "cores": cores, "kind": "oracle",
                "sample": "%d random rows of the dense FP64 oracle matvec (of %d), %.1f s" % (args.cpu_rows, n, dt)}
+        # the timed GPU products against the same oracle rows (same x)
+        err = {"rows": int(args.cpu_rows), "row_seed": 7, "metric": "relative L2 over the sampled rows",
+               "chosen_matvec": _rel(y_chosen[rows], ref), "plain_matvec": _rel(y_plain[rows], ref)}
+        if u_chosen is not None:
+            # the chosen solve's solution: residual b - A u with the oracle's A on
+            # the first 256 sampled rows, and its distance to the Mie series
+            r2 = rows[:256]
+            err["solution_oracle_residual"] = _rel(oracle.matvec(v, f, k, u_chosen, rows=r2), b_host[r2])
+            c = np.mean(v[f], axis=1)
+            err["solution_vs_mie"] = _rel(u_chosen, oracle.mie_surface_field(k, c[:, 2] / np.linalg.norm(c, axis=1)))
 
     if cpu is not None and solve and "plain" in solve:
         # the oracle's matrix-free GMRES at this size, from its matvec rate and
@@ -426,6 +454,7 @@ def run_native(args):
                            "pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt64.tolist()))},
             "chosen_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32.tolist())),
             "chosen_simt_m2l_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], pt32_simt.tolist())),
+            "err_vs_oracle": err,
             "near_field_roofline": near_roof,
             "batched_rhs": batched,
             "solve": solve,
@@ -890,6 +919,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-plain-unpreconditioned", action="store_true")
     ap.add_argument("--no-alt-coupling", action="store_true")
+    ap.add_argument("--alt-plain", action="store_true",
+                    help="also solve the alpha = +i/k problem with the plain FP64 form (about a minute)")
     ap.add_argument("--blockdiag", action="store_true", help="also solve with the block-diagonal preconditioner")
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")

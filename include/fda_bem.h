@@ -71,8 +71,12 @@ typedef struct {
     int maxit;             /* GMRES iteration cap (default 1000) */
     int precond;           /* 0 none (the paper's setting), 1 leaf block-diagonal (right preconditioner);
                               the learned preconditioner (2) is selected with fda_set_precond after fda_sai_set */
-    double alpha_sign;     /* coupling alpha = alpha_sign * i/k: +1 (default) the paper's i/k as written with the
-                              normal into the body; -1 the conjugate coupling */
+    double alpha_sign;     /* coupling alpha = alpha_sign * i/k with G = e^{ikr}/(4 pi r) and the normal into
+                              the body.  -1 (default): the paper's operator.  Its closed form of Sec. 5.1,
+                              u = 1/(1 + ik), and its iteration counts (Table tab_usphpls, Sec. 5.3) hold for
+                              the complex conjugate of the printed equations (G = e^{-ikr}, alpha = i/k), and
+                              conjugating that gives alpha = -i/k here.  +1: alpha = +i/k as printed, which
+                              puts sphere eigenvalues around 0 and slows GMRES down */
     int max_rhs;           /* right-hand sides one fda_apply pass processes together (1..256, default 1);
                               densities and staging vectors are sized for it */
     int tensor_cores;      /* chosen precision: run M2L on the tensor cores (split-bf16 tcgen05 GEMMs, FP32
@@ -229,8 +233,14 @@ fda_status fda_rhs_neumann(fda_handle *h, const fda_c128 *q, fda_c128 *b, int nr
  *     host threads) race on it.  The first call on a device looks up the
  *     array's device address; make that first call before any stream
  *     capture.
- * The result equals fda_rhs_plane_wave's.  Stream-ordered; does not
- * synchronise. */
+ *   - dirs is copied into the staging array by cudaMemcpyAsync on the
+ *     handle's stream.  From pageable host memory CUDA may first wait for
+ *     the stream's earlier work and returns once dirs has been read, so the
+ *     caller may reuse dirs on return.  From pinned host memory the copy runs
+ *     later, in stream order: dirs must stay valid and unchanged until the
+ *     stream has reached it (synchronise, or wait on an event recorded after
+ *     the call).
+ * The result equals fda_rhs_plane_wave's.  Stream-ordered. */
 #define FDA_NOALLOC_MAX_DIRS 256
 fda_status fda_rhs_plane_wave_noalloc(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b);
 
@@ -251,6 +261,17 @@ fda_status fda_set_precision(fda_handle *h, int precision);
 /* Switch the tensor-core M2L of the chosen precision on (1) or off (0) for
  * later calls (needs a handle created with tensor_cores = 1 to turn on). */
 fda_status fda_set_tensor_cores(fda_handle *h, int on);
+
+/* Force the tile shape of every tensor-core translation launch (Sec. 3.3
+ * Steps 2-3 on the tensor cores) for later calls, in place of the
+ * autotuner's choice: (columns per tile, 64-row tiles per CTA tile, ring
+ * stages) one of (32,1,2), (32,1,4), (64,1,2), (64,1,4), (32,2,4), (64,2,3),
+ * (32,3,3), (128,1,3); (0,0,0) returns to the tuned shapes.  A shape with
+ * more row tiles than an operator has falls back to one row tile there.
+ * Captured graphs are released (the next applies capture again).  Results
+ * equal the tuned shapes' up to the rounding order of the float atomics.
+ * FDA_ERR_ARG for any other shape. */
+fda_status fda_set_tc_tiles(fda_handle *h, int columns, int row_tiles, int stages);
 
 /* Select the preconditioner used by later fda_solve calls: 0 none, 1 leaf
  * block-diagonal (needs a handle created with precond = 1, which builds the

@@ -97,7 +97,7 @@ def gauss_legendre(n):
     return xs, ws
 
 
-def entry(verts, tris, k, i, j, alpha_sign=1.0):
+def entry(verts, tris, k, i, j, alpha_sign=-1.0):
     v, t = _mesh(verts, tris)
     load().orc_set_alpha_sign(float(alpha_sign))
     out = np.empty(2)
@@ -110,7 +110,7 @@ def is_near_pair(verts, tris, i, j) -> bool:
     return bool(load().orc_is_near_pair(_d(v), t.ctypes.data_as(_ip), int(i), int(j)))
 
 
-def matvec(verts, tris, k, x, rows=None, nthreads=0, alpha_sign=1.0):
+def matvec(verts, tris, k, x, rows=None, nthreads=0, alpha_sign=-1.0):
     """y = A x (all rows, or the listed rows).  x: complex [N] or [nrhs, N];
     returns complex [len(rows)] or [nrhs, len(rows)].  alpha = alpha_sign i/k."""
     v, t = _mesh(verts, tris)
@@ -131,7 +131,7 @@ def matvec(verts, tris, k, x, rows=None, nthreads=0, alpha_sign=1.0):
     return y[0] if squeeze else y
 
 
-def assemble(verts, tris, k, nthreads=0, alpha_sign=1.0):
+def assemble(verts, tris, k, nthreads=0, alpha_sign=-1.0):
     v, t = _mesh(verts, tris)
     load().orc_set_alpha_sign(float(alpha_sign))
     n = t.shape[0]
@@ -140,7 +140,7 @@ def assemble(verts, tris, k, nthreads=0, alpha_sign=1.0):
     return a
 
 
-def rhs_plane_wave(verts, tris, k, dirs, alpha_sign=1.0):
+def rhs_plane_wave(verts, tris, k, dirs, alpha_sign=-1.0):
     """b = u_inc + alpha du_inc/dn at centroids; dirs [nrhs, 3] -> [nrhs, N]"""
     v, t = _mesh(verts, tris)
     load().orc_set_alpha_sign(float(alpha_sign))
@@ -179,18 +179,18 @@ def _with_side(fn):
         load().orc_set_side(0)
 
 
-def rhs_layers_matvec(verts, tris, k, q, rows=None, nthreads=0, alpha_sign=1.0):
+def rhs_layers_matvec(verts, tris, k, q, rows=None, nthreads=0, alpha_sign=-1.0):
     """b = B q: b_i = -alpha q_i / 2 + sum_j int_{tri_j} [G + alpha dG/dn_x](x_i, y) dy q_j
     (all rows or the listed rows; q complex [N] or [nrhs, N])."""
     return _with_side(lambda: matvec(verts, tris, k, q, rows=rows, nthreads=nthreads, alpha_sign=alpha_sign))
 
 
-def rhs_layers_assemble(verts, tris, k, nthreads=0, alpha_sign=1.0):
+def rhs_layers_assemble(verts, tris, k, nthreads=0, alpha_sign=-1.0):
     """Dense B (row-major [N, N], small meshes only)."""
     return _with_side(lambda: assemble(verts, tris, k, nthreads=nthreads, alpha_sign=alpha_sign))
 
 
-def rhs_layers_entry(verts, tris, k, i, j, alpha_sign=1.0):
+def rhs_layers_entry(verts, tris, k, i, j, alpha_sign=-1.0):
     load().orc_set_alpha_sign(float(alpha_sign))
     return _with_side(lambda: entry(verts, tris, k, i, j, alpha_sign=alpha_sign))
 
@@ -203,7 +203,7 @@ def self_single_layer(verts, tris, t, k):
     return out[0] + 1j * out[1]
 
 
-def rhs_point_source(verts, tris, k, sources, alpha_sign=1.0):
+def rhs_point_source(verts, tris, k, sources, alpha_sign=-1.0):
     """b = u_inc + alpha du_inc/dn at centroids for u_inc = G(x, x_s);
     sources [nrhs, 3] -> [nrhs, N]"""
     v, t = _mesh(verts, tris)

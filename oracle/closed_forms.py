@@ -63,7 +63,7 @@ def mie_surface_field(k: float, cos_theta, nmax: int | None = None):
     return u
 
 
-def sphere_eigenvalue(n: int, k: float, alpha_sign: float = 1.0) -> complex:
+def sphere_eigenvalue(n: int, k: float, alpha_sign: float = -1.0) -> complex:
     """lambda_n for alpha = alpha_sign i/k: 1/2 + D + alpha H with
     D[Y_n] = -(i k^2/2)(j_n' h_n + j_n h_n') Y_n and H[Y_n] = i k^3 j_n' h_n' Y_n."""
     jn = special.spherical_jn(n, k)
@@ -81,7 +81,7 @@ def legendre_on_mesh(centroids, n: int, axis=(0.0, 0.0, 1.0)):
     return special.eval_legendre(n, u @ np.asarray(axis, dtype=np.float64))
 
 
-def sphere_rhs_eigenvalue(n: int, k: float, alpha_sign: float = 1.0) -> complex:
+def sphere_rhs_eigenvalue(n: int, k: float, alpha_sign: float = -1.0) -> complex:
     """beta_n for alpha = alpha_sign i/k: -alpha/2 + S + alpha K' on P_n."""
     jn = special.spherical_jn(n, k)
     jd = special.spherical_jn(n, k, derivative=True)

@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.fda_set_precision.argtypes = [H, cint]
     lib.fda_set_precond.argtypes = [H, cint]
     lib.fda_set_tensor_cores.argtypes = [H, cint]
+    lib.fda_set_tc_tiles.argtypes = [H, cint, cint, cint]
     lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
     lib.fda_cone_symmetry_table.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.fda_cone_symmetry_table.restype = ctypes.c_int
@@ -131,7 +132,7 @@ def load(path: str = LIB_PATH):
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
                  "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_far_field", "fda_scattered_field", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
-                 "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores"):
+                 "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores", "fda_set_tc_tiles"):
         getattr(lib, name).restype = cint
     _lib = lib
     return lib
@@ -248,6 +249,10 @@ def fda_set_precond(h, precond):
 
 def fda_set_tensor_cores(h, on):
     _check(h, load().fda_set_tensor_cores(h, 1 if on else 0))
+
+
+def fda_set_tc_tiles(h, columns=0, row_tiles=0, stages=0):
+    _check(h, load().fda_set_tc_tiles(h, int(columns), int(row_tiles), int(stages)))
 
 
 def fda_set_timing(h, enable=True):

@@ -118,7 +118,7 @@ void fda_default_config(fda_config *c)
     c->restart = 100;
     c->maxit = 1000;
     c->precond = 0;
-    c->alpha_sign = 1.0;
+    c->alpha_sign = -1.0;
     c->max_rhs = 1;
     c->tensor_cores = 1;
     c->cuda_stream = nullptr;
@@ -542,6 +542,26 @@ fda_status fda_set_tensor_cores(fda_handle *h, int on)
     }
     h->cfg.tensor_cores = on;
     return FDA_OK;
+}
+
+fda_status fda_set_tc_tiles(fda_handle *h, int columns, int row_tiles, int stages)
+{
+    if (!h) return FDA_ERR_ARG;
+    static const int shapes[8][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4},
+                                     {32, 2, 4}, {64, 2, 3}, {32, 3, 3}, {128, 1, 3}};
+    bool known = columns == 0 && row_tiles == 0 && stages == 0;
+    for (const auto &c : shapes) known |= c[0] == columns && c[1] == row_tiles && c[2] == stages;
+    if (!known) {
+        h->err = "unknown tensor-core tile shape (columns, row tiles, stages)";
+        return FDA_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        // captured graphs hold the previous shape's launches
+        fda_graphs_release(h);
+        h->tc_force[0] = columns;
+        h->tc_force[1] = row_tiles;
+        h->tc_force[2] = stages;
+    });
 }
 
 fda_status fda_set_precond(fda_handle *h, int precond)

@@ -250,6 +250,7 @@ struct fda_handle {
     dbuf qs[FDA_MAX_LEVELS], ps[FDA_MAX_LEVELS];  // FP32 densities split into bf16 hi/lo
     dbuf tc_err;
     int have_tc = 0;
+    int tc_force[3] = {0, 0, 0};  // tile shape forced by fda_set_tc_tiles (columns, row tiles, stages; 0 = auto)
 
     // batched translations per level (M2L at l; M2M and L2L between l and l+1)
     tr_batch b_m2l[FDA_MAX_LEVELS], b_m2m[FDA_MAX_LEVELS], b_l2l[FDA_MAX_LEVELS];

@@ -556,6 +556,11 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
         R = P.r_tuned;
         ST = P.st_tuned;
     }
+    if (!nc && !rows && !st && h->tc_force[0]) {
+        nc = h->tc_force[0];
+        rows = h->tc_force[1];
+        st = h->tc_force[2];
+    }
     if (nc) NC = nc;
     if (rows) R = rows;
     if (st) ST = st;

@@ -39,6 +39,11 @@ def test_default_config(lib):
     c = fda_default_config()
     assert c.eps == 1e-4 and c.leaf_max == 64 and c.p_lf == 8 and c.restart == 100
     assert c.precision == 0 and c.mode == 0 and c.graphs == 1 and c.autotune == 1
+    assert c.alpha_sign == -1.0
+
+
+def test_tile_shape_override_null_handle(lib):
+    assert lib.fda_set_tc_tiles(None, 0, 0, 0) == 1
 
 
 @pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", 0.5), ("leaf_max", 0), ("leaf_max", 65),

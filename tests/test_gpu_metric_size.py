@@ -1,0 +1,145 @@
+"""Parity at the benchmark's own size: unit icosphere level 7 (327,680
+triangles), k = 50 (kD = 100), eps = 1e-4, leaves <= 64 elements, and the
+level-7 ellipsoid with semi-axes (1, 0.6, 0.3) at the same k.
+
+At this size the tree has high-frequency levels with hundreds of cones and
+translation ranks above 300 (six 64-row tiles and eleven 32-wide K chunks
+per operator), which no smaller mesh reaches.  The reference is 256 rows
+(seed 7) of the FP64 oracle's dense matvec of the same vector; the bar is
+the FDA's accuracy eps = 1e-4 (Eq. epsg) as a relative L2 error over the
+sampled rows, for
+  - the chosen form with the autotuned tile shapes and with each of the
+    eight tile shapes the tensor-core translation kernel can launch, forced
+    through fda_set_tc_tiles (these also agree with the tuned result to the
+    rounding order of the float atomics);
+  - the plain FP64 form;
+  - both couplings alpha = -i/k (the default) and +i/k;
+  - the ellipsoid, both forms;
+  - a GMRES solution of the plane-wave problem: its residual b - A u over the
+    sampled rows, with A the oracle's operator, stays within the solve
+    tolerance plus the FDA's error, and its distance to the Mie series is
+    the discretisation error of constant elements at about 13 per
+    wavelength.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from inputs import icosphere, ellipsoid_from_icosphere, complex_normal
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+K = 50.0
+ROWS = 256
+SHAPES = [(32, 1, 2), (32, 1, 4), (64, 1, 2), (64, 1, 4), (32, 2, 4), (64, 2, 3), (32, 3, 3), (128, 1, 3)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_4747_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def _rows(n):
+    return np.random.default_rng(7).choice(n, ROWS, replace=False)
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    v, f = icosphere(7)
+    x = complex_normal(len(f), seed=1234)
+    return v, f, x, _rows(len(f))
+
+
+def test_sphere_every_tile_shape_and_both_precisions(sphere):
+    from paper_1403_4747_gb300 import FDAProblem, fda_set_tc_tiles, fda_set_precision
+    v, f, x, rows = sphere
+    ref = oracle.matvec(v, f, K, x, rows=rows)
+    P = FDAProblem(v, f, K, precision=1)
+    try:
+        st = P.stats()
+        ranks = [st.level_rank[l] for l in range(st.n_levels)]
+        cones = [st.level_cones[l] for l in range(st.n_levels)]
+        assert max(ranks) > 300 and max(cones) >= 96, (ranks, cones)
+        xd = _dev(x)
+        y_tuned = P.apply(xd).cpu().numpy()
+        errs = {"tuned": _rel(y_tuned[rows], ref)}
+        for shape in SHAPES:
+            fda_set_tc_tiles(P.h, *shape)
+            y = P.apply(xd).cpu().numpy()
+            errs[shape] = _rel(y[rows], ref)
+            assert _rel(y, y_tuned) < 1e-5, shape
+        fda_set_tc_tiles(P.h, 0, 0, 0)
+        fda_set_precision(P.h, 0)
+        errs["plain"] = _rel(P.apply(xd).cpu().numpy()[rows], ref)
+        print("relative error vs oracle rows:", errs)
+        assert all(e < 1e-4 for e in errs.values()), errs
+    finally:
+        P.close()
+
+
+def test_sphere_printed_coupling(sphere):
+    """alpha = +i/k (the coupling as printed, with the normal into the body)."""
+    from paper_1403_4747_gb300 import FDAProblem, fda_set_precision
+    v, f, x, rows = sphere
+    ref = oracle.matvec(v, f, K, x, rows=rows, alpha_sign=1.0)
+    P = FDAProblem(v, f, K, precision=1, alpha_sign=1.0)
+    try:
+        xd = _dev(x)
+        e32 = _rel(P.apply(xd).cpu().numpy()[rows], ref)
+        fda_set_precision(P.h, 0)
+        e64 = _rel(P.apply(xd).cpu().numpy()[rows], ref)
+        print("alpha = +i/k: chosen %.3e plain %.3e" % (e32, e64))
+        assert e32 < 1e-4 and e64 < 1e-4
+    finally:
+        P.close()
+
+
+def test_ellipsoid_both_precisions():
+    from paper_1403_4747_gb300 import FDAProblem, fda_set_precision
+    v, f = ellipsoid_from_icosphere(7)
+    x = complex_normal(len(f), seed=1235)
+    rows = _rows(len(f))
+    ref = oracle.matvec(v, f, K, x, rows=rows)
+    P = FDAProblem(v, f, K, precision=1)
+    try:
+        xd = _dev(x)
+        e32 = _rel(P.apply(xd).cpu().numpy()[rows], ref)
+        fda_set_precision(P.h, 0)
+        e64 = _rel(P.apply(xd).cpu().numpy()[rows], ref)
+        print("ellipsoid: chosen %.3e plain %.3e" % (e32, e64))
+        assert e32 < 1e-4 and e64 < 1e-4
+    finally:
+        P.close()
+
+
+def test_solution_residual_against_oracle_and_mie(sphere):
+    from paper_1403_4747_gb300 import FDAProblem
+    v, f, _, rows = sphere
+    P = FDAProblem(v, f, K, precision=1)
+    try:
+        b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+        u, info = P.solve(b, 1e-4)
+        un, bn = u.cpu().numpy(), b.cpu().numpy()
+    finally:
+        P.close()
+    assert info.rel_resid_fp64 <= 1e-4
+    resid = _rel(oracle.matvec(v, f, K, un, rows=rows), bn[rows])
+    c = np.mean(v[f], axis=1)
+    ct = c[:, 2] / np.linalg.norm(c, axis=1)
+    mie = _rel(un, oracle.mie_surface_field(K, ct))
+    print("iterations %d, oracle residual on sampled rows %.3e, error vs Mie %.3e" % (info.iters, resid, mie))
+    assert resid < 3e-4
+    assert mie < 5e-2

@@ -151,6 +151,13 @@ def test_errors_are_reported():
     with pytest.raises(FDAError) as e:
         fda_build_tree(h, v, deg, 1.0)
     assert e.value.status == FDA_ERR_ARG
+    from paper_1403_4747_gb300 import fda_set_tc_tiles
+    for shape in ((16, 1, 2), (32, 4, 2), (64, 1, 5)):
+        with pytest.raises(FDAError) as e:
+            fda_set_tc_tiles(h, *shape)
+        assert e.value.status == FDA_ERR_ARG
+    fda_set_tc_tiles(h, 32, 3, 3)
+    fda_set_tc_tiles(h, 0, 0, 0)
     fda_destroy(h)
 
 
@@ -186,17 +193,18 @@ def test_blockdiag_is_exact_inverse_on_a_single_leaf():
     assert _rel(x.cpu().numpy(), u) < 1e-9
 
 
-def test_conjugate_coupling_parity():
-    """alpha = -i/k: the GPU matvec and right-hand side match the oracle with
-    the same coupling."""
+@pytest.mark.parametrize("alpha_sign", [1.0, -1.0])
+def test_coupling_parity(alpha_sign):
+    """alpha = +i/k (as printed) and -i/k (the default): the GPU matvec and
+    right-hand side match the oracle with the same coupling."""
     v, f = icosphere(4)
     k = 20.0
     x = complex_normal(len(f), seed=4)
-    P = _problem(v, f, k, alpha_sign=-1.0)
+    P = _problem(v, f, k, alpha_sign=alpha_sign)
     y = P.apply(_dev(x)).cpu().numpy()
-    assert _rel(y, oracle.matvec(v, f, k, x, alpha_sign=-1.0)) < 1e-4
+    assert _rel(y, oracle.matvec(v, f, k, x, alpha_sign=alpha_sign)) < 1e-4
     b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0])).cpu().numpy()
-    assert _rel(b, oracle.rhs_plane_wave(v, f, k, [[0.0, 0.0, 1.0]], alpha_sign=-1.0)[0]) < 1e-13
+    assert _rel(b, oracle.rhs_plane_wave(v, f, k, [[0.0, 0.0, 1.0]], alpha_sign=alpha_sign)[0]) < 1e-13
 
 
 @pytest.mark.parametrize("precision", [0, 1])

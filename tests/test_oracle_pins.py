@@ -120,7 +120,7 @@ def test_element_rules_against_brute_force(case):
     near = oracle.is_near_pair(v, f, i, j)
     assert near == (case != "far")
     k = 5.0
-    got = oracle.entry(v, f, k, i, j)
+    got = oracle.entry(v, f, k, i, j, alpha_sign=1.0)
     ref = _brute_triangle(c[i], n[i], v[f[j]], n[j], k)
     tol = 2e-4 if case != "far" else 1e-6
     assert abs(got - ref) < tol * abs(ref), (got, ref)
@@ -260,16 +260,18 @@ def test_mie_series_against_mpmath_and_rayleigh():
     assert np.allclose(u, 1 + 1.5j * ks * cts, atol=5e-6)
 
 
-def test_eigenvalues_consistent_with_mie():
-    """lambda_n (i/k^2)/h_n'(k) = j_n(k) - i j_n'(k): the operator's
-    eigenvalue applied to the Mie coefficient reproduces the plane-wave
-    right-hand side's expansion coefficient."""
+@pytest.mark.parametrize("alpha_sign", [1.0, -1.0])
+def test_eigenvalues_consistent_with_mie(alpha_sign):
+    """lambda_n (i/k^2)/h_n'(k) = j_n(k) - s i j_n'(k) for alpha = s i/k: the
+    operator's eigenvalue applied to the Mie coefficient reproduces the
+    plane-wave right-hand side's expansion coefficient (u_inc + alpha
+    du_inc/dn with n = -r on the unit sphere)."""
     from scipy import special
     for k in (0.5, 5.0, 25.0):
         for n in range(0, 12):
             hd = special.spherical_jn(n, k, True) + 1j * special.spherical_yn(n, k, True)
-            lhs = oracle.sphere_eigenvalue(n, k) * (1j / k ** 2) / hd
-            rhs = special.spherical_jn(n, k) - 1j * special.spherical_jn(n, k, True)
+            lhs = oracle.sphere_eigenvalue(n, k, alpha_sign) * (1j / k ** 2) / hd
+            rhs = special.spherical_jn(n, k) - alpha_sign * 1j * special.spherical_jn(n, k, True)
             assert abs(lhs - rhs) < 1e-10 * (abs(rhs) + 1e-30)
 
 

@@ -89,7 +89,7 @@ def test_rhs_self_entry_is_jump_plus_single_layer():
         g = np.exp(1j * k * R) / (4 * np.pi * R)
         dgdnx = -np.exp(1j * k * R) * (1 - 1j * k * R) * (r @ n[i]) / (4 * np.pi * R ** 3)
         ref += wq * area[j] * (g + (1j / k) * dgdnx)
-    assert abs(oracle.rhs_layers_entry(v, f, k, i, j) - ref) < 1e-13 * abs(ref)
+    assert abs(oracle.rhs_layers_entry(v, f, k, i, j, alpha_sign=1.0) - ref) < 1e-13 * abs(ref)
 
 
 def test_uniform_single_layer_potential_on_sphere():
@@ -200,7 +200,7 @@ def test_rhs_element_rules_against_brute_force(case):
     else:
         j = int(np.argmax(np.linalg.norm(c - c[i], axis=1)))
     k = 5.0
-    got = oracle.rhs_layers_entry(v, f, k, i, j)
+    got = oracle.rhs_layers_entry(v, f, k, i, j, alpha_sign=1.0)
     ref = _brute_single_layer(c[i], n[i], v[f[j]], k)
     tol = 1e-4 if case != "far" else 1e-6
     assert abs(got - ref) < tol * abs(ref), (got, ref)
