@@ -105,7 +105,7 @@ typedef struct {
     double rel_resid_fp64;  /* ||b - A x|| / ||b|| with the plain FP64 FDA operator */
     double setup_s;         /* wall time of build_tree + precompute_translations */
     double solve_s;         /* wall time of this solve */
-    double matvec_s;        /* mean wall time of one operator application inside the solve */
+    double matvec_s;        /* mean device time of one operator application inside the solve (CUDA events) */
 } fda_info;
 
 typedef struct {

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfdabem.so")
 SOURCES = ["sort.cu", "geometry.cu", "tree.cu", "quadrature.cu", "precompute.cu", "translate.cu", "translate_tc.cu",
-           "precond.cu", "sai.cu", "apply.cu", "gmres.cu", "api.cu", "batch.cu", "field.cu"]
+           "leaf_tc.cu", "precond.cu", "sai.cu", "apply.cu", "gmres.cu", "api.cu", "batch.cu", "field.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include"), "-diag-suppress", "20054"]
@@ -27,7 +27,8 @@ def _stale(obj, src):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "fda_internal.cuh"), os.path.join(ROOT, "include", "fda_bem.h")]
+    deps = [src, os.path.join(ROOT, "include", "fda_bem.h")]
+    deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -266,7 +266,13 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     mark(0);
     const int max_rows = h->max_leaf_rows;
     const size_t xs_bytes = sizeof(cx<R>) * (size_t)h->max_near_cols;
-    if (mr == 1 && xs_bytes <= 160 * 1024) {
+    // several right-hand sides in the chosen precision: the leaf products
+    // (near field, S2M, L2T) as tensor-core GEMMs with the right-hand sides as
+    // columns; one right-hand side stays on the CUDA cores (bandwidth-bound)
+    const bool leaf_tc = sizeof(R) == 4 && h->have_tc && h->cfg.tensor_cores && mr > 1 && !x64;
+    if (leaf_tc) {
+        fda_leaf_tc(h, 0, near, reinterpret_cast<const c32f *>(x), y, mr);
+    } else if (mr == 1 && xs_bytes <= 160 * 1024) {
         dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
         static bool attr = false;
         if (!attr) {
@@ -304,10 +310,14 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         FDA_CUDA(cudaMemsetAsync(q[l].p, 0, bytes, s));
         FDA_CUDA(cudaMemsetAsync(p[l].p, 0, bytes, s));
     }
-    k_s2m<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
-                               h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(),
-                               St.template as<cx<R>>(), x, x64, N, mr);
-    FDA_CHECK_LAUNCH();
+    if (leaf_tc) {
+        fda_leaf_tc(h, 1, St, reinterpret_cast<const c32f *>(x), y, mr);
+    } else {
+        k_s2m<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(),
+                                   h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
+                                   h->leaf_op_off.as<int64_t>(), St.template as<cx<R>>(), x, x64, N, mr);
+        FDA_CHECK_LAUNCH();
+    }
     mark(2);
     // tensor cores (chosen precision): every translation reads bf16 hi/lo
     // splits of its source level, made once that level is complete
@@ -348,10 +358,14 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         }
     }
     mark(5);
-    k_l2t<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
-                               h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(), ops.Tt.template as<cx<R>>(),
-                               y, N, mr);
-    FDA_CHECK_LAUNCH();
+    if (leaf_tc) {
+        fda_leaf_tc(h, 2, ops.Tt, nullptr, y, mr);
+    } else {
+        k_l2t<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(),
+                                   h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
+                                   h->leaf_op_off.as<int64_t>(), ops.Tt.template as<cx<R>>(), y, N, mr);
+        FDA_CHECK_LAUNCH();
+    }
     mark(6);
 }
 

@@ -251,6 +251,14 @@ struct fda_handle {
     dbuf tc_err;
     int have_tc = 0;
     int tc_force[3] = {0, 0, 0};  // tile shape forced by fda_set_tc_tiles (columns, row tiles, stages; 0 = auto)
+    // tile lists of the tensor-core leaf products (near field, S2M, L2T) per
+    // (kind, right-hand sides, columns per tile); kept because captured
+    // graphs point into them
+    struct leaf_tile_set {
+        int kind = 0, mr = 0, nc = 0, n = 0;
+        dbuf buf;
+    };
+    std::deque<leaf_tile_set> leaf_sets;
 
     // batched translations per level (M2L at l; M2M and L2L between l and l+1)
     tr_batch b_m2l[FDA_MAX_LEVELS], b_m2m[FDA_MAX_LEVELS], b_l2l[FDA_MAX_LEVELS];
@@ -343,6 +351,9 @@ void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr);
 // side), dst the FP32 densities of the target level (dstride elements each)
 void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t svstride, c32f *dst, int mr,
                 int64_t dstride, int nc = 0, int rows = 0, int st = 0);
+// leaf products on the tensor cores for mr right-hand sides (kind 0 near
+// field y = A x, 1 S2M into q32, 2 L2T y += T~ p32); A: FP32 operator of the side
+void fda_leaf_tc(fda_handle *h, int kind, const dbuf &A, const c32f *x, c64d *y, int mr);
 // time the tile shapes of every tensor-core batch once and keep the fastest
 void fda_autotune_tc(fda_handle *h);
 int fda_tc_error(fda_handle *h);

@@ -1,11 +1,16 @@
 // GMRES solve of Sec. 5 (no preconditioner, tolerance on the relative
 // residual of the unpreconditioned system).  Readings of what the paper
 // leaves open: restarted GMRES(m), zero or caller initial guess, classical
-// Gram-Schmidt with one re-orthogonalisation (CGS2).  The Krylov basis, the
-// operator and every vector operation live on the device in FP64; the small
-// Hessenberg least-squares problem (Givens rotations on an (m+1) x m matrix)
-// is updated on the host after each Arnoldi step, which is also where the
-// convergence test reads the residual estimate.
+// Gram-Schmidt with one re-orthogonalisation (CGS2).  Everything inside a
+// restart cycle stays on the device in FP64: the Krylov basis, the operator,
+// the Gram-Schmidt coefficients, the Hessenberg column, the Givens rotations
+// and the residual estimate |g_{j+1}| / ||r_0|| of the small least-squares
+// problem.  The host only enqueues each Arnoldi step and reads the estimate
+// of the step before (so the GPU always has the next step queued); once the
+// estimate predicts convergence within a step it reads every step's estimate
+// as soon as that step ends.  A restart cycle ends with one synchronisation:
+// the back substitution on the (at most 255 x 255) triangular system and the
+// true residual of the next cycle.
 //
 // Chosen precision: GMRES runs on the FP32 FDA operator, inside an outer
 // loop that re-evaluates the true residual b - A x with the FP64 operator
@@ -21,7 +26,7 @@
 namespace {
 
 constexpr int RT = 256;
-constexpr int RCH = 128;  // chunks per vector for the two-stage dot products
+constexpr int RCH = 1024;  // chunks per vector for the two-stage dot products (enough CTAs to reach HBM bandwidth)
 
 // partial[i * RCH + c] = sum over chunk c of conj(V_i[n]) w[n].  A CTA takes
 // one chunk of the index range and a group of DVG vectors: every thread
@@ -119,6 +124,77 @@ __global__ void __launch_bounds__(RT) k_combine(const c64d *V, int64_t ldv, int 
     w[t] = c64d(w[t].re + sign * acc.re, w[t].im + sign * acc.im);
 }
 
+// Device state of one Arnoldi step, copied to pinned host memory after the
+// step: the residual estimate, ||w|| after orthogonalisation, and flags
+// (bit 0: a non-finite Hessenberg entry, bit 1: breakdown, ||w|| tiny).
+struct gm_status {
+    double est, hn;
+    int flags, j;
+};
+
+// The small work of Arnoldi step j on one thread: the Hessenberg column
+// h = c1 + c2 (the two Gram-Schmidt passes) with h_{j+1} = ||w||, the
+// previous Givens rotations applied to it, the new rotation that zeroes
+// h_{j+1}, and the rotated right-hand side g of the least-squares problem.
+// H is column-major with leading dimension ldh; *scale receives 1/||w||.
+__global__ void k_arnoldi_step(int j, int ldh, const c64d *c1, const c64d *c2, const c64d *nrm2, c64d *H, c64d *cs,
+                               c64d *sn, c64d *g, double rnorm0, double beta, double *scale, gm_status *st)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    c64d *hc = H + (int64_t)j * ldh;
+    int bad = 0;
+    for (int i = 0; i <= j; ++i) {
+        const c64d v = c1[i] + c2[i];
+        hc[i] = v;
+        bad |= !isfinite(v.re) || !isfinite(v.im);
+    }
+    const double hn = sqrt(fmax(nrm2->re, 0.0));
+    bad |= !isfinite(hn);
+    *scale = hn > 0.0 ? 1.0 / hn : 1.0;
+    c64d hj1(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+        // (h_i, h_{i+1}) <- (c h_i + s h_{i+1}, -conj(s) h_i + conj(c) h_{i+1})
+        const c64d a = hc[i], b = hc[i + 1];
+        hc[i] = cs[i] * a + sn[i] * b;
+        hc[i + 1] = conjg(cs[i]) * b - conjg(sn[i]) * a;
+    }
+    const c64d hjj = hc[j];
+    const double den = sqrt(hjj.re * hjj.re + hjj.im * hjj.im + hj1.re * hj1.re + hj1.im * hj1.im);
+    c64d c(1.0, 0.0), s(0.0, 0.0);
+    if (den > 0.0) {
+        c = c64d(hjj.re / den, -hjj.im / den);
+        s = c64d(hj1.re / den, -hj1.im / den);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    hc[j] = c * hjj + s * hj1;
+    hc[j + 1] = c64d();
+    const c64d gj = g[j];
+    g[j + 1] = c64d() - conjg(s) * gj;
+    g[j] = c * gj;
+    const c64d gn = g[j + 1];
+    st->est = sqrt(gn.re * gn.re + gn.im * gn.im) / rnorm0;
+    st->hn = hn;
+    st->flags = (bad ? 1 : 0) | (hn <= 1e-14 * beta ? 2 : 0);
+    st->j = j;
+}
+
+__global__ void k_gmres_init(c64d *g, int n, double beta)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) g[t] = c64d(t == 0 ? beta : 0.0, 0.0);
+}
+
+// x *= *s (a scale the device computed)
+__global__ void k_scale_dev(c64d *x, const double *s, int64_t n)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) {
+        const double f = *s;
+        x[t] = c64d(x[t].re * f, x[t].im * f);
+    }
+}
+
 __global__ void k_axpby(const c64d *x, double a, const c64d *y, double b, c64d *out, int64_t n)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -137,29 +213,93 @@ struct solver {
     dbuf partial, hd;
     double matvec_time = 0;
     int nmatvec = 0;
+    // device state of the current restart cycle: Hessenberg columns (ldh =
+    // m + 1), Givens rotations, rotated right-hand side, Gram-Schmidt
+    // coefficients of the two passes, ||w||^2, 1/||w||, step status
+    dbuf Hd, csd, snd, gd, c1d, c2d, nrm2d, scaled, std_, yd;
+    gm_status *hst = nullptr;   // pinned: status of the last RING steps
+    c64d *hH = nullptr, *hg = nullptr, *hy = nullptr;  // pinned: H, g, y of a cycle
+    static constexpr int RING = 4;
+    cudaEvent_t sev[RING] = {};
+    // matvec timing: event pairs around each product, read back in batches
+    static constexpr int MVR = 64;
+    cudaEvent_t mv0[MVR] = {}, mv1[MVR] = {};
+    int mv_pending = 0;
+    int ldh = 0;
 
-    void dots(const c64d *V, int nv, const c64d *w, std::vector<std::complex<double>> &out)
+    ~solver()
+    {
+        for (int i = 0; i < RING; ++i)
+            if (sev[i]) cudaEventDestroy(sev[i]);
+        for (int i = 0; i < MVR; ++i) {
+            if (mv0[i]) cudaEventDestroy(mv0[i]);
+            if (mv1[i]) cudaEventDestroy(mv1[i]);
+        }
+        if (hst) cudaFreeHost(hst);
+        if (hH) cudaFreeHost(hH);
+        if (hg) cudaFreeHost(hg);
+        if (hy) cudaFreeHost(hy);
+    }
+
+    void setup(int m)
+    {
+        ldh = m + 1;
+        partial.alloc(sizeof(c64d) * RCH * (size_t)(m + 2));
+        hd.alloc(sizeof(c64d) * (size_t)(m + 2));
+        Hd.alloc(sizeof(c64d) * (size_t)ldh * m);
+        csd.alloc(sizeof(c64d) * m);
+        snd.alloc(sizeof(c64d) * m);
+        gd.alloc(sizeof(c64d) * (m + 1));
+        c1d.alloc(sizeof(c64d) * (m + 1));
+        c2d.alloc(sizeof(c64d) * (m + 1));
+        nrm2d.alloc(sizeof(c64d));
+        scaled.alloc(sizeof(double));
+        std_.alloc(sizeof(gm_status));
+        yd.alloc(sizeof(c64d) * (m + 1));
+        FDA_CUDA(cudaMallocHost(&hst, sizeof(gm_status) * RING));
+        FDA_CUDA(cudaMallocHost(&hH, sizeof(c64d) * (size_t)ldh * m));
+        FDA_CUDA(cudaMallocHost(&hg, sizeof(c64d) * (m + 1)));
+        FDA_CUDA(cudaMallocHost(&hy, sizeof(c64d) * (m + 1)));
+        for (int i = 0; i < RING; ++i) FDA_CUDA(cudaEventCreateWithFlags(&sev[i], cudaEventDisableTiming));
+        for (int i = 0; i < MVR; ++i) {
+            FDA_CUDA(cudaEventCreate(&mv0[i]));
+            FDA_CUDA(cudaEventCreate(&mv1[i]));
+        }
+    }
+
+    // out[0 .. nv) = V^H w on the device (two-stage reduction)
+    void dots_dev(const c64d *V, int nv, const c64d *w, c64d *out)
     {
         dim3 g(RCH, (nv + DVG - 1) / DVG);
         k_dots<<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>());
         FDA_CHECK_LAUNCH();
-        k_dots_finish<<<nv, RT, 0, h->stream>>>(partial.as<c64d>(), nv, hd.as<c64d>());
+        k_dots_finish<<<nv, RT, 0, h->stream>>>(partial.as<c64d>(), nv, out);
         FDA_CHECK_LAUNCH();
-        out.resize(nv);
-        FDA_CUDA(cudaMemcpyAsync(out.data(), hd.p, sizeof(c64d) * nv, cudaMemcpyDeviceToHost, h->stream));
-        FDA_CUDA(cudaStreamSynchronize(h->stream));
     }
+    // ||w|| on the host (synchronises; once per restart cycle)
     double norm(const c64d *w)
     {
-        std::vector<std::complex<double>> d;
-        dots(w, 1, w, d);
-        return sqrt(std::max(d[0].real(), 0.0));
+        dots_dev(w, 1, w, hd.as<c64d>());
+        c64d d;
+        FDA_CUDA(cudaMemcpyAsync(&d, hd.p, sizeof(c64d), cudaMemcpyDeviceToHost, h->stream));
+        FDA_CUDA(cudaStreamSynchronize(h->stream));
+        return sqrt(std::max(d.re, 0.0));
     }
-    void combine(const c64d *V, const std::vector<std::complex<double>> &c, double sign, c64d *w)
+    // w += sign * V c, coefficients c on the device
+    void combine_dev(const c64d *V, int nv, const c64d *c, double sign, c64d *w)
     {
-        FDA_CUDA(cudaMemcpyAsync(hd.p, c.data(), sizeof(c64d) * c.size(), cudaMemcpyHostToDevice, h->stream));
-        k_combine<<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, n, (int)c.size(), hd.as<c64d>(), sign, w, n);
+        k_combine<<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, n, nv, c, sign, w, n);
         FDA_CHECK_LAUNCH();
+    }
+    void collect_matvec_times()
+    {
+        for (int i = 0; i < mv_pending; ++i) {
+            float ms = 0.0f;
+            FDA_CUDA(cudaEventSynchronize(mv1[i]));
+            FDA_CUDA(cudaEventElapsedTime(&ms, mv0[i], mv1[i]));
+            matvec_time += 1e-3 * ms;
+        }
+        mv_pending = 0;
     }
     dbuf ptmp;
     // y = A M x when the preconditioner is on (right preconditioning), else A x
@@ -173,17 +313,48 @@ struct solver {
             apply(x, y, precision);
         }
     }
+    // stream-ordered product (no synchronisation); its device time is
+    // measured with an event pair
     void apply(const c64d *x, c64d *y, int precision)
     {
-        auto t0 = std::chrono::steady_clock::now();
+        if (mv_pending == MVR) collect_matvec_times();
+        FDA_CUDA(cudaEventRecord(mv0[mv_pending], h->stream));
         // through the handle's staging vectors, so every product replays the
         // same captured graph
         FDA_CUDA(cudaMemcpyAsync(h->xs.p, x, sizeof(c64d) * n, cudaMemcpyDeviceToDevice, h->stream));
         fda_apply_staged(h, precision, 1);
         FDA_CUDA(cudaMemcpyAsync(y, h->ys.p, sizeof(c64d) * n, cudaMemcpyDeviceToDevice, h->stream));
-        FDA_CUDA(cudaStreamSynchronize(h->stream));
-        matvec_time += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        FDA_CUDA(cudaEventRecord(mv1[mv_pending], h->stream));
+        ++mv_pending;
         ++nmatvec;
+    }
+
+    // one Arnoldi step j of the current cycle, enqueued without
+    // synchronisation; its status lands in hst[j % RING], signalled by sev[]
+    void arnoldi_step(c64d *V, int j, double rnorm0, double beta, int precision)
+    {
+        c64d *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
+        apply_op(vj, vn, precision);
+        dots_dev(V, j + 1, vn, c1d.as<c64d>());
+        combine_dev(V, j + 1, c1d.as<c64d>(), -1.0, vn);
+        dots_dev(V, j + 1, vn, c2d.as<c64d>());
+        combine_dev(V, j + 1, c2d.as<c64d>(), -1.0, vn);
+        dots_dev(vn, 1, vn, nrm2d.as<c64d>());
+        k_arnoldi_step<<<1, 32, 0, h->stream>>>(j, ldh, c1d.as<c64d>(), c2d.as<c64d>(), nrm2d.as<c64d>(),
+                                                Hd.as<c64d>(), csd.as<c64d>(), snd.as<c64d>(), gd.as<c64d>(),
+                                                rnorm0, beta, scaled.as<double>(), std_.as<gm_status>());
+        FDA_CHECK_LAUNCH();
+        k_scale_dev<<<fda_blocks(n, RT), RT, 0, h->stream>>>(vn, scaled.as<double>(), n);
+        FDA_CHECK_LAUNCH();
+        FDA_CUDA(cudaMemcpyAsync(hst + j % RING, std_.p, sizeof(gm_status), cudaMemcpyDeviceToHost, h->stream));
+        FDA_CUDA(cudaEventRecord(sev[j % RING], h->stream));
+    }
+    const gm_status &status(int j)
+    {
+        FDA_CUDA(cudaEventSynchronize(sev[j % RING]));
+        const gm_status &s = hst[j % RING];
+        if (s.flags & 1) fda_fail(FDA_ERR_NUMERIC, "non-finite Hessenberg entry in GMRES");
+        return s;
     }
 
     // GMRES(m) on A_prec: solve A d = r to ||r - A d|| <= tol_rel ||r||; d in/out
@@ -192,6 +363,7 @@ struct solver {
               bool d_zero = false)
     {
         const int m = std::max(1, h->cfg.restart);
+        if (ldh != m + 1) setup(m);
         dbuf Vb, w;
         Vb.alloc(sizeof(c64d) * (size_t)(m + 1) * n);
         w.alloc(sizeof(c64d) * n);
@@ -222,73 +394,69 @@ struct solver {
             if (it >= maxit) return 1;
             k_scale<<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, 1.0 / beta, n);
             FDA_CHECK_LAUNCH();
-            std::vector<std::complex<double>> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
-            g[0] = beta;
-            int j = 0;
-            for (; j < m && it < maxit; ++j, ++it) {
-                c64d *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
-                apply_op(vj, vn, precision);
-                std::vector<std::complex<double>> hcol(j + 2, 0.0), c;
-                for (int pass = 0; pass < 2; ++pass) {
-                    dots(V, j + 1, vn, c);
-                    for (int i = 0; i <= j; ++i) hcol[i] += c[i];
-                    combine(V, c, -1.0, vn);
-                }
-                double hn = norm(vn);
-                hcol[j + 1] = hn;
-                for (auto &v : hcol)
-                    if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
-                        fda_fail(FDA_ERR_NUMERIC, "non-finite Hessenberg entry in GMRES");
-                if (hn > 0) {
-                    k_scale<<<fda_blocks(n, RT), RT, 0, h->stream>>>(vn, 1.0 / hn, n);
-                    FDA_CHECK_LAUNCH();
-                }
-                for (int i = 0; i < j; ++i) {
-                    std::complex<double> t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
-                    hcol[i + 1] = -std::conj(sn[i]) * hcol[i] + std::conj(cs[i]) * hcol[i + 1];
-                    hcol[i] = t;
-                }
-                double den = std::sqrt(std::norm(hcol[j]) + std::norm(hcol[j + 1]));
-                if (den == 0.0) {
-                    cs[j] = 1.0;
-                    sn[j] = 0.0;
-                } else {
-                    cs[j] = std::conj(hcol[j]) / den;
-                    sn[j] = std::conj(hcol[j + 1]) / den;
-                }
-                hcol[j] = cs[j] * hcol[j] + sn[j] * hcol[j + 1];
-                hcol[j + 1] = 0.0;
-                g[j + 1] = -std::conj(sn[j]) * g[j];
-                g[j] = cs[j] * g[j];
-                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-                est = std::abs(g[j + 1]) / rnorm0;
+            k_gmres_init<<<1, 256, 0, h->stream>>>(gd.as<c64d>(), m + 1, beta);
+            FDA_CHECK_LAUNCH();
+            // Arnoldi steps: step j is enqueued before the host waits for the
+            // status of step j - 1, so the device always has work queued; once
+            // the estimates predict convergence at the next step, each step is
+            // waited for right after it is enqueued.
+            int jend = 0;          // columns of this cycle's least-squares problem
+            bool eager = false;    // wait for each step's own status
+            double e_prev = est, e_prev2 = est;
+            for (int j = 0; j < m && it < maxit; ++j) {
+                arnoldi_step(V, j, rnorm0, beta, precision);
+                ++it;
                 ++iters_out;
-                if (est <= tol_rel || hn <= 1e-14 * beta) {
-                    ++j;
-                    ++it;
+                jend = j + 1;
+                const int jc = eager ? j : j - 1;  // step whose status is read now
+                if (jc < 0) continue;
+                const gm_status &s = status(jc);
+                const bool done = s.est <= tol_rel || (s.flags & 2);
+                if (done) {
+                    est = s.est;
+                    if (jc < j) {  // step j was enqueued past convergence: not used
+                        --it;
+                        --iters_out;
+                        jend = j;
+                    }
                     break;
                 }
+                est = s.est;
+                e_prev2 = e_prev;
+                e_prev = s.est;
+                // predicted estimate one step on, at the last step's rate
+                const double rate = e_prev2 > 0.0 ? std::min(1.0, e_prev / e_prev2) : 1.0;
+                if (!eager && e_prev * rate * rate <= 2.0 * tol_rel) eager = true;
             }
-            // back substitution H y = g, d += V y
+            // the cycle's last status (when the loop ended at m or maxit)
+            if (jend > 0) {
+                const gm_status &s = status(jend - 1);
+                est = s.est;
+            }
+            // back substitution H y = g on the host, then d += V y (or M V y)
+            const int j = jend;
+            FDA_CUDA(cudaMemcpyAsync(hH, Hd.p, sizeof(c64d) * (size_t)ldh * j, cudaMemcpyDeviceToHost, h->stream));
+            FDA_CUDA(cudaMemcpyAsync(hg, gd.p, sizeof(c64d) * j, cudaMemcpyDeviceToHost, h->stream));
+            FDA_CUDA(cudaStreamSynchronize(h->stream));
             std::vector<std::complex<double>> y(j, 0.0);
+            auto Hij = [&](int i, int k) { return std::complex<double>(hH[(size_t)k * ldh + i].re, hH[(size_t)k * ldh + i].im); };
             for (int i = j - 1; i >= 0; --i) {
-                std::complex<double> s = g[i];
-                for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
-                y[i] = s / H[(size_t)i * m + i];
+                std::complex<double> s(hg[i].re, hg[i].im);
+                for (int k = i + 1; k < j; ++k) s -= Hij(i, k) * y[k];
+                y[i] = s / Hij(i, i);
+                hy[i] = c64d(y[i].real(), y[i].imag());
             }
+            FDA_CUDA(cudaMemcpyAsync(yd.p, hy, sizeof(c64d) * j, cudaMemcpyHostToDevice, h->stream));
             if (h->cfg.precond != 0) {
                 // d += M (V y): form V y in w, then apply M into the basis slot V_m (free now)
                 FDA_CUDA(cudaMemsetAsync(w.p, 0, sizeof(c64d) * n, h->stream));
-                combine(V, y, 1.0, w.as<c64d>());
+                combine_dev(V, j, yd.as<c64d>(), 1.0, w.as<c64d>());
                 c64d *tmp = V + (int64_t)m * n;
                 fda_precond_apply(h, w.as<c64d>(), tmp);
-                std::vector<std::complex<double>> one(1, 1.0);
-                combine(tmp, one, 1.0, d);
+                k_axpby<<<fda_blocks(n, RT), RT, 0, h->stream>>>(d, 1.0, tmp, 1.0, d, n);
+                FDA_CHECK_LAUNCH();
             } else {
-                combine(V, y, 1.0, d);
-            }
-            if (it >= maxit && est > tol_rel) {
-                // one last true-residual check happens at the top of the loop
+                combine_dev(V, j, yd.as<c64d>(), 1.0, d);
             }
         }
         return 0;
@@ -316,8 +484,7 @@ fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda
     solver S;
     S.h = h;
     S.n = n;
-    S.partial.alloc(sizeof(c64d) * RCH * (size_t)(h->cfg.restart + 2));
-    S.hd.alloc(sizeof(c64d) * (size_t)(h->cfg.restart + 2));
+    S.setup(std::max(1, h->cfg.restart));
     dbuf bs, xs, r, d, ax;
     bs.alloc(sizeof(c64d) * n);
     xs.alloc(sizeof(c64d) * n);
@@ -384,6 +551,7 @@ fda_status fda_solve_impl(fda_handle *h, const c64d *b, c64d *x, double tol, fda
     }
     fda_scatter_from_sorted(h, xs.as<c64d>(), x);
     FDA_CUDA(cudaStreamSynchronize(h->stream));
+    S.collect_matvec_times();
     if (!(rel <= tol)) st = FDA_ERR_NOT_CONVERGED;
     if (!std::isfinite(rel)) st = FDA_ERR_NUMERIC;
     if (info) {

@@ -273,3 +273,25 @@ def test_graph_replay_matches_eager_launches():
     xe, ie = E.solve(b, 1e-6)
     assert abs(ig.iters - ie.iters) <= 2
     assert _rel(xg.cpu().numpy(), xe.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [2, 20, 40, 64])
+def test_leaf_products_on_tensor_cores(nrhs):
+    """Several right-hand sides in the chosen precision: the near field, S2M
+    and L2T run as tcgen05 GEMMs with the right-hand sides as columns (16, 32
+    or 64 per tile; 40 leaves a partial group).  They agree with the CUDA-core
+    path (tensor cores off) to the split-bf16 accuracy, and a column agrees
+    with the oracle to the FDA tolerance."""
+    from paper_1403_4747_gb300 import fda_set_tensor_cores
+    v, f = icosphere(4)
+    k = 20.0
+    x = complex_normal(len(f), seed=51, nrhs=nrhs)
+    P = _problem(v, f, k, precision=1, max_rhs=nrhs)
+    xd = _dev(x)
+    y_tc = P.apply(xd).cpu().numpy()
+    fda_set_tensor_cores(P.h, 0)
+    y_simt = P.apply(xd).cpu().numpy()
+    assert np.all(np.isfinite(y_tc))
+    assert _rel(y_tc, y_simt) < 2e-5
+    m = nrhs - 1
+    assert _rel(y_tc[m], oracle.matvec(v, f, k, x[m])) < 1e-4
