@@ -286,6 +286,46 @@ def run_native(args):
     pt64 = pass_times(1)
     F.fda_set_precision(P.h, F.FDA_CHOSEN_FP32)
 
+    # the same workload with every reduced M2L operator applied in full
+    # (Sec. 4.2's low-rank step off), for comparison
+    lowrank_off = None
+    if not args.no_lowrank_off:
+        t0 = time.perf_counter()
+        Q = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps, lowrank=0,
+                         max_rhs=1)
+        torch.cuda.synchronize()
+        setup_off = time.perf_counter() - t0
+        for _ in range(3):
+            Q.apply(x, y)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(20):
+            Q.apply(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        off_ms = e0.elapsed_time(e1) / 20
+        F.fda_set_timing(Q.h, True)
+        acc = np.zeros(6)
+        for _ in range(5):
+            Q.apply(x, y)
+            acc += np.array(F.fda_get_pass_times(Q.h))
+        F.fda_set_timing(Q.h, False)
+        F.fda_set_precision(Q.h, F.FDA_PLAIN_FP64)
+        Q.apply(x, y)
+        torch.cuda.synchronize()
+        tq = time.perf_counter()
+        for _ in range(max(1, args.plain_steps)):
+            Q.apply(x, y)
+        torch.cuda.synchronize()
+        off_plain_ms = (time.perf_counter() - tq) / max(1, args.plain_steps) * 1e3
+        lowrank_off = {"ms_per_matvec": off_ms, "matvec_per_s": 1e3 / off_ms, "setup_s": setup_off,
+                       "chosen_pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], (acc / 5).tolist())),
+                       "m2l_bytes": _m2l_bytes(Q), "m2l_flops": _m2l_flops(Q),
+                       "plain_fp64_ms_per_matvec": off_plain_ms}
+        Q.close()
+        del Q
+        torch.cuda.empty_cache()
+
     # many right-hand sides per pass (incidence directions): every operator
     # read serves all of them
     batched = None
@@ -457,12 +497,19 @@ def run_native(args):
             "err_vs_oracle": err,
             "near_field_roofline": near_roof,
             "batched_rhs": batched,
+            "lowrank_off": lowrank_off,
             "solve": solve,
             "tree": {"levels": nlev, "boxes": st.n_boxes, "leaves": st.n_leaves, "nnz_near": st.nnz_near,
                      "m2l_pairs": st.n_m2l, "m2l_ops": st.n_m2l_ops,
                      "rank_per_level": [st.level_rank[l] for l in range(nlev)],
                      "regime_per_level": [st.level_regime[l] for l in range(nlev)],
                      "cones_per_level": [st.level_cones[l] for l in range(nlev)],
+                     "m2l_pairs_per_level": [st.level_m2l_pairs[l] for l in range(nlev)],
+                     "m2l_ops_per_level": [st.level_m2l_ops[l] for l in range(nlev)],
+                     "lowrank_ops_per_level": [st.level_lr_ops[l] for l in range(nlev)],
+                     "lowrank_pairs_per_level": [st.level_lr_pairs[l] for l in range(nlev)],
+                     "lowrank_rank_mean_per_level": [round(st.level_lr_rank_mean[l], 1) for l in range(nlev)],
+                     "lowrank_rank_max_per_level": [st.level_lr_rank_max[l] for l in range(nlev)],
                      "device_gb": st.device_bytes / 1e9}}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -490,25 +537,21 @@ def _m2l_traffic(args):
 
 
 def _m2l_bytes(P):
-    """Algorithmic bytes of the M2L pass per apply: distinct operators once
-    (8 bytes per complex entry), source densities read once, target
-    densities read and written once (8 bytes per complex value)."""
+    """Algorithmic bytes of the M2L pass per apply, as the library counts
+    them from its batches: every operator applied read once (8 bytes per
+    complex entry: T^2 in full form, 2 r T in the low-rank form of Sec. 4.2
+    with the operator's own rank r), source densities read once, target
+    densities read and written once, each low-rank pair's intermediate
+    written and read once."""
     st = P.stats()
-    total = 0
-    for l in range(st.n_levels):
-        T = st.level_rank[l]
-        if T == 0 or st.level_m2l_pairs[l] == 0:
-            continue
-        total += 8 * st.level_m2l_ops[l] * T * T
-        total += 3 * 8 * st.level_boxes[l] * st.level_cones[l] * T
-    return int(total)
+    return int(sum(st.level_m2l_bytes[l] for l in range(st.n_levels)))
 
 
 def _m2l_flops(P):
-    """Real flops of the M2L pass per apply: 8 T_l^2 per interaction pair
-    (one complex multiply-add is 8 real flops)."""
+    """Real flops of the M2L pass per apply that the method performs: 8 T^2
+    per pair in full form, 8 (2 r T) per pair in low-rank form."""
     st = P.stats()
-    return int(sum(8.0 * st.level_rank[l] ** 2 * st.level_m2l_pairs[l] for l in range(st.n_levels)))
+    return int(sum(st.level_m2l_flops[l] for l in range(st.n_levels)))
 
 
 def run_many_meshes(args):
@@ -919,6 +962,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-plain-unpreconditioned", action="store_true")
     ap.add_argument("--no-alt-coupling", action="store_true")
+    ap.add_argument("--no-lowrank-off", action="store_true",
+                    help="skip the comparison run with the low-rank M2L step (Sec. 4.2) off")
     ap.add_argument("--alt-plain", action="store_true",
                     help="also solve the alpha = +i/k problem with the plain FP64 form (about a minute)")
     ap.add_argument("--blockdiag", action="store_true", help="also solve with the block-diagonal preconditioner")

@@ -97,6 +97,10 @@ typedef struct {
                               as one text line "key columns row_tiles stages" each.  A missing file is
                               created; an unreadable or unwritable one only disables the cache.  The
                               string is read during fda_precompute_translations only. */
+    int lowrank;           /* 1 (default): Sec. 4.2, each reduced M2L operator K~ (T x T) is factorised as
+                              U^ V^ (T x r, r x T) truncated at eps times its largest singular value (Eq. epsk,
+                              error measured in the Frobenius norm) and applied as two products where that is
+                              cheaper; 0: every K~ applied in full */
 } fda_config;
 
 typedef struct {
@@ -128,6 +132,18 @@ typedef struct {
     int32_t graph_fallback;       /* 1 if a capture failed and the handle launches kernels one by one */
     int32_t autotune_cached;      /* tensor-core batches whose tile shape came from the autotune cache */
     int32_t autotune_timed;       /* tensor-core batches timed by the autotuner at setup */
+    int32_t level_lr_ops[32];     /* per level: M2L operators applied in low-rank form (Sec. 4.2) */
+    int32_t level_lr_rank_max[32];   /* per level: largest retained rank r of those operators */
+    float level_lr_rank_mean[32];    /* per level: mean retained rank r of every operator factorised */
+    int64_t level_lr_pairs[32];   /* per level: M2L pairs applied in low-rank form */
+    double level_m2l_flops[32];   /* per level: real flops of the M2L pass for one right-hand side, as the
+                                     method performs them (8 T^2 per pair in full form, 8 (2 r T) per pair
+                                     in low-rank form with the operator's own rank r) */
+    double level_m2l_bytes[32];   /* per level: algorithmic bytes of the M2L pass for one right-hand side in
+                                     the chosen precision: every operator applied read once (8 bytes per
+                                     complex entry; T^2, or 2 r T in low-rank form), source densities read
+                                     once, target densities read and written once, and each low-rank pair's
+                                     intermediate written and read once */
 } fda_stats;
 
 typedef struct fda_handle fda_handle;
@@ -261,6 +277,27 @@ fda_status fda_set_precision(fda_handle *h, int precision);
 /* Switch the tensor-core M2L of the chosen precision on (1) or off (0) for
  * later calls (needs a handle created with tensor_cores = 1 to turn on). */
 fda_status fda_set_tensor_cores(fda_handle *h, int on);
+
+/* The octree and lists of Sec. 3.3 Step 1 as built on the device, copied to
+ * the host for checking them against an independent construction (no
+ * counterpart in the paper's interface).  fda_tree_sizes fills sizes[0] =
+ * boxes over all levels, sizes[1] = leaves, sizes[2] = interaction-list
+ * entries, sizes[3] = near-field columns over all leaves.  fda_get_tree
+ * copies (host arrays, caller-owned, sized from fda_tree_sizes; any may be
+ * NULL to skip it; synchronises the stream):
+ *   box_level[nbox], box_coord[nbox][3] (integer cube coordinates at the
+ *   box's level: the cube is root_lo + w_l [c, c + 1)), box_leaf[nbox] (0/1),
+ *   box_parent[nbox] (-1 for the root), box_begin[nbox] / box_end[nbox] (the
+ *   box's elements as a range of Morton positions), perm[nt] (Morton
+ *   position -> caller's triangle index), il_ptr[nbox + 1] / il_src[n_il]
+ *   (each box's M2L interaction list: source boxes of its level),
+ *   leaf_box[nleaf] (box of each leaf), nf_colptr[nleaf + 1] / nf_cols[ncols]
+ *   (each leaf's near-field columns as Morton positions).
+ * Boxes are numbered level by level.  FDA_ERR_STATE before fda_build_tree. */
+fda_status fda_tree_sizes(fda_handle *h, int64_t *sizes);
+fda_status fda_get_tree(fda_handle *h, int32_t *box_level, int32_t *box_coord, int32_t *box_leaf,
+                        int32_t *box_parent, int32_t *box_begin, int32_t *box_end, int32_t *perm, int64_t *il_ptr,
+                        int32_t *il_src, int32_t *leaf_box, int64_t *nf_colptr, int32_t *nf_cols);
 
 /* Force the tile shape of every tensor-core translation launch (Sec. 3.3
  * Steps 2-3 on the tensor cores) for later calls, in place of the

@@ -27,7 +27,7 @@ class fda_config(ctypes.Structure):
                 ("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("precond", ctypes.c_int),
                 ("alpha_sign", ctypes.c_double), ("max_rhs", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p)]
+                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p), ("lowrank", ctypes.c_int)]
 
 
 class fda_info(ctypes.Structure):
@@ -46,7 +46,10 @@ class fda_stats(ctypes.Structure):
                 ("level_m2l_pairs", ctypes.c_int64 * 32),
                 ("level_m2l_ops", ctypes.c_int32 * 32), ("graph_replays", ctypes.c_int64),
                 ("graph_fallback", ctypes.c_int32), ("autotune_cached", ctypes.c_int32),
-                ("autotune_timed", ctypes.c_int32)]
+                ("autotune_timed", ctypes.c_int32), ("level_lr_ops", ctypes.c_int32 * 32),
+                ("level_lr_rank_max", ctypes.c_int32 * 32), ("level_lr_rank_mean", ctypes.c_float * 32),
+                ("level_lr_pairs", ctypes.c_int64 * 32), ("level_m2l_flops", ctypes.c_double * 32),
+                ("level_m2l_bytes", ctypes.c_double * 32)]
 
 
 class fda_sai_config(ctypes.Structure):
@@ -96,6 +99,8 @@ def load(path: str = LIB_PATH):
     lib.fda_set_precond.argtypes = [H, cint]
     lib.fda_set_tensor_cores.argtypes = [H, cint]
     lib.fda_set_tc_tiles.argtypes = [H, cint, cint, cint]
+    lib.fda_tree_sizes.argtypes = [H, vp]
+    lib.fda_get_tree.argtypes = [H] + [vp] * 12
     lib.fda_get_pass_times.argtypes = [H, ctypes.POINTER(ctypes.c_float)]
     lib.fda_cone_symmetry_table.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.fda_cone_symmetry_table.restype = ctypes.c_int
@@ -132,7 +137,8 @@ def load(path: str = LIB_PATH):
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
                  "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_far_field", "fda_scattered_field", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
-                 "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores", "fda_set_tc_tiles"):
+                 "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores", "fda_set_tc_tiles",
+                 "fda_tree_sizes", "fda_get_tree"):
         getattr(lib, name).restype = cint
     _lib = lib
     return lib
@@ -249,6 +255,28 @@ def fda_set_precond(h, precond):
 
 def fda_set_tensor_cores(h, on):
     _check(h, load().fda_set_tensor_cores(h, 1 if on else 0))
+
+
+def fda_get_tree(h):
+    """Host copies of the device octree and lists (dict of numpy arrays)."""
+    import numpy as np
+    sz = np.zeros(4, dtype=np.int64)
+    _check(h, load().fda_tree_sizes(h, sz.ctypes.data))
+    nb, nl, nil, ncol = (int(v) for v in sz)
+    st = fda_get_stats(h)
+    n = int(st.n_elements)
+    out = {"box_level": np.zeros(nb, np.int32), "box_coord": np.zeros((nb, 3), np.int32),
+           "box_leaf": np.zeros(nb, np.int32), "box_parent": np.zeros(nb, np.int32),
+           "box_begin": np.zeros(nb, np.int32), "box_end": np.zeros(nb, np.int32), "perm": np.zeros(n, np.int32),
+           "il_ptr": np.zeros(nb + 1, np.int64), "il_src": np.zeros(max(nil, 1), np.int32),
+           "leaf_box": np.zeros(nl, np.int32), "nf_colptr": np.zeros(nl + 1, np.int64),
+           "nf_cols": np.zeros(max(ncol, 1), np.int32)}
+    order = ["box_level", "box_coord", "box_leaf", "box_parent", "box_begin", "box_end", "perm", "il_ptr", "il_src",
+             "leaf_box", "nf_colptr", "nf_cols"]
+    _check(h, load().fda_get_tree(h, *[out[k].ctypes.data for k in order]))
+    out["il_src"] = out["il_src"][:nil]
+    out["nf_cols"] = out["nf_cols"][:ncol]
+    return out
 
 
 def fda_set_tc_tiles(h, columns=0, row_tiles=0, stages=0):

@@ -125,6 +125,7 @@ void fda_default_config(fda_config *c)
     c->graphs = 1;
     c->autotune = 1;
     c->autotune_cache = nullptr;
+    c->lowrank = 1;
 }
 
 fda_status fda_create(const fda_config *cfg, fda_handle **out)
@@ -138,7 +139,7 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
         (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
         (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.restart > 255 || c.maxit < 1 || c.precond < 0 ||
         c.precond > 1 || (c.graphs != 0 && c.graphs != 1) || (c.autotune != 0 && c.autotune != 1) || (c.alpha_sign != 1.0 && c.alpha_sign != -1.0) || c.max_rhs < 1 || c.max_rhs > 256 ||
-        c.tensor_cores < 0 || c.tensor_cores > 1)
+        c.tensor_cores < 0 || c.tensor_cores > 1 || c.lowrank < 0 || c.lowrank > 1)
         return FDA_ERR_ARG;
     fda_handle *h = new (std::nothrow) fda_handle();
     if (!h) return FDA_ERR_OOM;
@@ -468,6 +469,51 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
         out->graph_fallback = h->graphs_broken;
         out->autotune_cached = h->autotune_cached;
         out->autotune_timed = h->autotune_timed;
+        for (int l = 0; l < h->nlev && l < 32; ++l) {
+            const level_info &L = h->lev[l];
+            const std::vector<int> &rk = h->op_rank[l];
+            const std::vector<int> &bk = h->op_bucket[l];
+            double rsum = 0.0;
+            int rcnt = 0, rmax = 0, nlr = 0;
+            for (size_t o = 0; o < rk.size(); ++o) {
+                if (rk[o] >= 0) {
+                    rsum += rk[o];
+                    ++rcnt;
+                }
+                if (o < bk.size() && bk[o] >= 0) {
+                    ++nlr;
+                    rmax = std::max(rmax, rk[o]);
+                }
+            }
+            out->level_lr_ops[l] = nlr;
+            out->level_lr_rank_max[l] = rmax;
+            out->level_lr_rank_mean[l] = rcnt ? (float)(rsum / rcnt) : 0.0f;
+            int64_t lrp = 0;
+            for (const lr_bucket &B : h->lr[l]) lrp += B.npairs;
+            out->level_lr_pairs[l] = lrp;
+            // algorithmic work of the level's M2L pass, one right-hand side
+            const double T = L.T;
+            if (T == 0 || L.n_il == 0) continue;
+            const tr_batch &F = h->b_m2l[l];
+            double fl = 0.0, by = 0.0;
+            for (int o = 0; o + 1 < (int)F.op_start.size(); ++o) {
+                const int np = F.op_start[o + 1] - F.op_start[o];
+                if (np == 0) continue;
+                fl += 8.0 * T * T * np;
+                by += 8.0 * T * T;
+            }
+            for (const lr_bucket &B : h->lr[l]) {
+                for (size_t i = 0; i < B.ops.size(); ++i) {
+                    const double r = rk[B.ops[i]];
+                    const int np = B.b1.op_start[i + 1] - B.b1.op_start[i];
+                    fl += 8.0 * 2.0 * r * T * np;
+                    by += 8.0 * 2.0 * r * T + 2.0 * 8.0 * r * np;
+                }
+            }
+            by += 3.0 * 8.0 * L.nbox * L.ncones * T;
+            out->level_m2l_flops[l] = fl;
+            out->level_m2l_bytes[l] = by;
+        }
         int rb = h->cfg.precision == FDA_CHOSEN_FP32 ? 8 : 16;
         out->bytes_near = h->nnz_near * rb;
         // far-field flop count (real flops, 8 per complex multiply-add)
@@ -542,6 +588,50 @@ fda_status fda_set_tensor_cores(fda_handle *h, int on)
     }
     h->cfg.tensor_cores = on;
     return FDA_OK;
+}
+
+fda_status fda_tree_sizes(fda_handle *h, int64_t *sizes)
+{
+    if (!h || !sizes) return FDA_ERR_ARG;
+    if (h->state < 1) {
+        h->err = "fda_tree_sizes before fda_build_tree";
+        return FDA_ERR_STATE;
+    }
+    sizes[0] = h->nbox_total;
+    sizes[1] = h->nleaf;
+    sizes[2] = h->n_il_total;
+    sizes[3] = h->ncols_total;
+    return FDA_OK;
+}
+
+fda_status fda_get_tree(fda_handle *h, int32_t *box_level, int32_t *box_coord, int32_t *box_leaf,
+                        int32_t *box_parent, int32_t *box_begin, int32_t *box_end, int32_t *perm, int64_t *il_ptr,
+                        int32_t *il_src, int32_t *leaf_box, int64_t *nf_colptr, int32_t *nf_cols)
+{
+    if (!h) return FDA_ERR_ARG;
+    if (h->state < 1) {
+        h->err = "fda_get_tree before fda_build_tree";
+        return FDA_ERR_STATE;
+    }
+    return guarded(h, [&] {
+        const size_t nb = (size_t)h->nbox_total, nl = (size_t)h->nleaf;
+        auto cp = [&](void *dst, const dbuf &src, size_t bytes) {
+            if (dst && bytes) FDA_CUDA(cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDeviceToHost, h->stream));
+        };
+        cp(box_level, h->box_level, 4 * nb);
+        cp(box_coord, h->box_coord, 12 * nb);
+        cp(box_leaf, h->box_leaf, 4 * nb);
+        cp(box_parent, h->box_parent, 4 * nb);
+        cp(box_begin, h->box_begin, 4 * nb);
+        cp(box_end, h->box_end, 4 * nb);
+        cp(perm, h->perm, 4 * (size_t)h->N);
+        cp(il_ptr, h->il_ptr, 8 * (nb + 1));
+        cp(il_src, h->il_src, 4 * (size_t)h->n_il_total);
+        cp(leaf_box, h->leaf_box, 4 * nl);
+        cp(nf_colptr, h->nf_colptr, 8 * (nl + 1));
+        cp(nf_cols, h->nf_cols, 4 * (size_t)h->ncols_total);
+        FDA_CUDA(cudaStreamSynchronize(h->stream));
+    });
 }
 
 fda_status fda_set_tc_tiles(fda_handle *h, int columns, int row_tiles, int stages)

@@ -11,6 +11,7 @@
 // per box and cone; p~ = U_dn^H p).  Every pass is templated on the real
 // type: double (plain FP64 form) or float (chosen form: FP32 operators and
 // densities, FP32 accumulation, the result added into the FP64 output).
+#include <cuda_bf16.h>
 #include <stdio.h>
 
 #include <algorithm>
@@ -248,6 +249,35 @@ lvl_ptrs<R> make_ptrs(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p)
     return P;
 }
 
+// M2L of the low-rank operators of one rank bucket at level l (Sec. 4.2):
+// t_p = V^ q~_C for every pair p, then p~_D += U^ t_p.  The intermediates
+// were allocated for max_rhs right-hand sides at setup (never reallocated:
+// captured graphs hold their addresses).
+template <typename R>
+void lowrank_m2l(fda_handle *h, lr_bucket &B, int l, const lvl_ptrs<R> &P, int mr, bool tc)
+{
+    if (B.npairs == 0) return;
+    cudaStream_t s = h->stream;
+    const int T = h->lev[l].T;
+    const int64_t per = B.npairs * B.rpad;  // intermediate values per right-hand side
+    dbuf &t = sizeof(R) == 8 ? B.t64 : B.t32;
+    const size_t need = sizeof(cx<R>) * (size_t)per * mr;
+    if (t.bytes < need) fda_fail(FDA_ERR_STATE, "low-rank intermediate smaller than max_rhs columns");
+    FDA_CUDA(cudaMemsetAsync(t.p, 0, need, s));
+    if (tc) {
+        const size_t sneed = sizeof(__nv_bfloat16) * (size_t)B.npairs * mr * 4 * ((B.rpad + 31) / 32 * 32);
+        if (B.ts.bytes < sneed) fda_fail(FDA_ERR_STATE, "low-rank split buffer smaller than max_rhs columns");
+        fda_run_tc(h, B.b1, B.tc1, h->qs[l], P.stride[l] / std::max(1, T), t.as<c32f>(), mr, per);
+        fda_split_vectors(h, t.as<c32f>(), B.npairs * mr, B.rpad, B.ts);
+        fda_run_tc(h, B.b2, B.tc2, B.ts, B.npairs, reinterpret_cast<c32f *>(P.p[l]), mr, P.stride[l]);
+    } else {
+        const dbuf &V = sizeof(R) == 8 ? B.V64 : B.V32;
+        const dbuf &U = sizeof(R) == 8 ? B.U64 : B.U32;
+        fda_run_batch<R>(B.b1, V.as<cx<R>>(), B.rpad, T, P.q[l], t.as<cx<R>>(), mr, P.stride[l], per, s);
+        fda_run_batch<R>(B.b2, U.as<cx<R>>(), T, B.rpad, t.as<cx<R>>(), P.p[l], mr, per, P.stride[l], s);
+    }
+}
+
 // side 0: the Burton-Miller operator of Eq. eq_sum applied to u; side 1: the
 // right-hand side's layers of Eq. eq_bm applied to q = du/dn (its own near
 // field and single-layer S2M; every translation and the L2T are shared)
@@ -344,6 +374,7 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         else
             fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
                              P.stride[l], s);
+        for (lr_bucket &B : h->lr[l]) lowrank_m2l<R>(h, B, l, P, mr, tc);
     }
     mark(4);
     // L2L top-down: p~_child += L~ p~_parent
@@ -499,6 +530,14 @@ void fda_autotune_tc(fda_handle *h)
     for (int l = h->lev_lo; l < h->nlev; ++l) {
         if (h->lev[l].T == 0) continue;
         tune("m2l", l, h->b_m2l[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<float *>(P.p[l]), P.stride[l]);
+        for (lr_bucket &B : h->lr[l]) {
+            if (B.npairs == 0) continue;
+            const int64_t per = B.npairs * B.rpad;
+            if (B.t32.bytes < sizeof(c32f) * (size_t)per || B.ts.bytes < 8 * (size_t)per)
+                fda_fail(FDA_ERR_STATE, "low-rank intermediates missing at autotune");
+            tune("lr1", l, B.b1, B.tc1, h->qs[l], sv(l), reinterpret_cast<float *>(B.t32.p), per);
+            tune("lr2", l, B.b2, B.tc2, B.ts, B.npairs, reinterpret_cast<float *>(P.p[l]), P.stride[l]);
+        }
         if (l + 1 < h->nlev && h->lev[l + 1].T > 0) {
             tune("m2m", l, h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], sv(l + 1), reinterpret_cast<float *>(P.q[l]),
                  P.stride[l]);

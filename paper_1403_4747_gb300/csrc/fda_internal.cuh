@@ -163,6 +163,20 @@ struct tc_ops {
     int nc_tuned = 0, r_tuned = 1, st_tuned = 0;  // autotuner's choice for one right-hand side (0 = rule)
 };
 
+// Low-rank reduced M2L operators of one level and rank bucket (Sec. 4.2):
+// K~_o ~= U^_o V^_o with U^ (T x r) and V^ (r x T), zero-padded to the
+// bucket's rank rpad, applied in two stages: t_p = V^_o q~_C into one
+// intermediate vector per pair, then p~_D += U^_o t_p.
+struct lr_bucket {
+    int rpad = 0;
+    std::vector<int> ops;       // operator indices of the level in this bucket
+    dbuf U64, V64, U32, V32;    // [n][T x rpad] and [n][rpad x T], column-major
+    tr_batch b1, b2;            // stage 1 (q~ -> t) and stage 2 (t -> p~) pairs, grouped by bucket operator
+    tc_ops tc1, tc2;            // tensor-core panels of V^ and U^
+    dbuf t64, t32, ts;          // intermediates [mr][pairs][rpad] (FP64, FP32) and the FP32 split into bf16
+    int64_t npairs = 0;
+};
+
 template <typename T>
 struct far_ops {
     // per level (index = level)
@@ -244,6 +258,12 @@ struct fda_handle {
     int rhs_layers = 0;  // near field and S2M of the right-hand side's layers built
     int autotune_cached = 0, autotune_timed = 0;  // tensor-core batches from the cache / timed at setup
     std::string autotune_cache;                   // cfg.autotune_cache copied at fda_create ("" = none)
+
+    // low-rank M2L (Sec. 4.2): per level the retained rank of every operator
+    // (T: applied in full) and the rank buckets of the low-rank ones
+    std::vector<int> op_rank[FDA_MAX_LEVELS];
+    std::vector<int> op_bucket[FDA_MAX_LEVELS];  // bucket of each operator, -1 = full
+    std::deque<lr_bucket> lr[FDA_MAX_LEVELS];
 
     // tensor-core M2L (chosen precision)
     tc_ops tc_m2l[FDA_MAX_LEVELS], tc_m2m[FDA_MAX_LEVELS], tc_l2l[FDA_MAX_LEVELS];
@@ -344,6 +364,8 @@ void fda_sai_loss_grad_impl(int64_t n, const double *cent, const double *nrm, co
                             const int64_t *bptr, const int32_t *belem, const c64d *A, const double *W, int fp32,
                             double *loss, double *grad);
 void fda_pack_tc(fda_handle *h);
+// split nvec FP32 vectors of length T into bf16 hi/lo (the gather layout of the tensor-core kernel)
+void fda_split_vectors(fda_handle *h, const c32f *src, int64_t nvec, int T, dbuf &out);
 // split level l's FP32 densities (mr right-hand sides) into bf16 hi/lo
 void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr);
 // dst += op * src for every pair of batch B on the tensor cores; src is the

@@ -26,21 +26,21 @@
 namespace {
 
 constexpr int RT = 256;
-constexpr int RCH = 1024;  // chunks per vector for the two-stage dot products (enough CTAs to reach HBM bandwidth)
+constexpr int RCH = 1024;  // most chunks per vector for the two-stage dot products
 
-// partial[i * RCH + c] = sum over chunk c of conj(V_i[n]) w[n].  A CTA takes
+// partial[i * rch + c] = sum over chunk c of conj(V_i[n]) w[n].  A CTA takes
 // one chunk of the index range and a group of DVG vectors: every thread
 // reads its w values once and accumulates DVG products from them, then the
 // DVG sums are reduced across the CTA.
 constexpr int DVG = 8;  // vectors per CTA
 
 __global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv, const c64d *w, int64_t n,
-                                             c64d *partial)
+                                             c64d *partial, int rch)
 {
     __shared__ double sr[RT / 32][DVG], si[RT / 32][DVG];
     const int c = blockIdx.x, i0 = blockIdx.y * DVG, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ng = min(DVG, nv - i0);
-    const int64_t per = (n + RCH - 1) / RCH;
+    const int64_t per = (n + rch - 1) / rch;
     const int64_t b = (int64_t)c * per, e = b + per < n ? b + per : n;
     double ar[DVG], ai[DVG];
 #pragma unroll
@@ -74,18 +74,18 @@ __global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv,
             r += sr[q][threadIdx.x];
             im += si[q][threadIdx.x];
         }
-        partial[(int64_t)(i0 + threadIdx.x) * RCH + c] = c64d(r, im);
+        partial[(int64_t)(i0 + threadIdx.x) * rch + c] = c64d(r, im);
     }
 }
 
-__global__ void k_dots_finish(const c64d *partial, int nv, c64d *out)
+__global__ void k_dots_finish(const c64d *partial, int nv, c64d *out, int rch)
 {
     __shared__ double sr[RT], si[RT];
     int i = blockIdx.x;
     double ar = 0.0, ai = 0.0;
-    for (int c = threadIdx.x; c < RCH; c += RT) {
-        ar += partial[(int64_t)i * RCH + c].re;
-        ai += partial[(int64_t)i * RCH + c].im;
+    for (int c = threadIdx.x; c < rch; c += RT) {
+        ar += partial[(int64_t)i * rch + c].re;
+        ai += partial[(int64_t)i * rch + c].im;
     }
     sr[threadIdx.x] = ar;
     si[threadIdx.x] = ai;
@@ -270,10 +270,13 @@ struct solver {
     // out[0 .. nv) = V^H w on the device (two-stage reduction)
     void dots_dev(const c64d *V, int nv, const c64d *w, c64d *out)
     {
-        dim3 g(RCH, (nv + DVG - 1) / DVG);
-        k_dots<<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>());
+        // about 2048 CTAs whatever the number of vectors (groups of DVG)
+        const int ng = (nv + DVG - 1) / DVG;
+        const int rch = std::max(128, std::min(RCH, 2048 / ng));
+        dim3 g(rch, ng);
+        k_dots<<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>(), rch);
         FDA_CHECK_LAUNCH();
-        k_dots_finish<<<nv, RT, 0, h->stream>>>(partial.as<c64d>(), nv, out);
+        k_dots_finish<<<nv, RT, 0, h->stream>>>(partial.as<c64d>(), nv, out, rch);
         FDA_CHECK_LAUNCH();
     }
     // ||w|| on the host (synchronises; once per restart cycle)

@@ -184,6 +184,13 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_leaf_tc(leaf_args a, leaf_lev
 
     if (warp >= 5) {
         // ---------------- producers
+        // Each thread's loads of a stage are issued together, into registers,
+        // before it waits for the ring slot; the split and the shared-memory
+        // stores follow.  Item i of thread tp: operator item tp + i LT_NPROD
+        // (row, pair of K) and input item tp + i LT_NPROD (column, pair of K).
+        constexpr int AI = 64 * 16 / LT_NPROD;  // operator items per thread
+        constexpr int BI = NC * 16 / LT_NPROD;  // input items per thread
+        static_assert(AI >= 1 && BI >= 1, "at least one item per producer thread");
         const int tp = tid - 160;
         int g = 0;
         bool ok = true;
@@ -194,6 +201,32 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_leaf_tc(leaf_args a, leaf_lev
             const int rmax = min(64, f.rows - 64 * t.rt);
             for (int s = 0; s < nkc; ++s, ++g) {
                 const int b = g % ST;
+                const int k0 = s * KC;
+                c32f av[AI][2], bv[BI][2];
+#pragma unroll
+                for (int i = 0; i < AI; ++i) {
+                    const int e = tp + i * LT_NPROD;
+                    const int r = KIND == LT_NEAR ? e >> 4 : e & 63;
+                    const int kp = KIND == LT_NEAR ? e & 15 : e >> 6;
+                    const int k = k0 + 2 * kp, rg = 64 * t.rt + r;
+                    av[i][0] = c32f();
+                    av[i][1] = c32f();
+                    if (r < rmax) {
+                        if (k < f.K) av[i][0] = a_at<KIND>(a, f, rg, k);
+                        if (k + 1 < f.K) av[i][1] = a_at<KIND>(a, f, rg, k + 1);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < BI; ++i) {
+                    const int e = tp + i * LT_NPROD;
+                    const int n = e >> 4, k = k0 + 2 * (e & 15), m = t.m0 + n;
+                    bv[i][0] = c32f();
+                    bv[i][1] = c32f();
+                    if (m < a.mr) {
+                        if (k < f.K) bv[i][0] = b_at<KIND>(a, lv, f, k, m);
+                        if (k + 1 < f.K) bv[i][1] = b_at<KIND>(a, lv, f, k + 1, m);
+                    }
+                }
                 const bool fail = g >= ST && !mbar_wait_ab(smem_u32(&empty[b]), ((g - ST) / ST) & 1, abort_v);
                 if (bar_any(1, LT_NPROD, fail)) {
                     if (fail && !*abort_v) atomicExch(a.err, 2);
@@ -202,39 +235,31 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_leaf_tc(leaf_args a, leaf_lev
                     break;
                 }
                 uint8_t *st = smem + b * STAGE;
-                const int k0 = s * KC;
-                // operator: 64 rows x 16 pairs of K; along K for the row-major
-                // near-field blocks, along the rows for S~ and T~ (coalesced loads)
-                for (int e = tp; e < 64 * 16; e += LT_NPROD) {
+                // operator: Re rows 0-63, Im rows 64-127, hi then lo
+#pragma unroll
+                for (int i = 0; i < AI; ++i) {
+                    const int e = tp + i * LT_NPROD;
                     const int r = KIND == LT_NEAR ? e >> 4 : e & 63;
                     const int kp = KIND == LT_NEAR ? e & 15 : e >> 6;
                     if (r >= rmax) continue;
-                    const int k = k0 + 2 * kp, rg = 64 * t.rt + r;
-                    c32f v0, v1;
-                    if (k < f.K) v0 = a_at<KIND>(a, f, rg, k);
-                    if (k + 1 < f.K) v1 = a_at<KIND>(a, f, rg, k + 1);
                     uint32_t rh, rl, ih, il;
-                    split2(v0.re, v1.re, rh, rl);
-                    split2(v0.im, v1.im, ih, il);
+                    split2(av[i][0].re, av[i][1].re, rh, rl);
+                    split2(av[i][0].im, av[i][1].im, ih, il);
                     const int ore = core_off(r, 2 * kp), oim = core_off(64 + r, 2 * kp);
                     *reinterpret_cast<uint32_t *>(st + ore) = rh;
                     *reinterpret_cast<uint32_t *>(st + oim) = ih;
                     *reinterpret_cast<uint32_t *>(st + ABYTES + ore) = rl;
                     *reinterpret_cast<uint32_t *>(st + ABYTES + oim) = il;
                 }
-                // inputs: NC right-hand sides x 16 pairs of K: Br hi, Bi hi, Br lo, Bi lo
+                // inputs: Br hi, Bi hi, Br lo, Bi lo panels of NC rows
                 uint8_t *sb = st + AR;
-                for (int e = tp; e < NC * 16; e += LT_NPROD) {
-                    const int n = e >> 4, kp = e & 15, k = k0 + 2 * kp, m = t.m0 + n;
-                    c32f v0, v1;
-                    if (m < a.mr) {
-                        if (k < f.K) v0 = b_at<KIND>(a, lv, f, k, m);
-                        if (k + 1 < f.K) v1 = b_at<KIND>(a, lv, f, k + 1, m);
-                    }
+#pragma unroll
+                for (int i = 0; i < BI; ++i) {
+                    const int e = tp + i * LT_NPROD;
                     uint32_t rh, rl, ih, il;
-                    split2(v0.re, v1.re, rh, rl);
-                    split2(v0.im, v1.im, ih, il);
-                    const int o = core_off(n, 2 * kp);
+                    split2(bv[i][0].re, bv[i][1].re, rh, rl);
+                    split2(bv[i][0].im, bv[i][1].im, ih, il);
+                    const int o = core_off(e >> 4, 2 * (e & 15));
                     *reinterpret_cast<uint32_t *>(sb + o) = rh;
                     *reinterpret_cast<uint32_t *>(sb + BB + o) = ih;
                     *reinterpret_cast<uint32_t *>(sb + 2 * BB + o) = rl;

@@ -447,6 +447,197 @@ __global__ void k_diag(const c64d *A, int n, double *d)
     if (i < n) d[i] = A[i + (int64_t)i * n].re;
 }
 
+// ---- low-rank reduced M2L operators (Sec. 4.2, Eq. epsk)
+// Column-pivoted modified Gram-Schmidt of one m x n column-major matrix per
+// CTA, in place (A becomes the residual of the retained columns): at each
+// step the remaining column of largest norm is orthogonalised once more
+// against the chosen ones, normalised and stored as the next column of Q,
+// and projected out of every remaining column.  It stops when the squared
+// Frobenius norm of the remaining columns is at most (tol_rel x the largest
+// initial column norm)^2, or after kmax columns (rank[] = kmax + 1 then:
+// not converged).  Q (m x kmax) is zero beyond the rank.  m <= 1024.
+constexpr int QRT = 256;
+
+__global__ void __launch_bounds__(QRT) k_cpqr(c64d *A, int m, int n, int64_t sA, c64d *Q, int64_t sQ, int kmax,
+                                              double tol_rel, int *rank)
+{
+    extern __shared__ double qr_smem[];
+    double *nrm = qr_smem;                                   // [n]
+    c64d *q = reinterpret_cast<c64d *>(qr_smem + n + (n & 1));  // [m]
+    __shared__ double red_v[QRT / 32];
+    __shared__ int red_i[QRT / 32];
+    __shared__ c64d coef[1024];
+    __shared__ double s_tol2, s_tot;
+    __shared__ int s_piv;
+    c64d *a = A + (int64_t)blockIdx.x * sA;
+    c64d *Qm = Q + (int64_t)blockIdx.x * sQ;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = QRT / 32;
+    for (int j = warp; j < n; j += nw) {
+        double s = 0.0;
+        for (int r = lane; r < m; r += 32) s += a[r + (int64_t)j * m].re * a[r + (int64_t)j * m].re + a[r + (int64_t)j * m].im * a[r + (int64_t)j * m].im;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) nrm[j] = s;
+    }
+    for (int e = tid; e < m * kmax; e += QRT) Qm[e] = c64d();
+    __syncthreads();
+    int k = 0;
+    bool done = false;
+    for (; k <= kmax; ++k) {
+        // remaining mass and pivot
+        double tot = 0.0, best = -1.0;
+        int bi = -1;
+        for (int j = tid; j < n; j += QRT) {
+            const double v = nrm[j];
+            if (v >= 0.0) {
+                tot += v;
+                if (v > best) { best = v; bi = j; }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; coef[warp] = c64d(tot, 0.0); }
+        __syncthreads();
+        if (tid == 0) {
+            double b2 = -1.0, t2 = 0.0;
+            int i2 = -1;
+            for (int w = 0; w < nw; ++w) {
+                t2 += coef[w].re;
+                if (red_v[w] > b2 || (red_v[w] == b2 && red_i[w] >= 0 && (i2 < 0 || red_i[w] < i2))) { b2 = red_v[w]; i2 = red_i[w]; }
+            }
+            if (k == 0) s_tol2 = tol_rel * tol_rel * fmax(b2, 0.0);
+            s_tot = t2;
+            s_piv = i2;
+        }
+        __syncthreads();
+        if (s_tot <= s_tol2 || s_piv < 0) { done = true; break; }
+        if (k == kmax) break;
+        const int p = s_piv;
+        for (int r = tid; r < m; r += QRT) q[r] = a[r + (int64_t)p * m];
+        __syncthreads();
+        // one more orthogonalisation against the chosen columns
+        for (int i = warp; i < k; i += nw) {
+            c64d c;
+            for (int r = lane; r < m; r += 32) cfma_conj(c, Qm[r + (int64_t)i * m], q[r]);
+            for (int o = 16; o > 0; o >>= 1) {
+                c.re += __shfl_xor_sync(0xffffffffu, c.re, o);
+                c.im += __shfl_xor_sync(0xffffffffu, c.im, o);
+            }
+            if (lane == 0) coef[i] = c;
+        }
+        __syncthreads();
+        for (int r = tid; r < m; r += QRT) {
+            c64d v = q[r];
+            for (int i = 0; i < k; ++i) {
+                const c64d t = coef[i] * Qm[r + (int64_t)i * m];
+                v.re -= t.re;
+                v.im -= t.im;
+            }
+            q[r] = v;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double s = 0.0;
+            for (int r = lane; r < m; r += 32) s += q[r].re * q[r].re + q[r].im * q[r].im;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) red_v[0] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+        }
+        __syncthreads();
+        const double inv = red_v[0];
+        for (int r = tid; r < m; r += QRT) {
+            const c64d v(q[r].re * inv, q[r].im * inv);
+            q[r] = v;
+            Qm[r + (int64_t)k * m] = v;
+        }
+        if (tid == 0) nrm[p] = -1.0;
+        __syncthreads();
+        // project q out of the remaining columns, fresh norms
+        for (int j = warp; j < n; j += nw) {
+            if (nrm[j] < 0.0) continue;
+            c64d c;
+            for (int r = lane; r < m; r += 32) cfma_conj(c, q[r], a[r + (int64_t)j * m]);
+            for (int o = 16; o > 0; o >>= 1) {
+                c.re += __shfl_xor_sync(0xffffffffu, c.re, o);
+                c.im += __shfl_xor_sync(0xffffffffu, c.im, o);
+            }
+            double s = 0.0;
+            for (int r = lane; r < m; r += 32) {
+                c64d v = a[r + (int64_t)j * m];
+                const c64d t = c * q[r];
+                v.re -= t.re;
+                v.im -= t.im;
+                a[r + (int64_t)j * m] = v;
+                s += v.re * v.re + v.im * v.im;
+            }
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) nrm[j] = s;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) rank[blockIdx.x] = done ? k : kmax + 1;
+}
+
+// err2[b] = || K_b - U_b Q_b^H ||_F^2 and ref2[b] = (largest column norm of
+// K_b)^2 for T x T operators K, U and Q of T x r columns (column-major).
+__global__ void k_lr_check(const c64d *K, const c64d *U, const c64d *Qm, int T, int r, double *err2, double *ref2)
+{
+    __shared__ double se[QRT / 32], sr[QRT / 32];
+    const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const c64d *Kb = K + (int64_t)b * T * T, *Ub = U + (int64_t)b * T * r, *Qb = Qm + (int64_t)b * T * r;
+    double e = 0.0, mx = 0.0;
+    for (int j = warp; j < T; j += QRT / 32) {
+        double cn = 0.0;
+        for (int i = lane; i < T; i += 32) {
+            c64d v = Kb[i + (int64_t)j * T];
+            cn += v.re * v.re + v.im * v.im;
+            for (int t = 0; t < r; ++t) {
+                const c64d u = Ub[i + (int64_t)t * T], qq = Qb[j + (int64_t)t * T];
+                // v -= u conj(qq)
+                v.re -= u.re * qq.re + u.im * qq.im;
+                v.im -= u.im * qq.re - u.re * qq.im;
+            }
+            e += v.re * v.re + v.im * v.im;
+        }
+        for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, o);
+        mx = fmax(mx, cn);
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) {
+        se[warp] = e;
+        sr[warp] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, m = 0.0;
+        for (int w = 0; w < QRT / 32; ++w) {
+            a += se[w];
+            m = fmax(m, sr[w]);
+        }
+        err2[b] = a;
+        ref2[b] = m;
+    }
+}
+
+// bucket factors: U^ (T x rpad) from U (T x rcap) and V^ = Q^H (rpad x T)
+// from Q (T x rcap), for the bucket's operators ops[b]
+__global__ void k_lr_gather(const c64d *U, const c64d *Qm, int T, int rcap, const int32_t *ops, int rpad, c64d *Ub,
+                            c64d *Vb)
+{
+    const int b = blockIdx.y, o = ops[b];
+    const c64d *Uo = U + (int64_t)o * T * rcap, *Qo = Qm + (int64_t)o * T * rcap;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)T * rpad;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % T), j = (int)(e / T);  // U^(i, j)
+        Ub[(int64_t)b * T * rpad + e] = j < rcap ? Uo[i + (int64_t)j * T] : c64d();
+        // V^(j, i) = conj(Q(i, j)), column-major rpad x T
+        const c64d q = j < rcap ? Qo[i + (int64_t)j * T] : c64d();
+        Vb[(int64_t)b * T * rpad + j + (int64_t)i * rpad] = c64d(q.re, -q.im);
+    }
+}
+
 __global__ void k_f64_to_f32(const c64d *a, c32f *b, int64_t n)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -674,6 +865,131 @@ static void leaf_operators(fda_handle *h, int side)
     }
 }
 
+// Sec. 4.2: truncated low-rank factorisation of every reduced M2L operator
+// K~_o of level l in FP64, K~_o ~= (K~_o Q) Q^H with Q (T x r) orthonormal.
+// A randomized range sketch (Y = K~ Omega, s columns, Omega Gaussian) and a
+// pivoted Gram-Schmidt of Y give a basis Q1 of K~'s range; a pivoted
+// Gram-Schmidt of C = K~^H Q1 = (Q1^H K~)^H, stopped when the Frobenius norm
+// of what remains is at most eps times its largest column norm, gives the
+// row-space basis Q of rank r (Eq. epsk, in the Frobenius norm).  Every
+// factorisation is checked explicitly: ||K~ - U^ V^||_F <= eps times the
+// largest column norm of K~ (a lower bound of sigma_0); an operator that
+// fails the check or needs r >= T/2 stays in full form.  Operators whose
+// two-stage application (rank padded to 32) is cheaper than the full one,
+// both in flops (2 r T < T^2) and in tensor-core tiles (64 rows, 32 of K),
+// are grouped by padded rank.
+static void lowrank_level(fda_handle *h, int l)
+{
+    level_info &L = h->lev[l];
+    const int T = L.T, nops = L.n_ops;
+    h->op_rank[l].assign(std::max(nops, 0), -1);
+    h->op_bucket[l].assign(std::max(nops, 0), -1);
+    h->lr[l].clear();
+    const int rcap = (T - 1) / 2;  // r < T/2
+    if (!h->cfg.lowrank || nops == 0 || T > 1024 || 2 * 32 >= T) return;
+    const int sk = std::min(T, rcap + 16);
+    const double eps = h->cfg.eps;
+    cudaStream_t st = h->stream;
+    // Gaussian test matrix (splitmix64 and the Box-Muller transform), T x sk
+    std::vector<c64d> om((size_t)T * sk);
+    uint64_t z = 0x2545f4914f6cdd1dull + 0x9e3779b97f4a7c15ull * (uint64_t)(l + 1);
+    auto next = [&]() {
+        z += 0x9e3779b97f4a7c15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+        x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+        return x ^ (x >> 31);
+    };
+    for (auto &v : om) {
+        const double u1 = ((double)(next() >> 11) + 0.5) / 9007199254740992.0;
+        const double u2 = ((double)(next() >> 11) + 0.5) / 9007199254740992.0;
+        const double rr = sqrt(-2.0 * log(u1));
+        v = c64d(rr * cos(2.0 * FDA_PI * u2), rr * sin(2.0 * FDA_PI * u2));
+    }
+    dbuf Om, Uall, Qall;
+    Om.alloc(sizeof(c64d) * om.size());
+    FDA_CUDA(cudaMemcpy(Om.p, om.data(), sizeof(c64d) * om.size(), cudaMemcpyHostToDevice));
+    Uall.alloc(sizeof(c64d) * (size_t)nops * T * rcap);
+    Qall.alloc(sizeof(c64d) * (size_t)nops * T * rcap);
+    const int chunk = std::max(1, std::min(nops, (int)((512ll << 20) / (16ll * T * (2 * sk)))));
+    dbuf Y, Q1, C, rk1, rk2, e2, r2;
+    Y.alloc(sizeof(c64d) * (size_t)chunk * T * sk);
+    Q1.alloc(sizeof(c64d) * (size_t)chunk * T * sk);
+    C.alloc(sizeof(c64d) * (size_t)chunk * T * sk);
+    rk1.alloc(sizeof(int) * chunk);
+    rk2.alloc(sizeof(int) * chunk);
+    e2.alloc(sizeof(double) * chunk);
+    r2.alloc(sizeof(double) * chunk);
+    const size_t qsm = sizeof(double) * (sk + (sk & 1)) + sizeof(c64d) * T;
+    const c64d *K = h->op64.Kt[l].as<c64d>();
+    std::vector<int> hr(chunk);
+    std::vector<double> he(chunk), hq(chunk);
+    for (int o0 = 0; o0 < nops; o0 += chunk) {
+        const int nb = std::min(chunk, nops - o0);
+        std::vector<gemm_job> g1(nb), g2(nb), g3(nb);
+        for (int b = 0; b < nb; ++b) {
+            const c64d *Ko = K + (size_t)(o0 + b) * T * T;
+            g1[b] = gemm_job{Ko, Om.as<c64d>(), Y.as<c64d>() + (size_t)b * T * sk};
+            g2[b] = gemm_job{Ko, Q1.as<c64d>() + (size_t)b * T * sk, C.as<c64d>() + (size_t)b * T * sk};
+            g3[b] = gemm_job{Ko, Qall.as<c64d>() + (size_t)(o0 + b) * T * rcap,
+                             Uall.as<c64d>() + (size_t)(o0 + b) * T * rcap};
+        }
+        run_gemm(h, g1, T, sk, T, T, T, T, 0, 0);  // Y = K~ Omega
+        k_cpqr<<<nb, QRT, qsm, st>>>(Y.as<c64d>(), T, sk, (int64_t)T * sk, Q1.as<c64d>(), (int64_t)T * sk, sk,
+                                     0.01 * eps, rk1.as<int>());
+        FDA_CHECK_LAUNCH();
+        run_gemm(h, g2, T, sk, T, T, T, T, 2, 0);  // C = K~^H Q1
+        k_cpqr<<<nb, QRT, qsm, st>>>(C.as<c64d>(), T, sk, (int64_t)T * sk,
+                                     Qall.as<c64d>() + (size_t)o0 * T * rcap, (int64_t)T * rcap, rcap, eps,
+                                     rk2.as<int>());
+        FDA_CHECK_LAUNCH();
+        run_gemm(h, g3, T, rcap, T, T, T, T, 0, 0);  // U^ = K~ Q
+        k_lr_check<<<nb, QRT, 0, st>>>(K + (size_t)o0 * T * T, Uall.as<c64d>() + (size_t)o0 * T * rcap,
+                                       Qall.as<c64d>() + (size_t)o0 * T * rcap, T, rcap, e2.as<double>(),
+                                       r2.as<double>());
+        FDA_CHECK_LAUNCH();
+        FDA_CUDA(cudaMemcpyAsync(hr.data(), rk2.p, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+        FDA_CUDA(cudaMemcpyAsync(he.data(), e2.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        FDA_CUDA(cudaMemcpyAsync(hq.data(), r2.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        FDA_CUDA(cudaStreamSynchronize(st));
+        for (int b = 0; b < nb; ++b) {
+            const bool ok = hr[b] >= 1 && hr[b] <= rcap && std::isfinite(he[b]) && he[b] <= eps * eps * hq[b];
+            h->op_rank[l][o0 + b] = ok ? hr[b] : -1;
+        }
+    }
+    // buckets of padded rank where the two stages are cheaper
+    auto nrt = [](int x) { return (x + 63) / 64; };
+    auto nkc = [](int x) { return (x + 31) / 32; };
+    std::vector<int> bucket_of_rpad(T + 1, -1);
+    for (int o = 0; o < nops; ++o) {
+        const int r = h->op_rank[l][o];
+        if (r < 1) continue;
+        const int rpad = (r + 31) / 32 * 32;
+        const int cost_full = nrt(T) * nkc(T), cost_lr = nrt(rpad) * nkc(T) + nrt(T) * nkc(rpad);
+        if (2 * rpad >= T || cost_lr >= cost_full) continue;
+        if (bucket_of_rpad[rpad] < 0) {
+            bucket_of_rpad[rpad] = (int)h->lr[l].size();
+            h->lr[l].emplace_back();
+            h->lr[l].back().rpad = rpad;
+        }
+        const int b = bucket_of_rpad[rpad];
+        h->op_bucket[l][o] = b;
+        h->lr[l][b].ops.push_back(o);
+    }
+    for (lr_bucket &B : h->lr[l]) {
+        const int nb = (int)B.ops.size();
+        dbuf dops;
+        dops.alloc(sizeof(int32_t) * nb);
+        FDA_CUDA(cudaMemcpy(dops.p, B.ops.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
+        B.U64.alloc(sizeof(c64d) * (size_t)nb * T * B.rpad);
+        B.V64.alloc(sizeof(c64d) * (size_t)nb * T * B.rpad);
+        k_lr_gather<<<dim3(64, nb), 256, 0, st>>>(Uall.as<c64d>(), Qall.as<c64d>(), T, rcap, dops.as<int32_t>(),
+                                                  B.rpad, B.U64.as<c64d>(), B.V64.as<c64d>());
+        FDA_CHECK_LAUNCH();
+    }
+    FDA_CUDA(cudaStreamSynchronize(st));
+}
+
 void fda_far_precompute(fda_handle *h)
 {
     cudaStream_t s = h->stream;
@@ -772,6 +1088,7 @@ void fda_far_precompute(fda_handle *h)
             run_gemm(h, g1, n, T, n, n, n, n, 0, 0);
             run_gemm(h, g2, T, T, n, n, n, T, 1, 0);
         }
+        lowrank_level(h, l);
     }
 
     // ---- M2M and L2L operators (parent level l, child level l+1)
@@ -888,6 +1205,10 @@ void fda_far_convert_f32(fda_handle *h)
         conv(h->op64.Kt[l], h->op32.Kt[l]);
         conv(h->op64.Mt[l], h->op32.Mt[l]);
         conv(h->op64.Lt[l], h->op32.Lt[l]);
+        for (lr_bucket &B : h->lr[l]) {
+            conv(B.U64, B.U32);
+            conv(B.V64, B.V32);
+        }
     }
     conv(h->op64.St, h->op32.St);
     conv(h->op64.Tt, h->op32.Tt);

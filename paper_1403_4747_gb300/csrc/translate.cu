@@ -198,6 +198,49 @@ void fda_build_batches(fda_handle *h)
                 pr.push_back(pair_rec{ilo[e], ((ils[e] - L.box0) * L.ncones + su) * L.T,
                                       ((b - L.box0) * L.ncones + u) * L.T});
             }
+        // low-rank operators (Sec. 4.2): their pairs go to the rank buckets,
+        // stage 1 writing pair p's intermediate at p rpad, stage 2 reading it
+        const std::vector<int> &bk = h->op_bucket[l];
+        if (!h->lr[l].empty()) {
+            std::vector<pair_rec> full;
+            std::vector<std::vector<pair_rec>> per(h->lr[l].size());
+            std::vector<int> local(L.n_ops, -1);  // operator index inside its bucket
+            for (size_t b = 0; b < h->lr[l].size(); ++b)
+                for (size_t i = 0; i < h->lr[l][b].ops.size(); ++i) local[h->lr[l][b].ops[i]] = (int)i;
+            for (const pair_rec &p : pr) {
+                const int b = p.op < (int)bk.size() ? bk[p.op] : -1;
+                if (b < 0) full.push_back(p);
+                else per[b].push_back(pair_rec{local[p.op], p.src, p.dst});
+            }
+            for (size_t b = 0; b < per.size(); ++b) {
+                lr_bucket &B = h->lr[l][b];
+                std::vector<pair_rec> &q = per[b];
+                // group by bucket operator (stable), so both stages see the same order
+                std::stable_sort(q.begin(), q.end(), [](const pair_rec &x, const pair_rec &y) { return x.op < y.op; });
+                std::vector<pair_rec> s1(q.size()), s2(q.size());
+                for (size_t i = 0; i < q.size(); ++i) {
+                    s1[i] = pair_rec{q[i].op, q[i].src, (int)i * B.rpad};
+                    s2[i] = pair_rec{q[i].op, (int)i * B.rpad, q[i].dst};
+                }
+                const int nb = std::max(1, (int)B.ops.size());
+                make_batch(s1, nb, B.rpad, B.b1);
+                make_batch(s2, nb, L.T, B.b2);
+                B.npairs = (int64_t)q.size();
+                // intermediates for max_rhs right-hand sides, allocated once:
+                // captured graphs keep their addresses
+                const size_t vals = (size_t)B.npairs * B.rpad * std::max(1, h->cfg.max_rhs);
+                B.t64.alloc(sizeof(c64d) * vals);
+                if (h->cfg.precision == FDA_CHOSEN_FP32) {
+                    B.t32.alloc(sizeof(c32f) * vals);
+                    if (h->cfg.tensor_cores) {
+                        // bf16 hi/lo of Re and Im: 8 bytes per value (rpad is a multiple of 32)
+                        B.ts.alloc(8 * vals);
+                        FDA_CUDA(cudaMemsetAsync(B.ts.p, 0, B.ts.bytes, h->stream));
+                    }
+                }
+            }
+            pr.swap(full);
+        }
         make_batch(pr, std::max(1, L.n_ops), L.T, h->b_m2l[l]);
         if (l + 1 >= h->nlev) continue;
         const level_info &C = h->lev[l + 1];

@@ -445,6 +445,11 @@ void fda_pack_tc(fda_handle *h)
             pack_one(h, h->tc_m2m[l], h->b_m2m[l], h->op64.Mt[l], 8 * L.ncones, L.T, Tc);
             pack_one(h, h->tc_l2l[l], h->b_l2l[l], h->op64.Lt[l], 8 * L.ncones, Tc, L.T);
         }
+        // low-rank M2L buckets (Sec. 4.2): V^ (rpad x T) and U^ (T x rpad) panels
+        for (lr_bucket &B : h->lr[l]) {
+            pack_one(h, B.tc1, B.b1, B.V64, (int)B.ops.size(), B.rpad, L.T);
+            pack_one(h, B.tc2, B.b2, B.U64, (int)B.ops.size(), L.T, B.rpad);
+        }
         const size_t nvec = (size_t)L.nbox * L.ncones * mrmax;
         const size_t Tp = (size_t)((L.T + KC - 1) / KC) * KC;
         h->qs[l].alloc(sizeof(__nv_bfloat16) * nvec * 4 * Tp);
@@ -466,6 +471,15 @@ void fda_split_tc(fda_handle *h, int l, const c32f *src, dbuf &out, int mr)
     const int64_t nvec = (int64_t)L.nbox * L.ncones * mr;
     if (out.bytes < sizeof(__nv_bfloat16) * (size_t)nvec * 4 * Tp) fda_fail(FDA_ERR_STATE, "split buffer too small");
     k_split_density<<<1024, 256, 0, h->stream>>>(src, nvec, L.T, Tp, out.as<__nv_bfloat16>());
+    FDA_CHECK_LAUNCH();
+}
+
+void fda_split_vectors(fda_handle *h, const c32f *src, int64_t nvec, int T, dbuf &out)
+{
+    const int Tp = (T + KC - 1) / KC * KC;
+    const size_t need = sizeof(__nv_bfloat16) * (size_t)nvec * 4 * Tp;
+    if (out.bytes < need) fda_fail(FDA_ERR_STATE, "split buffer too small");
+    k_split_density<<<1024, 256, 0, h->stream>>>(src, nvec, T, Tp, out.as<__nv_bfloat16>());
     FDA_CHECK_LAUNCH();
 }
 

@@ -31,10 +31,17 @@ def _stats():
 
 
 def test_m2l_bytes_and_flops():
-    P = _FakeProblem(_stats())
-    # level 1: 8 * 2 * 100 + 24 * 8 * 6 * 10; level 2: 8 * 5 * 16 + 24 * 64 * 4
-    assert bench._m2l_bytes(P) == 8 * 2 * 100 + 24 * 48 * 10 + 8 * 5 * 16 + 24 * 64 * 4
-    assert bench._m2l_flops(P) == 8 * 100 * 7 + 8 * 16 * 100
+    """The bench sums the library's per-level algorithmic M2L work over the
+    levels in use (the per-level counts are checked against the closed form
+    in the GPU tests)."""
+    st = _stats()
+    st.level_m2l_bytes = [0.0] * 32
+    st.level_m2l_flops = [0.0] * 32
+    st.level_m2l_bytes[1], st.level_m2l_bytes[2] = 1.5e6, 2.5e6
+    st.level_m2l_flops[1], st.level_m2l_flops[2] = 3.0e9, 4.0e9
+    P = _FakeProblem(st)
+    assert bench._m2l_bytes(P) == 4000000
+    assert bench._m2l_flops(P) == 7000000000
 
 
 def test_traffic_record_is_keyed_to_the_kernel_source():

@@ -73,6 +73,9 @@ def test_sphere_every_tile_shape_and_both_precisions(sphere):
         ranks = [st.level_rank[l] for l in range(st.n_levels)]
         cones = [st.level_cones[l] for l in range(st.n_levels)]
         assert max(ranks) > 300 and max(cones) >= 96, (ranks, cones)
+        # the rank-342 level runs in the low-rank form of Sec. 4.2
+        l3 = ranks.index(max(r for r in ranks if r < 345))
+        assert st.level_lr_ops[l3] > 0 and st.level_lr_rank_max[l3] < ranks[l3] / 2
         xd = _dev(x)
         y_tuned = P.apply(xd).cpu().numpy()
         errs = {"tuned": _rel(y_tuned[rows], ref)}
@@ -102,6 +105,24 @@ def test_sphere_printed_coupling(sphere):
         fda_set_precision(P.h, 0)
         e64 = _rel(P.apply(xd).cpu().numpy()[rows], ref)
         print("alpha = +i/k: chosen %.3e plain %.3e" % (e32, e64))
+        assert e32 < 1e-4 and e64 < 1e-4
+    finally:
+        P.close()
+
+
+def test_sphere_full_form_operators(sphere):
+    """The same matvec with Sec. 4.2's low-rank step off (every reduced M2L
+    operator in full), both precisions."""
+    from paper_1403_4747_gb300 import FDAProblem, fda_set_precision
+    v, f, x, rows = sphere
+    ref = oracle.matvec(v, f, K, x, rows=rows)
+    P = FDAProblem(v, f, K, precision=1, lowrank=0)
+    try:
+        xd = _dev(x)
+        e32 = _rel(P.apply(xd).cpu().numpy()[rows], ref)
+        fda_set_precision(P.h, 0)
+        e64 = _rel(P.apply(xd).cpu().numpy()[rows], ref)
+        print("low-rank off: chosen %.3e plain %.3e" % (e32, e64))
         assert e32 < 1e-4 and e64 < 1e-4
     finally:
         P.close()

@@ -295,3 +295,64 @@ def test_leaf_products_on_tensor_cores(nrhs):
     assert _rel(y_tc, y_simt) < 2e-5
     m = nrhs - 1
     assert _rel(y_tc[m], oracle.matvec(v, f, k, x[m])) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lowrank_m2l_matches_full_and_oracle(precision):
+    """Sec. 4.2: with each reduced M2L operator factorised as U^ V^ at eps
+    (Eq. epsk) and applied as two products, the matvec stays within the FDA
+    tolerance of the oracle and close to the same matvec with every operator
+    in full; the statistics show low-rank operators with r < T/2 at the levels
+    where T is large enough for the two stages to be cheaper."""
+    v, f = icosphere(5)
+    k = 25.0
+    x = complex_normal(len(f), seed=61)
+    on = _problem(v, f, k, precision=precision)
+    off = _problem(v, f, k, precision=precision, lowrank=0)
+    st = on.stats()
+    nl = st.n_levels
+    assert sum(st.level_lr_ops[l] for l in range(nl)) > 0
+    assert sum(off.stats().level_lr_ops[l] for l in range(nl)) == 0
+    for l in range(nl):
+        if st.level_lr_ops[l]:
+            assert 0 < st.level_lr_rank_max[l] < st.level_rank[l] / 2
+            assert st.level_lr_pairs[l] > 0
+            # the method's flops of that level drop below the full form's
+            assert st.level_m2l_flops[l] < 8.0 * st.level_rank[l] ** 2 * st.level_m2l_pairs[l]
+    so = off.stats()
+    for l in range(nl):
+        T = so.level_rank[l]
+        if T == 0 or so.level_m2l_pairs[l] == 0:
+            continue
+        # full form: 8 T^2 flops per pair; each distinct operator once, source
+        # densities once, target densities read and written once (8 bytes each)
+        assert so.level_m2l_flops[l] == 8.0 * T * T * so.level_m2l_pairs[l]
+        assert so.level_m2l_bytes[l] == 8.0 * so.level_m2l_ops[l] * T * T + 24.0 * so.level_boxes[l] * so.level_cones[l] * T
+    xd = _dev(x)
+    y_on = on.apply(xd).cpu().numpy()
+    y_off = off.apply(xd).cpu().numpy()
+    ref = oracle.matvec(v, f, k, x)
+    assert _rel(y_on, ref) < 1e-4 and _rel(y_off, ref) < 1e-4
+    assert _rel(y_on, y_off) < 1e-4
+
+
+def test_graphs_survive_changing_right_hand_side_counts():
+    """One handle with graphs and the low-rank M2L applies one, then eight,
+    then one right-hand side again (each count captured and replayed), then
+    solves: every result equals an eager handle's, so no captured graph
+    points at a buffer that a later count re-sized."""
+    v, f = icosphere(5)
+    k = 25.0
+    x1 = _dev(complex_normal(len(f), seed=71))
+    x8 = _dev(complex_normal(len(f), seed=72, nrhs=8))
+    G = _problem(v, f, k, precision=1, max_rhs=8, graphs=1)
+    E = _problem(v, f, k, precision=1, max_rhs=8, graphs=0)
+    assert sum(G.stats().level_lr_ops[l] for l in range(G.stats().n_levels)) > 0
+    r1, r8 = E.apply(x1).cpu().numpy(), E.apply(x8).cpu().numpy()
+    for x, r in ((x1, r1), (x8, r8), (x1, r1)):
+        for _ in range(3):
+            assert _rel(G.apply(x).cpu().numpy(), r) < 1e-6
+    b = G.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
+    xg, ig = G.solve(b, 1e-6)
+    xe, ie = E.solve(b, 1e-6)
+    assert ig.rel_resid_fp64 <= 1e-6 and _rel(xg.cpu().numpy(), xe.cpu().numpy()) < 1e-5
