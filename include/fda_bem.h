@@ -136,14 +136,16 @@ typedef struct {
     int32_t level_lr_rank_max[32];   /* per level: largest retained rank r of those operators */
     float level_lr_rank_mean[32];    /* per level: mean retained rank r of every operator factorised */
     int64_t level_lr_pairs[32];   /* per level: M2L pairs applied in low-rank form */
-    double level_m2l_flops[32];   /* per level: real flops of the M2L pass for one right-hand side, as the
-                                     method performs them (8 T^2 per pair in full form, 8 (2 r T) per pair
-                                     in low-rank form with the operator's own rank r) */
-    double level_m2l_bytes[32];   /* per level: algorithmic bytes of the M2L pass for one right-hand side in
-                                     the chosen precision: every operator applied read once (8 bytes per
-                                     complex entry; T^2, or 2 r T in low-rank form), source densities read
-                                     once, target densities read and written once, and each low-rank pair's
-                                     intermediate written and read once */
+    double level_m2l_flops[32];   /* per level: real flops of the M2L pass for one right-hand side in the
+                                     form the handle's current precision applies (8 T^2 per pair in full
+                                     form, 8 (2 r T) per pair in low-rank form with the operator's own rank r) */
+    double level_m2l_bytes[32];   /* per level, same form: algorithmic bytes for one right-hand side at 8
+                                     bytes per complex value: every operator applied read once (T^2, or
+                                     2 r T in low-rank form), source densities read once, target densities
+                                     read and written once, each low-rank pair's intermediate written and
+                                     read once */
+    int32_t level_lr_tc[32];      /* per level: 1 if the tensor-core path applies the low-rank form there
+                                     (the setup autotuner found it faster than the full form) */
 } fda_stats;
 
 typedef struct fda_handle fda_handle;
@@ -303,7 +305,8 @@ fda_status fda_get_tree(fda_handle *h, int32_t *box_level, int32_t *box_coord, i
  * Steps 2-3 on the tensor cores) for later calls, in place of the
  * autotuner's choice: (columns per tile, 64-row tiles per CTA tile, ring
  * stages) one of (32,1,2), (32,1,4), (64,1,2), (64,1,4), (32,2,4), (64,2,3),
- * (32,3,3), (128,1,3); (0,0,0) returns to the tuned shapes.  A shape with
+ * (32,3,3), (128,1,3), (128,2,2), (64,4,2) (the last two with one
+ * accumulator slot); (0,0,0) returns to the tuned shapes.  A shape with
  * more row tiles than an operator has falls back to one row tile there.
  * Captured graphs are released (the next applies capture again).  Results
  * equal the tuned shapes' up to the rounding order of the float atomics.

@@ -49,7 +49,7 @@ class fda_stats(ctypes.Structure):
                 ("autotune_timed", ctypes.c_int32), ("level_lr_ops", ctypes.c_int32 * 32),
                 ("level_lr_rank_max", ctypes.c_int32 * 32), ("level_lr_rank_mean", ctypes.c_float * 32),
                 ("level_lr_pairs", ctypes.c_int64 * 32), ("level_m2l_flops", ctypes.c_double * 32),
-                ("level_m2l_bytes", ctypes.c_double * 32)]
+                ("level_m2l_bytes", ctypes.c_double * 32), ("level_lr_tc", ctypes.c_int32 * 32)]
 
 
 class fda_sai_config(ctypes.Structure):

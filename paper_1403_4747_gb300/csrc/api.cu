@@ -491,10 +491,14 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
             int64_t lrp = 0;
             for (const lr_bucket &B : h->lr[l]) lrp += B.npairs;
             out->level_lr_pairs[l] = lrp;
-            // algorithmic work of the level's M2L pass, one right-hand side
+            out->level_lr_tc[l] = h->lr_tc[l];
+            // algorithmic work of the level's M2L pass, one right-hand side, in
+            // the form the current precision applies
             const double T = L.T;
             if (T == 0 || L.n_il == 0) continue;
-            const tr_batch &F = h->b_m2l[l];
+            const bool tcpath = h->cfg.precision == FDA_CHOSEN_FP32 && h->have_tc && h->cfg.tensor_cores;
+            const bool lrform = !h->lr[l].empty() && (!tcpath || h->lr_tc[l]);
+            const tr_batch &F = (lrform || h->lr[l].empty()) ? h->b_m2l[l] : h->b_m2l_all[l];
             double fl = 0.0, by = 0.0;
             for (int o = 0; o + 1 < (int)F.op_start.size(); ++o) {
                 const int np = F.op_start[o + 1] - F.op_start[o];
@@ -502,14 +506,15 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
                 fl += 8.0 * T * T * np;
                 by += 8.0 * T * T;
             }
-            for (const lr_bucket &B : h->lr[l]) {
-                for (size_t i = 0; i < B.ops.size(); ++i) {
-                    const double r = rk[B.ops[i]];
-                    const int np = B.b1.op_start[i + 1] - B.b1.op_start[i];
-                    fl += 8.0 * 2.0 * r * T * np;
-                    by += 8.0 * 2.0 * r * T + 2.0 * 8.0 * r * np;
+            if (lrform)
+                for (const lr_bucket &B : h->lr[l]) {
+                    for (size_t i = 0; i < B.ops.size(); ++i) {
+                        const double r = rk[B.ops[i]];
+                        const int np = B.b1.op_start[i + 1] - B.b1.op_start[i];
+                        fl += 8.0 * 2.0 * r * T * np;
+                        by += 8.0 * 2.0 * r * T + 2.0 * 8.0 * r * np;
+                    }
                 }
-            }
             by += 3.0 * 8.0 * L.nbox * L.ncones * T;
             out->level_m2l_flops[l] = fl;
             out->level_m2l_bytes[l] = by;
@@ -637,8 +642,8 @@ fda_status fda_get_tree(fda_handle *h, int32_t *box_level, int32_t *box_coord, i
 fda_status fda_set_tc_tiles(fda_handle *h, int columns, int row_tiles, int stages)
 {
     if (!h) return FDA_ERR_ARG;
-    static const int shapes[8][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4},
-                                     {32, 2, 4}, {64, 2, 3}, {32, 3, 3}, {128, 1, 3}};
+    static const int shapes[10][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4},
+                                      {64, 2, 3}, {32, 3, 3}, {128, 1, 3}, {128, 2, 2}, {64, 4, 2}};
     bool known = columns == 0 && row_tiles == 0 && stages == 0;
     for (const auto &c : shapes) known |= c[0] == columns && c[1] == row_tiles && c[2] == stages;
     if (!known) {

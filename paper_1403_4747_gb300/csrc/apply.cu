@@ -367,14 +367,21 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     if (tc) fda_split_tc(h, h->lev_lo, c32(P.q[h->lev_lo]), h->qs[h->lev_lo], mr);
     mark(3);
     // M2L at every level: p~_target += K~ q~_source
+    // (the CUDA-core forms always apply the low-rank operators of Sec. 4.2
+    // in two stages; the tensor-core form does so where the autotuner found
+    // it faster, else it applies every operator in full)
     for (int l = h->lev_lo; l < h->nlev; ++l) {
-        if (tc)
-            fda_run_tc(h, h->b_m2l[l], h->tc_m2l[l], h->qs[l], P.stride[l] / std::max(1, h->lev[l].T), c32(P.p[l]),
-                       mr, P.stride[l]);
-        else
+        const bool lr = !h->lr[l].empty() && (!tc || (mr == 1 ? h->lr_tc[l] : h->lr_tc_many[l]));
+        if (tc) {
+            tr_batch &F = lr || h->lr[l].empty() ? h->b_m2l[l] : h->b_m2l_all[l];
+            fda_run_tc(h, F, h->tc_m2l[l], h->qs[l], P.stride[l] / std::max(1, h->lev[l].T), c32(P.p[l]), mr,
+                       P.stride[l]);
+        } else {
             fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
                              P.stride[l], s);
-        for (lr_bucket &B : h->lr[l]) lowrank_m2l<R>(h, B, l, P, mr, tc);
+        }
+        if (lr)
+            for (lr_bucket &B : h->lr[l]) lowrank_m2l<R>(h, B, l, P, mr, tc);
     }
     mark(4);
     // L2L top-down: p~_child += L~ p~_parent
@@ -462,8 +469,8 @@ void fda_autotune_tc(fda_handle *h)
     FDA_CUDA(cudaEventCreate(&e1));
     lvl_ptrs<float> P = make_ptrs<float>(h, h->op32, h->q32, h->p32);
     // (columns, row tiles, stages)
-    static const int cand[8][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4}, {64, 2, 3}, {32, 3, 3},
-                                   {128, 1, 3}};
+    static const int cand[10][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4},
+                                    {64, 2, 3}, {32, 3, 3}, {128, 1, 3}, {128, 2, 2}, {64, 4, 2}};
     std::map<std::string, std::array<int, 3>> cache;
     std::string added;
     std::string gpu;
@@ -495,9 +502,9 @@ void fda_autotune_tc(fda_handle *h)
                 bool known = false;
                 for (const auto &k : cand) known |= k[0] == c[0] && k[1] == c[1] && k[2] == c[2];
                 if (known && c[1] <= T.nrt) {
-                    T.nc_tuned = c[0];
-                    T.r_tuned = c[1];
-                    T.st_tuned = c[2];
+                    B.nc_tuned = c[0];
+                    B.r_tuned = c[1];
+                    B.st_tuned = c[2];
                     ++h->autotune_cached;
                     return;
                 }
@@ -517,26 +524,54 @@ void fda_autotune_tc(fda_handle *h)
             }
             if (ms < best) {
                 best = ms;
-                T.nc_tuned = c[0];
-                T.r_tuned = c[1];
-                T.st_tuned = c[2];
+                B.nc_tuned = c[0];
+                B.r_tuned = c[1];
+                B.st_tuned = c[2];
             }
         }
         if (!key.empty())
-            added += key + " " + std::to_string(T.nc_tuned) + " " + std::to_string(T.r_tuned) + " " +
-                     std::to_string(T.st_tuned) + "\n";
+            added += key + " " + std::to_string(B.nc_tuned) + " " + std::to_string(B.r_tuned) + " " +
+                     std::to_string(B.st_tuned) + "\n";
     };
     auto sv = [&](int l) { return P.stride[l] / std::max(1, h->lev[l].T); };
     for (int l = h->lev_lo; l < h->nlev; ++l) {
         if (h->lev[l].T == 0) continue;
         tune("m2l", l, h->b_m2l[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<float *>(P.p[l]), P.stride[l]);
-        for (lr_bucket &B : h->lr[l]) {
-            if (B.npairs == 0) continue;
-            const int64_t per = B.npairs * B.rpad;
-            if (B.t32.bytes < sizeof(c32f) * (size_t)per || B.ts.bytes < 8 * (size_t)per)
-                fda_fail(FDA_ERR_STATE, "low-rank intermediates missing at autotune");
-            tune("lr1", l, B.b1, B.tc1, h->qs[l], sv(l), reinterpret_cast<float *>(B.t32.p), per);
-            tune("lr2", l, B.b2, B.tc2, B.ts, B.npairs, reinterpret_cast<float *>(P.p[l]), P.stride[l]);
+        if (!h->lr[l].empty()) {
+            tune("m2l_all", l, h->b_m2l_all[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<float *>(P.p[l]),
+                 P.stride[l]);
+            for (lr_bucket &B : h->lr[l]) {
+                if (B.npairs == 0) continue;
+                const int64_t per = B.npairs * B.rpad;
+                if (B.t32.bytes < sizeof(c32f) * (size_t)per || B.ts.bytes < 8 * (size_t)per)
+                    fda_fail(FDA_ERR_STATE, "low-rank intermediates missing at autotune");
+                tune("lr1", l, B.b1, B.tc1, h->qs[l], sv(l), reinterpret_cast<float *>(B.t32.p), per);
+                tune("lr2", l, B.b2, B.tc2, B.ts, B.npairs, reinterpret_cast<float *>(P.p[l]), P.stride[l]);
+            }
+            // the level's M2L in full form against the low-rank form (Sec. 4.2),
+            // tuned shapes, for one right-hand side and for max_rhs; the faster
+            // form is kept for each
+            const int mmax = std::max(1, h->cfg.max_rhs);
+            for (int mr = 1; mr <= mmax; mr = mr == mmax ? mmax + 1 : mmax) {
+                float t_full = 0.0f, t_lr = 0.0f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    FDA_CUDA(cudaEventRecord(e0, s));
+                    fda_run_tc(h, h->b_m2l_all[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<c32f *>(P.p[l]),
+                               mr, P.stride[l]);
+                    FDA_CUDA(cudaEventRecord(e1, s));
+                    FDA_CUDA(cudaEventSynchronize(e1));
+                    FDA_CUDA(cudaEventElapsedTime(&t_full, e0, e1));
+                    FDA_CUDA(cudaEventRecord(e0, s));
+                    fda_run_tc(h, h->b_m2l[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<c32f *>(P.p[l]), mr,
+                               P.stride[l]);
+                    for (lr_bucket &B : h->lr[l]) lowrank_m2l<float>(h, B, l, P, mr, true);
+                    FDA_CUDA(cudaEventRecord(e1, s));
+                    FDA_CUDA(cudaEventSynchronize(e1));
+                    FDA_CUDA(cudaEventElapsedTime(&t_lr, e0, e1));
+                }
+                (mr == 1 ? h->lr_tc[l] : h->lr_tc_many[l]) = t_lr < t_full ? 1 : 0;
+                if (mmax == 1) h->lr_tc_many[l] = h->lr_tc[l];
+            }
         }
         if (l + 1 < h->nlev && h->lev[l + 1].T > 0) {
             tune("m2m", l, h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], sv(l + 1), reinterpret_cast<float *>(P.q[l]),

@@ -149,18 +149,20 @@ struct tr_batch {
     int64_t npairs = 0;
     std::vector<int> op_start;  // pairs of operator o: [op_start[o], op_start[o+1])
     std::deque<tile_set> tilesets;  // columns per tile: 64 if an operator averages >= 48, else 32
+    // tensor-core form of the batch: tile lists per (right-hand sides, columns,
+    // row tiles) and the autotuner's shape for one right-hand side (0 = rule)
+    std::deque<tile_set> tc_tilesets;
+    int nc_tuned = 0, r_tuned = 1, st_tuned = 0;
 };
 
-// tensor-core form of one translation batch: the operators as bf16 hi/lo
-// panels (64 complex output rows x 32 complex input columns per panel) and the
-// tiles cut for the current number of right-hand sides
+// tensor-core form of a set of translation operators: bf16 hi/lo panels
+// (64 complex output rows x 32 complex input columns per panel); the tiles
+// and tuned shapes belong to the batch that applies them
 struct tc_ops {
     dbuf A;
     int Tout = 0, Tin = 0;
     int nrt = 0, nkc = 0;     // row tiles (64 complex rows), K stages (32 complex columns)
     int64_t op_bytes = 0;
-    std::deque<tile_set> tilesets;
-    int nc_tuned = 0, r_tuned = 1, st_tuned = 0;  // autotuner's choice for one right-hand side (0 = rule)
 };
 
 // Low-rank reduced M2L operators of one level and rank bucket (Sec. 4.2):
@@ -264,6 +266,12 @@ struct fda_handle {
     std::vector<int> op_rank[FDA_MAX_LEVELS];
     std::vector<int> op_bucket[FDA_MAX_LEVELS];  // bucket of each operator, -1 = full
     std::deque<lr_bucket> lr[FDA_MAX_LEVELS];
+    // levels with low-rank buckets also keep every pair in one full-form
+    // batch; the tensor-core path uses the low-rank form at level l only if
+    // lr_tc[l] (set by the setup autotuner when it is faster)
+    tr_batch b_m2l_all[FDA_MAX_LEVELS];
+    int lr_tc[FDA_MAX_LEVELS] = {};       // one right-hand side
+    int lr_tc_many[FDA_MAX_LEVELS] = {};  // several (decided at max_rhs)
 
     // tensor-core M2L (chosen precision)
     tc_ops tc_m2l[FDA_MAX_LEVELS], tc_m2m[FDA_MAX_LEVELS], tc_l2l[FDA_MAX_LEVELS];

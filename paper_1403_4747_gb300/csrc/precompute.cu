@@ -459,7 +459,7 @@ __global__ void k_diag(const c64d *A, int n, double *d)
 constexpr int QRT = 256;
 
 __global__ void __launch_bounds__(QRT) k_cpqr(c64d *A, int m, int n, int64_t sA, c64d *Q, int64_t sQ, int kmax,
-                                              double tol_rel, int *rank)
+                                              double tol_rel, int *rank, double *colmax2)
 {
     extern __shared__ double qr_smem[];
     double *nrm = qr_smem;                                   // [n]
@@ -508,7 +508,10 @@ __global__ void __launch_bounds__(QRT) k_cpqr(c64d *A, int m, int n, int64_t sA,
                 t2 += coef[w].re;
                 if (red_v[w] > b2 || (red_v[w] == b2 && red_i[w] >= 0 && (i2 < 0 || red_i[w] < i2))) { b2 = red_v[w]; i2 = red_i[w]; }
             }
-            if (k == 0) s_tol2 = tol_rel * tol_rel * fmax(b2, 0.0);
+            if (k == 0) {
+                s_tol2 = tol_rel * tol_rel * fmax(b2, 0.0);
+                if (colmax2) colmax2[blockIdx.x] = fmax(b2, 0.0);
+            }
             s_tot = t2;
             s_piv = i2;
         }
@@ -873,8 +876,9 @@ static void leaf_operators(fda_handle *h, int side)
 // of what remains is at most eps times its largest column norm, gives the
 // row-space basis Q of rank r (Eq. epsk, in the Frobenius norm).  Every
 // factorisation is checked explicitly: ||K~ - U^ V^||_F <= eps times the
-// largest column norm of K~ (a lower bound of sigma_0); an operator that
-// fails the check or needs r >= T/2 stays in full form.  Operators whose
+// larger of the largest column norms of K~ and of C (both lower bounds of
+// sigma_0); an operator that fails the check or needs r >= T/2 stays in full
+// form.  Operators whose
 // two-stage application (rank padded to 32) is cheaper than the full one,
 // both in flops (2 r T < T^2) and in tensor-core tiles (64 rows, 32 of K),
 // are grouped by padded rank.
@@ -912,7 +916,7 @@ static void lowrank_level(fda_handle *h, int l)
     Uall.alloc(sizeof(c64d) * (size_t)nops * T * rcap);
     Qall.alloc(sizeof(c64d) * (size_t)nops * T * rcap);
     const int chunk = std::max(1, std::min(nops, (int)((512ll << 20) / (16ll * T * (2 * sk)))));
-    dbuf Y, Q1, C, rk1, rk2, e2, r2;
+    dbuf Y, Q1, C, rk1, rk2, e2, r2, c2;
     Y.alloc(sizeof(c64d) * (size_t)chunk * T * sk);
     Q1.alloc(sizeof(c64d) * (size_t)chunk * T * sk);
     C.alloc(sizeof(c64d) * (size_t)chunk * T * sk);
@@ -920,10 +924,11 @@ static void lowrank_level(fda_handle *h, int l)
     rk2.alloc(sizeof(int) * chunk);
     e2.alloc(sizeof(double) * chunk);
     r2.alloc(sizeof(double) * chunk);
+    c2.alloc(sizeof(double) * chunk);
     const size_t qsm = sizeof(double) * (sk + (sk & 1)) + sizeof(c64d) * T;
     const c64d *K = h->op64.Kt[l].as<c64d>();
     std::vector<int> hr(chunk);
-    std::vector<double> he(chunk), hq(chunk);
+    std::vector<double> he(chunk), hq(chunk), hc(chunk);
     for (int o0 = 0; o0 < nops; o0 += chunk) {
         const int nb = std::min(chunk, nops - o0);
         std::vector<gemm_job> g1(nb), g2(nb), g3(nb);
@@ -936,12 +941,12 @@ static void lowrank_level(fda_handle *h, int l)
         }
         run_gemm(h, g1, T, sk, T, T, T, T, 0, 0);  // Y = K~ Omega
         k_cpqr<<<nb, QRT, qsm, st>>>(Y.as<c64d>(), T, sk, (int64_t)T * sk, Q1.as<c64d>(), (int64_t)T * sk, sk,
-                                     0.01 * eps, rk1.as<int>());
+                                     0.01 * eps, rk1.as<int>(), nullptr);
         FDA_CHECK_LAUNCH();
         run_gemm(h, g2, T, sk, T, T, T, T, 2, 0);  // C = K~^H Q1
         k_cpqr<<<nb, QRT, qsm, st>>>(C.as<c64d>(), T, sk, (int64_t)T * sk,
                                      Qall.as<c64d>() + (size_t)o0 * T * rcap, (int64_t)T * rcap, rcap, eps,
-                                     rk2.as<int>());
+                                     rk2.as<int>(), c2.as<double>());
         FDA_CHECK_LAUNCH();
         run_gemm(h, g3, T, rcap, T, T, T, T, 0, 0);  // U^ = K~ Q
         k_lr_check<<<nb, QRT, 0, st>>>(K + (size_t)o0 * T * T, Uall.as<c64d>() + (size_t)o0 * T * rcap,
@@ -951,9 +956,12 @@ static void lowrank_level(fda_handle *h, int l)
         FDA_CUDA(cudaMemcpyAsync(hr.data(), rk2.p, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
         FDA_CUDA(cudaMemcpyAsync(he.data(), e2.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
         FDA_CUDA(cudaMemcpyAsync(hq.data(), r2.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        FDA_CUDA(cudaMemcpyAsync(hc.data(), c2.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
         FDA_CUDA(cudaStreamSynchronize(st));
         for (int b = 0; b < nb; ++b) {
-            const bool ok = hr[b] >= 1 && hr[b] <= rcap && std::isfinite(he[b]) && he[b] <= eps * eps * hq[b];
+            // both column maxima (of K~ and of C = K~^H Q1) are lower bounds of sigma_0^2
+            const bool ok = hr[b] >= 1 && hr[b] <= rcap && std::isfinite(he[b]) &&
+                            he[b] <= eps * eps * std::max(hq[b], hc[b]);
             h->op_rank[l][o0 + b] = ok ? hr[b] : -1;
         }
     }

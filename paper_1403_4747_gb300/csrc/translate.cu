@@ -202,6 +202,8 @@ void fda_build_batches(fda_handle *h)
         // stage 1 writing pair p's intermediate at p rpad, stage 2 reading it
         const std::vector<int> &bk = h->op_bucket[l];
         if (!h->lr[l].empty()) {
+            std::vector<pair_rec> all(pr);
+            make_batch(all, std::max(1, L.n_ops), L.T, h->b_m2l_all[l]);
             std::vector<pair_rec> full;
             std::vector<std::vector<pair_rec>> per(h->lr[l].size());
             std::vector<int> local(L.n_ops, -1);  // operator index inside its bucket

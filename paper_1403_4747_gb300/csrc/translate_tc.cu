@@ -82,7 +82,8 @@ __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv
 //   warps 0-3 (epilogue, one warp per TMEM lane quarter): read the slot,
 //       combine real and imaginary parts and add the result to the targets,
 //       then arrive on acce[slot] (count 128) so the slot can be reused.
-// Two accumulator slots (2 R NC TMEM columns each) let the epilogue of tile j
+// Where tensor memory holds two accumulator slots (2 R NC TMEM columns each,
+// 4 R NC <= 512) they let the epilogue of tile j
 // overlap the MMAs of tile j + 1.  Every wait is bounded and also gives up
 // once another role has recorded an error; the CTA then waits (bounded) for
 // its copies and MMAs in flight, frees its tensor memory and returns.
@@ -103,7 +104,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
     constexpr int AR = R * 2 * ABYTES;             // A hi, A lo of each of the R row tiles
     constexpr int STAGE = AR + 4 * BB;             // then Br hi, Bi hi, Br lo, Bi lo
     constexpr int SLOT = R * 2 * NC;               // TMEM columns of one accumulator slot
-    constexpr int TALLOC = 2 * SLOT <= 128 ? 128 : (2 * SLOT <= 256 ? 256 : 512);  // power of two
+    constexpr int NSLOT = 2 * SLOT <= 512 ? 2 : 1; // one slot for the widest tiles (no epilogue overlap)
+    constexpr int TALLOC = NSLOT * SLOT <= 128 ? 128 : (NSLOT * SLOT <= 256 ? 256 : 512);  // power of two
+    static_assert(NSLOT * SLOT <= 512, "accumulators exceed tensor memory");
     static_assert(NC <= NPROD, "one tile column per producer thread");
     float2 *stg = reinterpret_cast<float2 *>(smem + ST * STAGE);  // epilogue staging [EPC][128 lanes]
     __shared__ long long srcv[NC];             // producers: source vector per column of the current tile
@@ -229,8 +232,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
             int g = 0;
             bool ok = true;
             for (int j = 0; j < my_tiles && ok; ++j) {
-                const int slot = j & 1;
-                if (j >= 2 && !mbar_wait_ab(smem_u32(&acce[slot]), ((j - 2) >> 1) & 1, abort_v)) {
+                const int slot = j % NSLOT;
+                if (j >= NSLOT && !mbar_wait_ab(smem_u32(&acce[slot]), ((j - NSLOT) / NSLOT) & 1, abort_v)) {
                     if (!*abort_v) atomicExch(err, 3);
                     *abort_v = 1;
                     break;
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
         // two lanes of its row for EPC / 2 columns and adds them to the target.
         const int row = (warp & 1) * 32 + lane, half = warp >> 1;
         for (int j = 0; j < my_tiles; ++j) {
-            const int slot = j & 1;
+            const int slot = j % NSLOT;
             const tc_tile t = tiles[blockIdx.x + (int64_t)j * gridDim.x];
             asm volatile("bar.sync 2, 128;");  // everyone is done with the previous tgt
             for (int c = tid; c < NC; c += 128) {
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
                 }
                 tgt[c] = v;
             }
-            const bool have = mbar_wait_ab(smem_u32(&accf[slot]), (j >> 1) & 1, abort_v);
+            const bool have = mbar_wait_ab(smem_u32(&accf[slot]), (j / NSLOT) & 1, abort_v);
             if (bar_any(2, 128, !have)) {
                 if (!have && !*abort_v) atomicExch(err, 4);
                 *abort_v = 1;
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
                     asm volatile("bar.sync 2, 128;");
                 }
             }
-            // this slot is read: the MMAs of tile j + 2 may overwrite it
+            // this slot is read: the MMAs of tile j + NSLOT may overwrite it
             asm volatile("tcgen05.fence::before_thread_sync;");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[slot])));
         }
@@ -406,8 +409,9 @@ void launch_tc(const tc_args &a, int ntiles, cudaStream_t s)
         FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         FDA_CUDA(cudaFuncSetAttribute(k_btr_tc<NC, R, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         FDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_btr_tc<NC, R, ST>, WS_THREADS, smem));
-        const int talloc = 4 * R * NC <= 128 ? 128 : (4 * R * NC <= 256 ? 256 : 512);
-        per_sm = std::min(per_sm, 512 / talloc);  // tensor memory: two slots of 2 R NC columns per CTA
+        const int cols = (4 * R * NC <= 512 ? 2 : 1) * 2 * R * NC;  // accumulator slots x slot columns
+        const int talloc = cols <= 128 ? 128 : (cols <= 256 ? 256 : 512);
+        per_sm = std::min(per_sm, 512 / talloc);  // tensor memory per CTA
         if (per_sm < 1) fda_fail(FDA_ERR_CUDA, "tensor-core translation kernel does not fit on an SM");
     }
     const int grid = std::min(ntiles, per_sm * nsm);
@@ -439,7 +443,10 @@ void fda_pack_tc(fda_handle *h)
     for (int l = h->lev_lo; l >= 0 && l < h->nlev; ++l) {
         const level_info &L = h->lev[l];
         if (L.T == 0) continue;
-        pack_one(h, h->tc_m2l[l], h->b_m2l[l], h->op64.Kt[l], L.n_ops, L.T, L.T);
+        // every operator in full form (the batch of all pairs where the level
+        // has low-rank buckets)
+        pack_one(h, h->tc_m2l[l], h->lr[l].empty() ? h->b_m2l[l] : h->b_m2l_all[l], h->op64.Kt[l], L.n_ops, L.T,
+                 L.T);
         if (l + 1 < h->nlev && h->lev[l + 1].T > 0) {
             const int Tc = h->lev[l + 1].T;
             pack_one(h, h->tc_m2m[l], h->b_m2m[l], h->op64.Mt[l], 8 * L.ncones, L.T, Tc);
@@ -494,10 +501,10 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     // tuned one (one right-hand side), else narrow tiles where an operator
     // has few columns, one row tile, four stages
     int NC = avg_cols < 48.0 ? 32 : (avg_cols < 256.0 ? 64 : 128), R = 1, ST = NC == 128 ? 3 : 4;
-    if (mr == 1 && P.nc_tuned) {
-        NC = P.nc_tuned;
-        R = P.r_tuned;
-        ST = P.st_tuned;
+    if (mr == 1 && B.nc_tuned) {
+        NC = B.nc_tuned;
+        R = B.r_tuned;
+        ST = B.st_tuned;
     }
     if (!nc && !rows && !st && h->tc_force[0]) {
         nc = h->tc_force[0];
@@ -507,11 +514,15 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (nc) NC = nc;
     if (rows) R = rows;
     if (st) ST = st;
+    // the instantiated shapes (columns, row tiles, stages):
+    // (32,1,2) (32,1,4) (64,1,2) (64,1,4) (128,1,3) (32,2,4) (64,2,3) (128,2,2) (32,3,3) (64,4,2)
     if (R > P.nrt) R = 1;
-    if (R == 3) NC = 32;  // three row tiles fit tensor memory only with 32 columns
-    if (NC == 128) R = 1, ST = 3;
+    if (R == 3) NC = 32, ST = 3;
+    if (R == 4) NC = 64, ST = 2;
+    if (R == 2) ST = NC == 32 ? 4 : (NC == 64 ? 3 : 2);
+    if (R == 1) ST = NC == 128 ? 3 : (ST == 2 ? 2 : 4);
     const tile_set *ts = nullptr;
-    for (const auto &t : P.tilesets)
+    for (const auto &t : B.tc_tilesets)
         if (t.mr == mr && t.nc == NC && t.rows == R) ts = &t;
     if (!ts) {
         std::vector<tc_tile> tiles;
@@ -520,8 +531,8 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
             for (int p0 = a; p0 < b; p0 += NC)
                 for (int rt = 0; rt < P.nrt; rt += R) tiles.push_back(tc_tile{o, p0, std::min(NC, b - p0), rt});
         }
-        P.tilesets.emplace_back();
-        tile_set &t = P.tilesets.back();
+        B.tc_tilesets.emplace_back();
+        tile_set &t = B.tc_tilesets.back();
         t.mr = mr;
         t.nc = NC;
         t.rows = R;
@@ -534,11 +545,14 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (ts->n == 0) return;
     tc_args a{ts->buf.as<tc_tile>(), B.pairs.as<int2>(), P.A.as<uint8_t>(), P.op_bytes, P.nkc, P.nrt, P.Tout, P.Tin,
               src.as<__nv_bfloat16>(), dst, mr, svstride, dstride, h->tc_err.as<int>()};
-    if (R == 3) {
+    if (R == 4) {
+        launch_tc<64, 4, 2>(a, ts->n, h->stream);
+    } else if (R == 3) {
         launch_tc<32, 3, 3>(a, ts->n, h->stream);
     } else if (R == 2) {
         if (NC == 32) launch_tc<32, 2, 4>(a, ts->n, h->stream);
-        else launch_tc<64, 2, 3>(a, ts->n, h->stream);
+        else if (NC == 64) launch_tc<64, 2, 3>(a, ts->n, h->stream);
+        else launch_tc<128, 2, 2>(a, ts->n, h->stream);
     } else if (NC == 128) {
         launch_tc<128, 1, 3>(a, ts->n, h->stream);
     } else if (NC == 32) {

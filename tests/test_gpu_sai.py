@@ -49,9 +49,15 @@ def test_loss_and_gradient_match_oracle(F, precision, tol_l, tol_g):
 
 def test_trained_network_gain(F):
     """Train on an ellipsoid's leaf blocks, apply to the sphere of the first
-    workload (level 4, k = 5): the loss falls, the preconditioned solve
-    reaches the unpreconditioned solution, and the iteration counts of none,
-    block-diagonal and learned are reported."""
+    workload (level 4, k = 5, alpha = -i/k): the loss falls, the
+    preconditioned solves reach the unpreconditioned solution, and the
+    measured relation of the iteration counts holds: the exact block inverse
+    saves a few iterations (19 against 22 when measured), the learned network
+    saves none (26: its per-pair prediction of the block inverse is close in
+    Frobenius norm on the training geometry, loss 0.06, but not on the sphere,
+    loss 0.23, and not in the directions GMRES needs).  Asserted: the target
+    loss is below that of M = 0 (1.0), block-diagonal needs no more iterations
+    than none, learned at most 6 more than none."""
     import torch
     k, tol = 5.0, 1e-5
     ve, fe = ellipsoid_from_icosphere(4)
@@ -75,6 +81,9 @@ def test_trained_network_gain(F):
         assert rr <= 1.5 * tol
         assert float((x - x0).norm() / x0.norm()) <= 50 * tol
     gain = res["none"][1] - res["learned"][1]
+    assert set_loss < 1.0
+    assert res["blockdiag"][1] <= res["none"][1]
+    assert res["learned"][1] <= res["none"][1] + 6
     print("learned SAI: train loss %.4f -> %.4f (%.2f s), sphere loss %.4f; GMRES iterations none %d, "
           "block-diagonal %d, learned %d (gain %d)" % (rep.loss_init, rep.loss_final, rep.train_s, set_loss,
                                                       res["none"][1], res["blockdiag"][1], res["learned"][1], gain))
