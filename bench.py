@@ -925,6 +925,16 @@ def run_far_field(args):
     t_pat = time.perf_counter() - t0
     Fp = Fp.cpu().numpy()
     err = float(np.linalg.norm(Fp - mie) / np.linalg.norm(mie))
+    # the same pattern through the fast algorithm's upward pass
+    P.far_field(u, dirs[:8], fast=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Ff = P.far_field(u, dirs, fast=True)
+    torch.cuda.synchronize()
+    t_fast = time.perf_counter() - t0
+    Ff = Ff.cpu().numpy()
+    fast = {"ms": t_fast * 1e3, "rel_l2_vs_direct": float(np.linalg.norm(Ff - Fp) / np.linalg.norm(Fp)),
+            "rel_l2_error_vs_mie": float(np.linalg.norm(Ff - mie) / np.linalg.norm(mie))}
     P.close()
     ve, fe = ellipsoid_from_icosphere(7)
     Q = F.FDAProblem(ve, fe, k, precision=F.FDA_CHOSEN_FP32, alpha_sign=args.alpha_sign)
@@ -939,10 +949,43 @@ def run_far_field(args):
             "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "icosphere level 7 (N = 327,680), k = 50, plane wave +z; ellipsoid level 7 "
                                    "reciprocity", "alpha_sign": args.alpha_sign},
-            "pattern_rel_l2_error_vs_mie": err, "solve_iters": info.iters, "solve_s": info.solve_s,
+            "pattern_rel_l2_error_vs_mie": err, "fast_pattern": fast, "solve_iters": info.iters,
+            "solve_s": info.solve_s,
             "reciprocity": {"F(a;d)": [f1.real, f1.imag], "F(-d;-a)": [f2.real, f2.imag],
                             "rel_gap": abs(f1 - f2) / abs(f1)}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile_apply(args):
+    """Profiling harness (--workload profile_apply): setup of the icosphere of
+    --level at --k (chosen form, eager launches), one warm apply of --batch
+    right-hand sides, then one more apply between cudaProfilerStart and
+    cudaProfilerStop, so that `ncu --profile-from-start off` captures exactly
+    the launches of one apply.  Prints one JSON line with the workload."""
+    import torch
+    from paper_1403_4747_gb300 import build as lib_build
+    lib_build.build()
+    import paper_1403_4747_gb300 as F
+    from inputs import icosphere, complex_normal
+    v, f = icosphere(args.level)
+    n = len(f)
+    nrhs = max(1, args.batch)
+    P = F.FDAProblem(v, f, args.k, precision=F.FDA_CHOSEN_FP32, eps=args.eps, max_rhs=nrhs, graphs=0,
+                     lowrank=0 if args.no_lowrank else 1)
+    x = torch.from_numpy(complex_normal(n, seed=77, nrhs=nrhs if nrhs > 1 else None)).cuda()
+    y = torch.empty_like(x)
+    P.apply(x, y)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    P.apply(x, y)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    st = P.stats()
+    print(json.dumps({"workload": "profile_apply", "level": args.level, "N": n, "k": args.k, "nrhs": nrhs,
+                      "lowrank": not args.no_lowrank,
+                      "lowrank_tc_levels": [st.level_lr_tc[l] for l in range(st.n_levels)]}), flush=True)
+    P.close()
     return 0
 
 
@@ -962,6 +1005,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-plain-unpreconditioned", action="store_true")
     ap.add_argument("--no-alt-coupling", action="store_true")
+    ap.add_argument("--no-lowrank", action="store_true", help="profile_apply: Sec. 4.2's low-rank step off")
     ap.add_argument("--no-lowrank-off", action="store_true",
                     help="skip the comparison run with the low-rank M2L step (Sec. 4.2) off")
     ap.add_argument("--alt-plain", action="store_true",
@@ -971,7 +1015,7 @@ def main():
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="sphere_l7_k50", choices=["sphere_l7_k50", "many_meshes", "pulsating", "point_source", "far_field",
-                             "p0_sweep", "precond"],
+                             "p0_sweep", "precond", "profile_apply"],
                     help="many_meshes: the eight-mesh batch; pulsating: the pulsating-sphere study")
     ap.add_argument("--pulsating-max-level", type=int, default=9)
     ap.add_argument("--p0-level", type=int, default=8, help="octahedral sphere level of the p0 study")
@@ -997,6 +1041,8 @@ def main():
         return run_p0_sweep(args)
     if args.workload == "precond":
         return run_precond_study(args)
+    if args.workload == "profile_apply":
+        return run_profile_apply(args)
     return run_native(args)
 
 

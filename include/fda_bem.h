@@ -216,6 +216,19 @@ fda_status fda_far_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, co
                          fda_c128 *F);
 fda_status fda_scattered_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *pts, int64_t npts,
                                fda_c128 *out);
+/* The same far-field pattern F through the fast algorithm's upward pass
+ * (Sec. 3.3 Step 2): the outgoing densities of -D[u] + S[q] (S2M of the
+ * operator for u, S2M of the right-hand side's layers for q, M2M in FP64)
+ * at the coarsest level with interaction lists, whose equivalent sources
+ * phi = V q~ give each box's pattern: F(xh) = (1/(4 pi)) sum over boxes and
+ * equivalent points of phi e^{-ik xh.y} (at a high-frequency level the box's
+ * densities of the cone containing xh).  Elements of leaves above that level
+ * are summed directly.  Accurate to the operator's eps; about (boxes x T +
+ * equivalent points x T) work per direction instead of N x 6.  A non-NULL q
+ * builds the right-hand side's layers on first use, as fda_rhs_neumann.
+ * Arguments, errors and synchronisation as fda_far_field. */
+fda_status fda_far_field_fast(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *dirs, int ndir,
+                              fda_c128 *F);
 
 /* Right-hand side of Eq. eq_bm for a radiating body with given Neumann data
  * q = du/dn (no incident field), the layers of the equation's right-hand

@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
     lib.fda_rhs_point_source.argtypes = [H, vp, cint, vp]
     lib.fda_far_field.argtypes = [H, vp, vp, vp, cint, vp]
     lib.fda_scattered_field.argtypes = [H, vp, vp, vp, i64, vp]
+    lib.fda_far_field_fast.argtypes = [H, vp, vp, vp, cint, vp]
     lib.fda_solve.argtypes = [H, vp, vp, cint, dbl, ctypes.POINTER(fda_info)]
     lib.fda_get_stats.argtypes = [H, ctypes.POINTER(fda_stats)]
     lib.fda_set_timing.argtypes = [H, cint]
@@ -136,7 +137,7 @@ def load(path: str = LIB_PATH):
     lib.fda_destroy.argtypes = [H]
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
-                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_far_field", "fda_scattered_field", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
+                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_far_field", "fda_far_field_fast", "fda_scattered_field", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
                  "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores", "fda_set_tc_tiles",
                  "fda_tree_sizes", "fda_get_tree"):
         getattr(lib, name).restype = cint
@@ -210,6 +211,13 @@ def fda_far_field(h, u_ptr, q_ptr, dirs, F_ptr):
     import numpy as np
     d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
     _check(h, load().fda_far_field(h, u_ptr, q_ptr or None, d.ctypes.data, d.shape[0], F_ptr))
+
+
+def fda_far_field_fast(h, u_ptr, q_ptr, dirs, F_ptr):
+    """Far-field pattern through the fast algorithm's upward pass (same arguments as fda_far_field)."""
+    import numpy as np
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    _check(h, load().fda_far_field_fast(h, u_ptr, q_ptr or None, d.ctypes.data, d.shape[0], F_ptr))
 
 
 def fda_scattered_field(h, u_ptr, q_ptr, points, out_ptr):

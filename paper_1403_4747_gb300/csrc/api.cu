@@ -372,8 +372,12 @@ fda_status field_call(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const
         dbuf dt;
         dt.alloc(sizeof(double) * 3 * ntgt);
         FDA_CUDA(cudaMemcpyAsync(dt.p, tgt, sizeof(double) * 3 * ntgt, cudaMemcpyHostToDevice, h->stream));
-        fda_field(h, reinterpret_cast<const c64d *>(u), reinterpret_cast<const c64d *>(q), dt.as<double>(), ntgt,
-                  far, reinterpret_cast<c64d *>(out));
+        if (far == 2)
+            fda_far_field_upward(h, reinterpret_cast<const c64d *>(u), reinterpret_cast<const c64d *>(q),
+                                 dt.as<double>(), (int)ntgt, reinterpret_cast<c64d *>(out));
+        else
+            fda_field(h, reinterpret_cast<const c64d *>(u), reinterpret_cast<const c64d *>(q), dt.as<double>(),
+                      ntgt, far, reinterpret_cast<c64d *>(out));
         FDA_CUDA(cudaStreamSynchronize(h->stream));
     });
 }
@@ -383,6 +387,12 @@ fda_status fda_far_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, co
                          fda_c128 *F)
 {
     return field_call(h, u, q, dirs, ndir, 1, F, "fda_far_field");
+}
+
+fda_status fda_far_field_fast(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *dirs, int ndir,
+                              fda_c128 *F)
+{
+    return field_call(h, u, q, dirs, ndir, 2, F, "fda_far_field_fast");
 }
 
 fda_status fda_scattered_field(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *pts, int64_t npts,

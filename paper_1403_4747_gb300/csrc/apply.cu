@@ -222,6 +222,12 @@ __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
     }
 }
 
+__global__ void k_add_c64(c64d *a, const c64d *b, int64_t n)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) a[t] = a[t] + b[t];
+}
+
 __global__ void k_c64_to_c32(const c64d *a, c32f *b, int64_t n)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -408,6 +414,51 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
 }
 
 }  // namespace
+
+// Upward pass only, FP64 (Sec. 3.3 Step 2), for the far-field pattern: the
+// outgoing densities q~ of every box from S2M at the leaves (side 0: the
+// double layer of xs; side 1: the single layer, added to what is there) and
+// M2M up to the coarsest level with interaction lists.  xs: Morton order.
+void fda_upward_fp64(fda_handle *h, const c64d *xs, int side, int add)
+{
+    if (h->lev_lo < 0) return;
+    cudaStream_t s = h->stream;
+    lvl_ptrs<double> Q = make_ptrs<double>(h, h->op64, h->q64, h->p64);
+    const dbuf &St = side ? h->op64.St1 : h->op64.St;
+    if (!St.p) fda_fail(FDA_ERR_STATE, "S2M operators of this side were not built");
+    // S2M writes the leaves' q~ into p64 (scratch) when adding, else into q64
+    lvl_ptrs<double> D = Q;
+    if (add)
+        for (int l = 0; l < FDA_MAX_LEVELS; ++l) D.q[l] = Q.p[l];
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        const level_info &L = h->lev[l];
+        if (!L.active || L.T == 0) continue;
+        const size_t bytes = sizeof(c64d) * (size_t)L.nbox * L.ncones * L.T;
+        FDA_CUDA(cudaMemsetAsync(D.q[l], 0, bytes, s));
+    }
+    k_s2m<double><<<h->nleaf, AT, 0, s>>>(D, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(),
+                                          h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
+                                          h->leaf_op_off.as<int64_t>(), St.as<c64d>(), xs, 1, h->N, 1);
+    FDA_CHECK_LAUNCH();
+    if (add)
+        for (int l = h->lev_lo; l < h->nlev; ++l) {
+            const level_info &L = h->lev[l];
+            if (!L.active || L.T == 0) continue;
+            const int64_t n = (int64_t)L.nbox * L.ncones * L.T;
+            k_add_c64<<<fda_blocks(n, 256), 256, 0, s>>>(Q.q[l], D.q[l], n);
+            FDA_CHECK_LAUNCH();
+        }
+}
+
+// M2M bottom-up in FP64 on q64 (after fda_upward_fp64)
+void fda_m2m_fp64(fda_handle *h)
+{
+    if (h->lev_lo < 0) return;
+    lvl_ptrs<double> Q = make_ptrs<double>(h, h->op64, h->q64, h->p64);
+    for (int l = h->nlev - 2; l >= h->lev_lo; --l)
+        fda_run_batch<double>(h->b_m2m[l], Q.Mt[l], h->lev[l].T, h->lev[l + 1].T, Q.q[l + 1], Q.q[l], 1,
+                              Q.stride[l + 1], Q.stride[l], h->stream);
+}
 
 void fda_alloc_densities(fda_handle *h, int want32)
 {

@@ -194,14 +194,26 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_leaf_tc(leaf_args a, leaf_lev
         const int tp = tid - 160;
         int g = 0;
         bool ok = true;
+        // every input item of this thread has the same pair of K in its stage
+        // (LT_NPROD is a multiple of 16): for the near field its two column
+        // indices are fetched one stage ahead, so the gather of x waits on one
+        // memory latency, not two
+        const int kp_b = tp & 15;
         for (int j = 0; j < my_tiles && ok; ++j) {
             const leaf_tile t = a.tiles[blockIdx.x + (int64_t)j * gridDim.x];
             const tile_info f = get_info<KIND>(a, lv, t);
             const int nkc = (f.K + KC - 1) / KC;
             const int rmax = min(64, f.rows - 64 * t.rt);
+            int cn0 = -1, cn1 = -1;  // near field: column elements of the next stage
+            if (KIND == LT_NEAR) {
+                const int k = 2 * kp_b;
+                if (k < f.K) cn0 = __ldg(a.cols + f.c0 + k);
+                if (k + 1 < f.K) cn1 = __ldg(a.cols + f.c0 + k + 1);
+            }
             for (int s = 0; s < nkc; ++s, ++g) {
                 const int b = g % ST;
                 const int k0 = s * KC;
+                const int ce0 = cn0, ce1 = cn1;
                 c32f av[AI][2], bv[BI][2];
 #pragma unroll
                 for (int i = 0; i < AI; ++i) {
@@ -223,9 +235,19 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_leaf_tc(leaf_args a, leaf_lev
                     bv[i][0] = c32f();
                     bv[i][1] = c32f();
                     if (m < a.mr) {
-                        if (k < f.K) bv[i][0] = b_at<KIND>(a, lv, f, k, m);
-                        if (k + 1 < f.K) bv[i][1] = b_at<KIND>(a, lv, f, k + 1, m);
+                        if (KIND == LT_NEAR) {
+                            if (ce0 >= 0) bv[i][0] = a.x[(int64_t)m * a.xstr + ce0];
+                            if (ce1 >= 0) bv[i][1] = a.x[(int64_t)m * a.xstr + ce1];
+                        } else {
+                            if (k < f.K) bv[i][0] = b_at<KIND>(a, lv, f, k, m);
+                            if (k + 1 < f.K) bv[i][1] = b_at<KIND>(a, lv, f, k + 1, m);
+                        }
                     }
+                }
+                if (KIND == LT_NEAR) {
+                    const int k = k0 + KC + 2 * kp_b;
+                    cn0 = k < f.K ? __ldg(a.cols + f.c0 + k) : -1;
+                    cn1 = k + 1 < f.K ? __ldg(a.cols + f.c0 + k + 1) : -1;
                 }
                 const bool fail = g >= ST && !mbar_wait_ab(smem_u32(&empty[b]), ((g - ST) / ST) & 1, abort_v);
                 if (bar_any(1, LT_NPROD, fail)) {

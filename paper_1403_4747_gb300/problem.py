@@ -50,13 +50,15 @@ class FDAProblem:
         _lib.fda_rhs_point_source(self.h, src, b.data_ptr())
         return b[0] if np.ndim(sources) == 1 else b
 
-    def far_field(self, u, dirs, q=None):
-        """Far-field pattern of the scattered field at unit directions (host [M, 3])."""
+    def far_field(self, u, dirs, q=None, fast=False):
+        """Far-field pattern of the scattered field at unit directions (host
+        [M, 3]); fast=True through the fast algorithm's upward pass."""
         import numpy as np
         import torch
         d = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
         F = torch.empty(d.shape[0], dtype=torch.complex128, device="cuda")
-        _lib.fda_far_field(self.h, self._c(u), self._c(q) if q is not None else None, d, F.data_ptr())
+        fn = _lib.fda_far_field_fast if fast else _lib.fda_far_field
+        fn(self.h, self._c(u), self._c(q) if q is not None else None, d, F.data_ptr())
         return F
 
     def scattered_field(self, u, points, q=None):

@@ -74,3 +74,37 @@ def test_reciprocity_from_gpu_solutions():
     f2 = P.far_field(u2, [-d]).cpu().numpy()[0]
     assert abs(f1 - f2) < 7e-3 * abs(f1)  # oracle at level 4: 9.0e-3, first order in h
     P.close()
+
+
+@pytest.mark.parametrize("mesh,k", [("sphere4", 20.0), ("ellipsoid4", 15.0), ("sphere5", 25.0)])
+@pytest.mark.parametrize("with_q", [False, True])
+def test_fast_pattern_matches_direct_and_oracle(mesh, k, with_q):
+    """fda_far_field_fast (the upward pass of the fast algorithm: S2M, M2M,
+    and each box's equivalent sources at the coarsest far-field level, the
+    cone of the direction at a high-frequency level) agrees with the direct
+    six-point sums and the oracle's pattern to the FDA's eps = 1e-4."""
+    from paper_1403_4747_gb300 import FDAProblem
+    level = int(mesh[-1])
+    v, f = icosphere(level) if mesh.startswith("sphere") else ellipsoid_from_icosphere(level)
+    P = FDAProblem(v, f, k)
+    st = P.stats()
+    assert any(st.level_regime[l] == 1 for l in range(st.n_levels)) or level < 5
+    u = complex_normal(len(f), seed=41)
+    q = complex_normal(len(f), seed=42) if with_q else None
+    dirs = fibonacci_directions(61)
+    ud, qd = _dev(u), (_dev(q) if with_q else None)
+    fast = P.far_field(ud, dirs, qd, fast=True).cpu().numpy()
+    direct = P.far_field(ud, dirs, qd).cpu().numpy()
+    ref = oracle.far_field(v, f, k, u, dirs, q=q)
+    assert _rel(fast, direct) < 1e-4 and _rel(fast, ref) < 1e-4
+
+
+def test_fast_pattern_without_far_field_is_the_direct_sum():
+    """A 20-triangle mesh is one leaf (no interaction lists): the fast pattern
+    sums every element directly, equal to fda_far_field to round-off."""
+    from paper_1403_4747_gb300 import FDAProblem
+    v, f = icosphere(0)
+    P = FDAProblem(v, f, 3.0)
+    u = _dev(complex_normal(len(f), seed=43))
+    dirs = fibonacci_directions(9)
+    assert _rel(P.far_field(u, dirs, fast=True).cpu().numpy(), P.far_field(u, dirs).cpu().numpy()) < 1e-13
