@@ -213,7 +213,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     P = F.FDAProblem(v, f, k, stream=stream, precision=F.FDA_CHOSEN_FP32, eps=args.eps,
-                     precond=1 if args.blockdiag else 0, restart=args.restart, max_rhs=max(1, args.batch))
+                     precond=0 if args.no_precond else 1, restart=args.restart, max_rhs=max(1, args.batch))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     st = P.stats()
@@ -403,8 +403,6 @@ def run_native(args):
         b = P.rhs_plane_wave(np.array([0.0, 0.0, 1.0]))
         b_host = b.cpu().numpy()
         runs = [("chosen", F.FDA_CHOSEN_FP32, 0)]
-        if args.blockdiag:
-            runs.append(("chosen_blockdiag", F.FDA_CHOSEN_FP32, 1))
         if not args.no_plain_unpreconditioned:
             runs.append(("plain", F.FDA_PLAIN_FP64, 0))
         for name, prec, pc in runs:
@@ -421,6 +419,8 @@ def run_native(args):
                            "matvec_s": info.matvec_s, "precond": ["none", "blockdiag"][pc]}
         F.fda_set_precision(P.h, F.FDA_CHOSEN_FP32)
         F.fda_set_precond(P.h, 0)
+        if not args.no_precond:
+            solve["preconditioners"] = _precond_block(F, P, b, args)
         if "plain" in solve and solve["chosen"]["solve_s"] > 0:
             solve["speedup_chosen_over_plain"] = solve["plain"]["solve_s"] / solve["chosen"]["solve_s"]
         solve["setup_s"] = setup_s
@@ -510,6 +510,8 @@ def run_native(args):
                      "lowrank_pairs_per_level": [st.level_lr_pairs[l] for l in range(nlev)],
                      "lowrank_rank_mean_per_level": [round(st.level_lr_rank_mean[l], 1) for l in range(nlev)],
                      "lowrank_rank_max_per_level": [st.level_lr_rank_max[l] for l in range(nlev)],
+                     "lowrank_tc_form_per_level": [st.level_lr_tc[l] for l in range(nlev)],
+                     "tc_shape_m2m_m2l_l2l_per_level": [list(st.level_tc_shape[l]) for l in range(nlev)],
                      "device_gb": st.device_bytes / 1e9}}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -517,6 +519,42 @@ def run_native(args):
         P.close()
     group.close()
     return 0
+
+
+def _precond_block(F, P, b, args):
+    """GMRES in the chosen form (the headline's coupling and tolerance) with
+    no preconditioner, the leaf block-diagonal inverse, and the learned
+    network on the near-field pattern trained on this mesh's own near-field
+    matrix (Adam, 64 leaves per step, weights seed 1); times include neither
+    training nor setting M, which are reported beside them."""
+    import torch
+    w = F.fda_sai_init_weights(1)
+    cfg = F.fda_sai_default_config(epochs=args.sai_epochs, pattern=1, sample_leaves=64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = F.fda_sai_train([P.h], cfg, w)
+    train_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    F.fda_sai_set_pattern(P.h, w, 1, want_loss=False)
+    torch.cuda.synchronize()
+    set_s = time.perf_counter() - t0
+    out = {}
+    x_ref = None
+    for name, pc in (("none", 0), ("blockdiag", 1), ("learned_near", 2)):
+        F.fda_set_precond(P.h, pc)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        x, info = P.solve(b, args.tol, raise_on_not_converged=False)
+        torch.cuda.synchronize()
+        if x_ref is None:
+            x_ref = x.clone()
+        out[name] = {"iters": info.iters, "solve_s": time.perf_counter() - ts, "rel_resid_fp64": info.rel_resid_fp64,
+                     "diff_vs_none": float((x - x_ref).norm() / x_ref.norm())}
+    F.fda_set_precond(P.h, 0)
+    out["learned_near_setup"] = {"epochs": args.sai_epochs, "sample_leaves": 64, "loss_init": rep.loss_init,
+                                 "loss_final": rep.loss_final, "train_s": train_s, "set_s": set_s,
+                                 "note": "loss on one fixed draw of 64 leaves, before and after training"}
+    return out
 
 
 def _m2l_traffic(args):
@@ -837,9 +875,10 @@ def run_precond_study(args):
     """Preconditioners at the large size (icosphere level 9, N = 5,242,880,
     k = 200): the learned network trained on the leaf blocks of level 6-8
     spheres and ellipsoids with kD in {50, 100, 200, 300} (weights seed 0),
-    then GMRES to 1e-4 with none, the leaf block-diagonal inverse and the
-    learned preconditioner (chosen form).  Not the headline workload
-    (--workload precond)."""
+    and the network on the near-field pattern trained on the target mesh's
+    own near-field matrix; GMRES to 1e-4 with none, the leaf block-diagonal
+    inverse and both learned preconditioners (chosen form).  Not the
+    headline workload (--workload precond)."""
     import numpy as np
     import torch
     from paper_1403_4747_gb300 import build as lib_build
@@ -869,7 +908,9 @@ def run_precond_study(args):
     b = P.rhs_plane_wave([0.0, 0.0, 1.0])
     res = {}
     x_ref = None
-    for name, pc in (("none", 0), ("blockdiag", 1), ("learned", 2)):
+
+    def run(name, pc):
+        nonlocal x_ref
         F.fda_set_precond(P.h, pc)
         x, info = P.solve(b, 1e-4, raise_on_not_converged=False)
         if x_ref is None:
@@ -877,9 +918,25 @@ def run_precond_study(args):
         res[name] = {"iters": info.iters, "solve_s": round(info.solve_s, 3), "rel_resid": info.rel_resid_fp64,
                      "diff_vs_none": float((x - x_ref).norm() / x_ref.norm())}
         print(json.dumps({name: res[name]}), file=sys.stderr, flush=True)
+
+    for name, pc in (("none", 0), ("blockdiag", 1), ("learned", 2)):
+        run(name, pc)
+    # the network on the near-field pattern, trained on this mesh's own
+    # near-field matrix (64 leaves per Adam step), then M on the whole pattern
+    wn = F.fda_sai_init_weights(1)
+    t0 = time.perf_counter()
+    rep_near = F.fda_sai_train([P.h], F.fda_sai_default_config(epochs=args.sai_epochs, pattern=1,
+                                                                sample_leaves=64), wn)
+    near_train_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    F.fda_sai_set_pattern(P.h, wn, 1, want_loss=False)
+    torch.cuda.synchronize()
+    near_set_s = time.perf_counter() - t0
+    run("learned_near", 2)
     st = P.stats()
     P.close()
-    line = {"metric": "GMRES iterations and solve time at 1e-4: none vs block-diagonal vs learned",
+    line = {"metric": "GMRES iterations and solve time at 1e-4: none vs block-diagonal vs learned (leaf blocks, "
+                      "near field)",
             "value": res["learned"]["solve_s"], "unit": "s", "higher_is_better": False, "n_gpus": 1,
             "dtype": "f32+bf16x3/f64", "data": "synthetic",
             "config": {"workload": "icosphere level %d (N = %d), k = %g, plane wave +z, chosen form"
@@ -887,6 +944,9 @@ def run_precond_study(args):
                        "training": [{"mesh": n, "N": len(m[1]), "k": kk} for n, m, kk in train]},
             "train": {"loss_init": rep.loss_init, "loss_final": rep.loss_final, "train_s": rep.train_s,
                       "setup_and_train_s": train_setup_s},
+            "train_near": {"pattern": "near field, trained on the target mesh", "epochs": args.sai_epochs,
+                           "sample_leaves": 64, "loss_init": rep_near.loss_init, "loss_final": rep_near.loss_final,
+                           "train_s": near_train_s, "set_s": near_set_s},
             "target_loss": set_loss, "setup_s": setup_s, "device_gb": st.device_bytes / 1e9, "solves": res}
     print(json.dumps(line), flush=True)
     return 0
@@ -963,6 +1023,7 @@ def run_profile_apply(args):
     right-hand sides, then one more apply between cudaProfilerStart and
     cudaProfilerStop, so that `ncu --profile-from-start off` captures exactly
     the launches of one apply.  Prints one JSON line with the workload."""
+    import numpy as np
     import torch
     from paper_1403_4747_gb300 import build as lib_build
     lib_build.build()
@@ -973,6 +1034,8 @@ def run_profile_apply(args):
     nrhs = max(1, args.batch)
     P = F.FDAProblem(v, f, args.k, precision=F.FDA_CHOSEN_FP32, eps=args.eps, max_rhs=nrhs, graphs=0,
                      lowrank=0 if args.no_lowrank else 1)
+    if args.tc_tiles:
+        F.fda_set_tc_tiles(P.h, *[int(c) for c in args.tc_tiles.split(",")])
     x = torch.from_numpy(complex_normal(n, seed=77, nrhs=nrhs if nrhs > 1 else None)).cuda()
     y = torch.empty_like(x)
     P.apply(x, y)
@@ -981,10 +1044,22 @@ def run_profile_apply(args):
     P.apply(x, y)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
+    # per-pass device times of five more applies (events on the library stream)
+    F.fda_set_timing(P.h, True)
+    acc = np.zeros(6)
+    for _ in range(5):
+        P.apply(x, y)
+        acc += np.array(F.fda_get_pass_times(P.h))
+    F.fda_set_timing(P.h, False)
     st = P.stats()
     print(json.dumps({"workload": "profile_apply", "level": args.level, "N": n, "k": args.k, "nrhs": nrhs,
-                      "lowrank": not args.no_lowrank,
-                      "lowrank_tc_levels": [st.level_lr_tc[l] for l in range(st.n_levels)]}), flush=True)
+                      "lowrank": not args.no_lowrank, "tc_tiles": args.tc_tiles or "tuned",
+                      "pass_ms": dict(zip(["s2m", "m2m", "m2l", "l2l", "l2t", "near"], (acc / 5).round(4).tolist())),
+                      "lowrank_tc_levels": [st.level_lr_tc[l] for l in range(st.n_levels)],
+                      "tc_shape_m2m_m2l_l2l": [list(st.level_tc_shape[l]) for l in range(st.n_levels)],
+                      "m2l_pairs_per_level": [st.level_m2l_pairs[l] for l in range(st.n_levels)],
+                      "m2l_bytes_per_level": [st.level_m2l_bytes[l] for l in range(st.n_levels)],
+                      "rank_per_level": [st.level_rank[l] for l in range(st.n_levels)]}), flush=True)
     P.close()
     return 0
 
@@ -1006,11 +1081,15 @@ def main():
     ap.add_argument("--no-plain-unpreconditioned", action="store_true")
     ap.add_argument("--no-alt-coupling", action="store_true")
     ap.add_argument("--no-lowrank", action="store_true", help="profile_apply: Sec. 4.2's low-rank step off")
+    ap.add_argument("--tc-tiles", default="", help="profile_apply: force one tensor-core tile shape "
+                    "'columns,row_tiles,stages' (fda_set_tc_tiles) in place of the tuned ones")
     ap.add_argument("--no-lowrank-off", action="store_true",
                     help="skip the comparison run with the low-rank M2L step (Sec. 4.2) off")
     ap.add_argument("--alt-plain", action="store_true",
                     help="also solve the alpha = +i/k problem with the plain FP64 form (about a minute)")
-    ap.add_argument("--blockdiag", action="store_true", help="also solve with the block-diagonal preconditioner")
+    ap.add_argument("--no-precond", action="store_true",
+                    help="skip the preconditioner comparison (block-diagonal, learned near-field) of the solve")
+    ap.add_argument("--sai-epochs", type=int, default=150, help="Adam steps of the learned near-field preconditioner")
     ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--batch", type=int, default=64, help="right-hand sides per pass for the batched measurement")
     ap.add_argument("--no-cpu", action="store_true")

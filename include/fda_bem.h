@@ -57,7 +57,9 @@ typedef enum { FDA_PLAIN_FP64 = 0, FDA_CHOSEN_FP32 = 1 } fda_precision;
 typedef enum { FDA_MODE_FDA = 0, FDA_MODE_DENSE = 1 } fda_mode;
 
 typedef struct {
-    double eps;            /* SVD truncation threshold of Eq. epsg / epsk (default 1e-4) */
+    double eps;            /* SVD truncation threshold of Eq. epsg / epsk (default 1e-4), in [1e-7, 0.1]: the
+                              SVDs are eigendecompositions of Gram matrices G^H G in FP64, which resolve
+                              singular values down to about 1e-8 of the largest, so smaller eps is rejected */
     int p_lf;              /* low-frequency cube surfaces: points per edge (default 8) */
     int p_hf;              /* high-frequency equivalent sphere: points per cube edge before projection (10) */
     int hf_nr;             /* high-frequency cone sampling: radial shells (5) */
@@ -144,8 +146,13 @@ typedef struct {
                                      2 r T in low-rank form), source densities read once, target densities
                                      read and written once, each low-rank pair's intermediate written and
                                      read once */
-    int32_t level_lr_tc[32];      /* per level: 1 if the tensor-core path applies the low-rank form there
-                                     (the setup autotuner found it faster than the full form) */
+    int32_t level_lr_tc[32];      /* per level: bit 0 set if the tensor-core path applies the low-rank form
+                                     there to one right-hand side, bit 1 if to several (the setup autotuner
+                                     found it faster than the full form, at one and at max_rhs columns) */
+    int32_t level_tc_shape[32][3]; /* per level: tile shape the setup autotuner chose for the tensor-core
+                                      M2M (from level l+1 into l), M2L (the full-form batch) and L2L (from
+                                      l into l+1) at one right-hand side, as columns * 100 + row tiles * 10
+                                      + stages; 0 if not tuned */
 } fda_stats;
 
 typedef struct fda_handle fda_handle;
@@ -154,7 +161,7 @@ typedef struct fda_handle fda_handle;
 void fda_default_config(fda_config *cfg);
 
 /* Create a handle.  cfg (host) is copied.  Returns FDA_ERR_ARG for invalid
- * settings (eps outside (0, 0.1], leaf_max outside [1, 64], ...). */
+ * settings (eps outside [1e-7, 0.1], leaf_max outside [1, 64], ...). */
 fda_status fda_create(const fda_config *cfg, fda_handle **out);
 
 /* Sec. 3.3 Step 1 (setup, first part): copy the mesh (host pointers) to the
@@ -223,7 +230,9 @@ fda_status fda_scattered_field(fda_handle *h, const fda_c128 *u, const fda_c128 
  * phi = V q~ give each box's pattern: F(xh) = (1/(4 pi)) sum over boxes and
  * equivalent points of phi e^{-ik xh.y} (at a high-frequency level the box's
  * densities of the cone containing xh).  Elements of leaves above that level
- * are summed directly.  Accurate to the operator's eps; about (boxes x T +
+ * are summed directly.  Accurate to a few times the operator's eps (a
+ * high-frequency cone's densities are fitted on check points out to the
+ * body's size, and the pattern extrapolates them to infinity); about (boxes x T +
  * equivalent points x T) work per direction instead of N x 6.  A non-NULL q
  * builds the right-hand side's layers on first use, as fda_rhs_neumann.
  * Arguments, errors and synchronisation as fda_far_field. */
@@ -329,7 +338,8 @@ fda_status fda_set_tc_tiles(fda_handle *h, int columns, int row_tiles, int stage
 /* Select the preconditioner used by later fda_solve calls: 0 none, 1 leaf
  * block-diagonal (needs a handle created with precond = 1, which builds the
  * block inverses during fda_precompute_translations; else FDA_ERR_STATE),
- * 2 learned SAI (needs fda_sai_set first; else FDA_ERR_STATE). */
+ * 2 learned SAI (needs fda_sai_set or fda_sai_set_pattern first; else
+ * FDA_ERR_STATE; the pattern last set is used). */
 fda_status fda_set_precond(fda_handle *h, int precond);
 
 /* Tree, list and operator statistics (host struct). */
@@ -344,7 +354,8 @@ fda_status fda_get_pass_times(fda_handle *h, float out[6]);
 
 /* ---- Learned sparse approximate inverse (SAI) preconditioner ----
  * Not in the paper (which solves unpreconditioned, Sec. 5.3): a right
- * preconditioner M on the leaf-block pattern (i, j in the same leaf) whose
+ * preconditioner M on the leaf-block pattern (i, j in the same leaf; the
+ * near-field pattern is below, fda_sai_set_pattern) whose
  * entries a small network predicts from the pair's local geometry and k
  * (8 rotation-invariant features: k|x_j - x_i|, the two normal projections of
  * the unit separation, n_i.n_j, k sqrt(area_i), k sqrt(area_j), [i == j],
@@ -355,9 +366,12 @@ fda_status fda_get_pass_times(fda_handle *h, float out[6]);
  * fda_precompute_translations built.  Weights are fda_sai_num_params() floats,
  * caller-owned, layout W1[32][8], b1[32], W2[32][32], b2[32], W3[2][32], b3[2]. */
 typedef struct {
-    int epochs;               /* full-batch Adam steps (default 400) */
+    int epochs;               /* Adam steps (default 400) */
     double lr;                /* Adam step size (default 3e-3) */
-    unsigned long long seed;  /* seed of fda_sai_init_weights used by callers (default 1) */
+    unsigned long long seed;  /* seed of fda_sai_init_weights used by callers, and of the leaf
+                                 draws of pattern 1 (default 1) */
+    int pattern;              /* 0: leaf blocks, full batch (default); 1: near-field pattern */
+    int sample_leaves;        /* pattern 1: leaves drawn from each handle per step (default 256) */
 } fda_sai_config;
 
 typedef struct {
@@ -370,7 +384,8 @@ int fda_sai_num_params(void);
 fda_status fda_sai_default_config(fda_sai_config *cfg);
 /* Xavier-uniform weights from splitmix64(seed), zero biases (host). */
 fda_status fda_sai_init_weights(unsigned long long seed, float *weights);
-/* Train on the leaf blocks of nhandles precomputed handles (their own
+/* Train on the leaf blocks (cfg->pattern 0) or the near-field pattern
+ * (cfg->pattern 1, below) of nhandles precomputed handles (their own
  * near-field matrices, FP32 kernels on the first handle's stream).  weights:
  * host, in = initial, out = trained.  FDA_ERR_STATE before precompute,
  * FDA_ERR_NUMERIC if the loss stops being finite; message on handles[0]. */
@@ -380,6 +395,32 @@ fda_status fda_sai_train(fda_handle *const *handles, int nhandles, const fda_sai
  * preconditioner (select it with fda_set_precond(h, 2)).  loss (optional,
  * host) receives L of the stored M against the FP64 blocks. */
 fda_status fda_sai_set(fda_handle *h, const float *weights, double *loss);
+/* The same network on the near-field pattern.  For pattern 1 it predicts
+ * M_ij for every row i of a leaf B and every column j of B's near-field
+ * columns C_B (the leaf's own elements and those of its near leaves, the
+ * columns of the near-field matrix's rows of B), and training minimises
+ *     L = (1/sum_B n_B) sum_B ||M[B, C_B] A_near[C_B, C_B] - I[B, C_B]||_F^2,
+ * A_near the near-field matrix (a row l of leaf C holds C's own near-field
+ * columns, 0 elsewhere), by Adam on sample_leaves leaves of each handle per
+ * step (loss_init / loss_final: L on one fixed draw of that many leaves per
+ * handle, before and after).
+ *   - fda_sai_set_pattern: pattern 0 is fda_sai_set; pattern 1 evaluates M on
+ *     h's whole near-field pattern (FP32, nnz_near entries, the near-field
+ *     matrix's layout) and keeps it as h's learned preconditioner, applied
+ *     by the near-field product (select with fda_set_precond(h, 2)).  loss
+ *     (optional, host) receives L over all leaves of h in FP32 (pattern 1)
+ *     or as fda_sai_set (pattern 0).  FDA_ERR_ARG for another pattern.
+ *   - fda_sai_loss_grad_near: L and dL/dweights (fda_sai_num_params()
+ *     doubles, host) over the leaves leaves[0 .. nleaves) of h (indices into
+ *     h's leaf list, as fda_get_tree's leaf_box; host), normalised by their
+ *     rows; precision FDA_PLAIN_FP64 runs the FP64 kernels on h's FP64
+ *     near-field matrix, FDA_CHOSEN_FP32 the FP32 training kernels (weights
+ *     rounded to FP32).  FDA_ERR_STATE before precompute; FDA_ERR_ARG for
+ *     indices out of range.
+ * Both need leaves of at most 64 elements (FDA_ERR_ARG otherwise). */
+fda_status fda_sai_set_pattern(fda_handle *h, const float *weights, int pattern, double *loss);
+fda_status fda_sai_loss_grad_near(fda_handle *h, const double *weights, int nleaves, const int32_t *leaves,
+                                  int precision, double *loss, double *grad);
 /* Loss L and gradient dL/dweights (fda_sai_num_params() doubles) of the
  * training kernels for caller-supplied data (host arrays, copied in): n elements
  * with centroids [n][3], normals [n][3], areas [n], wavenumber k; nblocks
@@ -461,6 +502,12 @@ int fda_cone_symmetry_table(int nc, int *rep, int *g);
  * region is the launches made inside it; a CUDA-graph replay counts the
  * kernels the graph holds).  Never fails. */
 long long fda_launch_count(void);
+
+/* Size in bytes of a public struct, for bindings to check their copy of
+ * its layout: which = 0 fda_config, 1 fda_info, 2 fda_stats,
+ * 3 fda_sai_config, 4 fda_sai_report, 5 fda_batch_stats; 0 for any other
+ * value.  Never fails. */
+size_t fda_struct_size(int which);
 
 /* Message of the last failing call on this handle (never NULL). */
 const char *fda_last_error(const fda_handle *h);

@@ -49,11 +49,13 @@ class fda_stats(ctypes.Structure):
                 ("autotune_timed", ctypes.c_int32), ("level_lr_ops", ctypes.c_int32 * 32),
                 ("level_lr_rank_max", ctypes.c_int32 * 32), ("level_lr_rank_mean", ctypes.c_float * 32),
                 ("level_lr_pairs", ctypes.c_int64 * 32), ("level_m2l_flops", ctypes.c_double * 32),
-                ("level_m2l_bytes", ctypes.c_double * 32), ("level_lr_tc", ctypes.c_int32 * 32)]
+                ("level_m2l_bytes", ctypes.c_double * 32), ("level_lr_tc", ctypes.c_int32 * 32),
+                ("level_tc_shape", (ctypes.c_int32 * 3) * 32)]
 
 
 class fda_sai_config(ctypes.Structure):
-    _fields_ = [("epochs", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+    _fields_ = [("epochs", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_ulonglong),
+                ("pattern", ctypes.c_int), ("sample_leaves", ctypes.c_int)]
 
 
 class fda_sai_report(ctypes.Structure):
@@ -112,8 +114,10 @@ def load(path: str = LIB_PATH):
     lib.fda_sai_train.argtypes = [vp, cint, ctypes.POINTER(fda_sai_config), vp, ctypes.POINTER(fda_sai_report)]
     lib.fda_sai_set.argtypes = [H, vp, vp]
     lib.fda_sai_loss_grad.argtypes = [i64, vp, vp, vp, dbl, cint, vp, vp, vp, vp, cint, vp, vp]
+    lib.fda_sai_set_pattern.argtypes = [H, vp, cint, vp]
+    lib.fda_sai_loss_grad_near.argtypes = [H, vp, cint, vp, cint, vp, vp]
     for name in ("fda_sai_default_config", "fda_sai_init_weights", "fda_sai_train", "fda_sai_set",
-                 "fda_sai_loss_grad"):
+                 "fda_sai_loss_grad", "fda_sai_set_pattern", "fda_sai_loss_grad_near"):
         getattr(lib, name).restype = cint
     B = ctypes.c_void_p
     lib.fda_create_batch.argtypes = [ctypes.POINTER(fda_config), cint, ctypes.POINTER(B)]
@@ -134,6 +138,12 @@ def load(path: str = LIB_PATH):
     lib.fda_launch_count.restype = ctypes.c_longlong
     lib.fda_last_error.argtypes = [H]
     lib.fda_last_error.restype = ctypes.c_char_p
+    lib.fda_struct_size.argtypes = [cint]
+    lib.fda_struct_size.restype = ctypes.c_size_t
+    for which, cls in enumerate((fda_config, fda_info, fda_stats, fda_sai_config, fda_sai_report, fda_batch_stats)):
+        if lib.fda_struct_size(which) != ctypes.sizeof(cls):
+            raise ImportError("%s: the library's struct has %d bytes, this binding's %d"
+                              % (cls.__name__, lib.fda_struct_size(which), ctypes.sizeof(cls)))
     lib.fda_destroy.argtypes = [H]
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
@@ -350,6 +360,30 @@ def fda_sai_set(h, weights) -> float:
     loss = ctypes.c_double()
     _check(h, load().fda_sai_set(h, weights.ctypes.data, ctypes.byref(loss)))
     return loss.value
+
+
+def fda_sai_set_pattern(h, weights, pattern, want_loss=True):
+    """Evaluate the network on h's leaf blocks (pattern 0) or its whole
+    near-field pattern (pattern 1) as its learned preconditioner; returns the
+    loss (None without want_loss)."""
+    import numpy as np
+    assert weights.dtype == np.float32 and weights.flags.c_contiguous
+    loss = ctypes.c_double()
+    _check(h, load().fda_sai_set_pattern(h, weights.ctypes.data, int(pattern),
+                                         ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def fda_sai_loss_grad_near(h, weights, leaves, precision=FDA_PLAIN_FP64):
+    """Loss and gradient of the near-field objective over the given leaves of h."""
+    import numpy as np
+    W = np.ascontiguousarray(weights, dtype=np.float64)
+    lv = np.ascontiguousarray(leaves, dtype=np.int32)
+    loss = ctypes.c_double()
+    grad = np.zeros(fda_sai_num_params(), dtype=np.float64)
+    _check(h, load().fda_sai_loss_grad_near(h, W.ctypes.data, len(lv), lv.ctypes.data, precision,
+                                            ctypes.byref(loss), grad.ctypes.data))
+    return loss.value, grad
 
 
 def fda_sai_loss_grad(cent, nrm, area, k, block_ptr, block_elems, blocks, weights, precision=FDA_PLAIN_FP64):

@@ -134,7 +134,7 @@ fda_status fda_create(const fda_config *cfg, fda_handle **out)
     *out = nullptr;
     fda_config c;
     if (cfg) c = *cfg; else fda_default_config(&c);
-    if (!(c.eps > 0 && c.eps <= 0.1) || c.leaf_max < 1 || c.leaf_max > 64 || c.p_lf < 3 || c.p_lf > 16 ||
+    if (!(c.eps >= 1e-7 && c.eps <= 0.1) || c.leaf_max < 1 || c.leaf_max > 64 || c.p_lf < 3 || c.p_lf > 16 ||
         c.p_hf < 3 || c.p_hf > 16 || c.hf_nr < 1 || c.hf_na < 8 || !(c.hf_wavelengths > 0) || !(c.rho_min >= 2.0) ||
         (c.precision != FDA_PLAIN_FP64 && c.precision != FDA_CHOSEN_FP32) ||
         (c.mode != FDA_MODE_FDA && c.mode != FDA_MODE_DENSE) || c.restart < 1 || c.restart > 255 || c.maxit < 1 || c.precond < 0 ||
@@ -501,7 +501,14 @@ fda_status fda_get_stats(fda_handle *h, fda_stats *out)
             int64_t lrp = 0;
             for (const lr_bucket &B : h->lr[l]) lrp += B.npairs;
             out->level_lr_pairs[l] = lrp;
-            out->level_lr_tc[l] = h->lr_tc[l];
+            out->level_lr_tc[l] = h->lr_tc[l] | (h->lr_tc_many[l] << 1);
+            {
+                auto code = [](const tr_batch &B) { return B.nc_tuned ? B.nc_tuned * 100 + B.r_tuned * 10 + B.st_tuned : 0; };
+                const tr_batch &F = !h->lr[l].empty() && !h->lr_tc[l] ? h->b_m2l_all[l] : h->b_m2l[l];
+                out->level_tc_shape[l][0] = l + 1 < h->nlev ? code(h->b_m2m[l]) : 0;
+                out->level_tc_shape[l][1] = code(F);
+                out->level_tc_shape[l][2] = l + 1 < h->nlev ? code(h->b_l2l[l]) : 0;
+            }
             // algorithmic work of the level's M2L pass, one right-hand side, in
             // the form the current precision applies
             const double T = L.T;
@@ -680,8 +687,8 @@ fda_status fda_set_precond(fda_handle *h, int precond)
         h->err = "block-diagonal preconditioner was not built (create the handle with precond = 1)";
         return FDA_ERR_STATE;
     }
-    if (precond == 2 && !h->sai_M.p) {
-        h->err = "learned preconditioner not set (call fda_sai_set first)";
+    if (precond == 2 && !h->sai_M.p && !h->sai_M32.p) {
+        h->err = "learned preconditioner not set (call fda_sai_set or fda_sai_set_pattern first)";
         return FDA_ERR_STATE;
     }
     h->cfg.precond = precond;
@@ -728,12 +735,27 @@ void fda_destroy(fda_handle *h)
 
 extern "C" int fda_sai_num_params(void) { return fda_sai_nparams(); }
 
+extern "C" size_t fda_struct_size(int which)
+{
+    switch (which) {
+    case 0: return sizeof(fda_config);
+    case 1: return sizeof(fda_info);
+    case 2: return sizeof(fda_stats);
+    case 3: return sizeof(fda_sai_config);
+    case 4: return sizeof(fda_sai_report);
+    case 5: return sizeof(fda_batch_stats);
+    default: return 0;
+    }
+}
+
 extern "C" fda_status fda_sai_default_config(fda_sai_config *c)
 {
     if (!c) return FDA_ERR_ARG;
     c->epochs = 400;
     c->lr = 3e-3;
     c->seed = 1;
+    c->pattern = 0;
+    c->sample_leaves = 256;
     return FDA_OK;
 }
 
@@ -747,7 +769,9 @@ extern "C" fda_status fda_sai_init_weights(unsigned long long seed, float *weigh
 extern "C" fda_status fda_sai_train(fda_handle *const *handles, int nhandles, const fda_sai_config *cfg,
                                     float *weights, fda_sai_report *rep)
 {
-    if (!handles || nhandles < 1 || !cfg || !weights || cfg->epochs < 0 || !(cfg->lr > 0)) return FDA_ERR_ARG;
+    if (!handles || nhandles < 1 || !cfg || !weights || cfg->epochs < 0 || !(cfg->lr > 0) ||
+        (cfg->pattern != 0 && cfg->pattern != 1) || (cfg->pattern == 1 && cfg->sample_leaves < 1))
+        return FDA_ERR_ARG;
     for (int q = 0; q < nhandles; ++q) {
         if (!handles[q]) return FDA_ERR_ARG;
         if (handles[q]->state != 2) {
@@ -757,7 +781,11 @@ extern "C" fda_status fda_sai_train(fda_handle *const *handles, int nhandles, co
     }
     return guarded(handles[0], [&] {
         double l0 = 0, l1 = 0, ts = 0;
-        fda_sai_train_impl(handles, nhandles, cfg->epochs, cfg->lr, weights, &l0, &l1, &ts);
+        if (cfg->pattern == 1)
+            fda_sai_train_near_impl(handles, nhandles, cfg->epochs, cfg->lr, cfg->sample_leaves, cfg->seed, weights,
+                                    &l0, &l1, &ts);
+        else
+            fda_sai_train_impl(handles, nhandles, cfg->epochs, cfg->lr, weights, &l0, &l1, &ts);
         if (rep) {
             rep->loss_init = l0;
             rep->loss_final = l1;
@@ -776,6 +804,40 @@ extern "C" fda_status fda_sai_set(fda_handle *h, const float *weights, double *l
     return guarded(h, [&] {
         double l = fda_sai_set_impl(h, weights);
         if (loss) *loss = l;
+    });
+}
+
+extern "C" fda_status fda_sai_set_pattern(fda_handle *h, const float *weights, int pattern, double *loss)
+{
+    if (!h || !weights || (pattern != 0 && pattern != 1)) return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = "fda_sai_set_pattern needs fda_precompute_translations first";
+        return FDA_ERR_STATE;
+    }
+    return guarded(h, [&] {
+        const double l = pattern == 1 ? fda_sai_set_near_impl(h, weights, loss != nullptr)
+                                      : fda_sai_set_impl(h, weights);
+        if (loss) *loss = l;
+    });
+}
+
+extern "C" fda_status fda_sai_loss_grad_near(fda_handle *h, const double *weights, int nleaves,
+                                             const int32_t *leaves, int precision, double *loss, double *grad)
+{
+    if (!h || !weights || nleaves < 1 || !leaves || !loss || !grad ||
+        (precision != FDA_PLAIN_FP64 && precision != FDA_CHOSEN_FP32))
+        return FDA_ERR_ARG;
+    if (h->state != 2) {
+        h->err = "fda_sai_loss_grad_near needs fda_precompute_translations first";
+        return FDA_ERR_STATE;
+    }
+    for (int b = 0; b < nleaves; ++b)
+        if (leaves[b] < 0 || leaves[b] >= h->nleaf) {
+            h->err = "leaf index out of range";
+            return FDA_ERR_ARG;
+        }
+    return guarded(h, [&] {
+        fda_sai_loss_grad_near_impl(h, weights, nleaves, leaves, precision == FDA_CHOSEN_FP32, loss, grad);
     });
 }
 

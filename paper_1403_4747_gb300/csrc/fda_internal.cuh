@@ -240,7 +240,8 @@ struct fda_handle {
     // near-field lists (CSR over leaves): source element ranges
     dbuf nr_ptr, nr_begin, nr_end;
     dbuf nf_colptr;            // int64 [nleaf+1]: column offsets per leaf
-    dbuf nf_cols;              // int32 [total cols]: sorted source element of each column
+    dbuf nf_cols;              // int32 [total cols]: source element of each column (the leaf's near
+                               // ranges one after another, in list order, each in element order)
     dbuf nf_off;               // int64 [nleaf+1]: entry offsets per leaf block
     int64_t nnz_near = 0, ncols_total = 0;
 
@@ -299,8 +300,11 @@ struct fda_handle {
 
     // leaf block-diagonal preconditioner (row-major n_B x n_B per leaf)
     dbuf pc_M, pc_off;
-    // learned SAI preconditioner on the same pattern (set by fda_sai_set)
-    dbuf sai_M, sai_off;
+    // learned SAI preconditioner: on the leaf-block pattern (sai_M, FP64,
+    // row-major n_B x n_B per leaf) or on the near-field pattern (sai_M32,
+    // FP32, the near-field matrix's layout); sai_pattern says which is set
+    dbuf sai_M, sai_off, sai_M32;
+    int sai_pattern = 0;
 
     // captured applies (one CUDA graph per precision, right-hand sides and
     // tensor-core switch), replayed on gstream joined to stream by events
@@ -377,6 +381,14 @@ double fda_sai_set_impl(fda_handle *h, const float *W);
 void fda_sai_loss_grad_impl(int64_t n, const double *cent, const double *nrm, const double *area, double k, int nb,
                             const int64_t *bptr, const int32_t *belem, const c64d *A, const double *W, int fp32,
                             double *loss, double *grad);
+void fda_sai_train_near_impl(fda_handle *const *hs, int nh, int epochs, double lr, int per_step, uint64_t seed,
+                             float *W, double *loss0, double *loss1, double *train_s);
+double fda_sai_set_near_impl(fda_handle *h, const float *W, bool want_loss);
+void fda_sai_loss_grad_near_impl(fda_handle *h, const double *W, int nleaves, const int32_t *leaves, int fp32,
+                                 double *loss, double *grad);
+// z = A x over the near-field pattern for an FP32 matrix A in the near-field
+// matrix's layout (one right-hand side, FP64 vectors)
+void fda_near_product_f32(fda_handle *h, const c32f *A, const c64d *x, c64d *z);
 void fda_pack_tc(fda_handle *h);
 // split nvec FP32 vectors of length T into bf16 hi/lo (the gather layout of the tensor-core kernel)
 void fda_split_vectors(fda_handle *h, const c32f *src, int64_t nvec, int T, dbuf &out);

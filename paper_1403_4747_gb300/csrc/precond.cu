@@ -180,6 +180,11 @@ void fda_precond_build(fda_handle *h)
 void fda_precond_apply(fda_handle *h, const c64d *r, c64d *z)
 {
     const bool learned = h->cfg.precond == 2;
+    if (learned && h->sai_pattern == 1) {
+        // learned M on the near-field pattern: the near-field product with M
+        fda_near_product_f32(h, h->sai_M32.as<c32f>(), r, z);
+        return;
+    }
     k_blockdiag_apply<<<h->nleaf, PT, 0, h->stream>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                       h->box_end.as<int32_t>(),
                                                       (learned ? h->sai_off : h->pc_off).as<int64_t>(),

@@ -35,16 +35,20 @@ constexpr int OW1 = 0, OB1 = OW1 + SH * SF, OW2 = OB1 + SH, OB2 = OW2 + SH * SH,
               OB3 = OW3 + 2 * SH, SP = OB3 + 2;  // parameter layout, SP = 1410
 constexpr int BT = 128;                          // threads per CTA in the per-entry kernels
 
-// blocks of one problem: element geometry, the elements of each block and
-// the offsets of each block's n_B x n_B row-major entries
+// blocks of one problem: element geometry, the row elements and the column
+// elements of each block (the same list for the leaf-block pattern, the
+// leaf's near-field columns for the near-field pattern) and the offsets of
+// each block's n_B x nc_B row-major entries
 struct sai_set {
     const double *cent, *nrm, *area;  // [n][3], [n][3], [n]
-    const int64_t *bptr;              // [nb + 1] into belem
+    const int64_t *bptr;              // [nb + 1] into belem (rows)
     const int32_t *belem;
+    const int64_t *cptr;              // [nb + 1] into celem (columns)
+    const int32_t *celem;
     const int64_t *moff;              // [nb + 1] entry offsets
     double k;
     int nb;
-    int maxn;                         // largest block
+    int maxn;                         // most rows of a block
 };
 
 template <typename T>
@@ -89,10 +93,16 @@ __device__ inline void sai_forward_entry(const T *W, const T f[SF], T h1[SH], T 
 // entry e of block b -> (row element, column element)
 __device__ inline void sai_entry(const sai_set &S, int b, int e, int &i, int &j)
 {
-    const int64_t p0 = S.bptr[b];
-    const int n = (int)(S.bptr[b + 1] - p0);
-    i = S.belem[p0 + e / n];
-    j = S.belem[p0 + e % n];
+    const int64_t c0 = S.cptr[b];
+    const int nc = (int)(S.cptr[b + 1] - c0);
+    i = S.belem[S.bptr[b] + e / nc];
+    j = S.celem[c0 + e % nc];
+}
+
+// entries of block b
+__device__ inline int sai_count(const sai_set &S, int b)
+{
+    return (int)(S.bptr[b + 1] - S.bptr[b]) * (int)(S.cptr[b + 1] - S.cptr[b]);
 }
 
 // M = network(features) on every entry of every block (one CTA per block)
@@ -103,8 +113,8 @@ __global__ void __launch_bounds__(BT) k_sai_forward(sai_set S, const T *Wg, cx<T
     for (int p = threadIdx.x; p < SP; p += BT) W[p] = Wg[p];
     __syncthreads();
     const int b = blockIdx.x;
-    const int n = (int)(S.bptr[b + 1] - S.bptr[b]);
-    for (int e = threadIdx.x; e < n * n; e += BT) {
+    const int ne = sai_count(S, b);
+    for (int e = threadIdx.x; e < ne; e += BT) {
         int i, j;
         sai_entry(S, b, e, i, j);
         T f[SF], h1[SH], h2[SH], o[2];
@@ -178,11 +188,11 @@ __global__ void __launch_bounds__(BT) k_sai_backward(sai_set S, const T *Wg, con
     __syncthreads();
     const int t = threadIdx.x;
     for (int b = blockIdx.x; b < S.nb; b += gridDim.x) {
-        const int n = (int)(S.bptr[b + 1] - S.bptr[b]);
-        for (int e0 = 0; e0 < n * n; e0 += BT) {
+        const int ne = sai_count(S, b);
+        for (int e0 = 0; e0 < ne; e0 += BT) {
             const int e = e0 + t;
-            const int cnt = min(BT, n * n - e0);
-            if (e < n * n) {
+            const int cnt = min(BT, ne - e0);
+            if (e < ne) {
                 int i, j;
                 sai_entry(S, b, e, i, j);
                 T f[SF], h1[SH], h2[SH], o[2];
@@ -254,6 +264,242 @@ __global__ void k_sai_adam(float *W, const float *g, float *m1, float *m2, float
     m1[p] = b1 * m1[p] + (1.0f - b1) * gp;
     m2[p] = b2 * m2[p] + (1.0f - b2) * gp * gp;
     W[p] -= lr * (m1[p] / c1) / (sqrtf(m2[p] / c2) + eps);
+}
+
+// ---- near-field pattern: M[B, C_B] for the rows of leaf B and its near-field
+// columns C_B (whole leaves, element order); the objective compares
+// M[B, C_B] A_near[C_B, C_B] with I[B, C_B], where a row l of A_near (in leaf
+// C) holds the entries of C's own near-field columns and 0 elsewhere
+
+// the handle's near-field layout: a leaf's columns are its near ranges
+// (whole boxes, each in element order) one after another, in the order the
+// ranges are listed, not sorted
+struct near_view {
+    const int32_t *leaf_box, *bbeg, *bend;
+    const int64_t *colptr;     // [NL + 1] columns of each leaf
+    const int64_t *rptr;       // [NL + 1] near ranges of each leaf
+    const int32_t *rb, *re;    // element range [rb, re) of each near range
+    const int64_t *off;        // [NL + 1] entry offsets of each leaf's rows (row-major, nc columns)
+    const int32_t *elem_leaf;  // [N] leaf index of each element
+};
+
+constexpr int NT = 256;     // threads of the near-pattern product kernels
+constexpr int QC = 64;      // B's columns per chunk
+constexpr int QS = QC + 1;  // padded row stride of the A tile in shared memory
+constexpr int MAXR = 512;   // near ranges of one leaf staged in shared memory
+
+// the leaf whose rows start at column p of block b's columns, and the map of
+// the chunk's columns q0 .. q0 + QC into that leaf's own columns (-1 where
+// the pair is not in the near field), found through the leaf's near ranges
+// (staged in rbs / res); returns whether any column maps, or -1 if the
+// columns are not whole leaves or the leaf has more than MAXR ranges (then
+// err is set)
+struct row_leaf {
+    int lc, nC, ncC;
+    int64_t off;
+};
+
+__device__ inline int chunk_map(const sai_set &S, const near_view &V, int b, int p, int q0, row_leaf &L, int *map,
+                                int *rbs, int *res, int *err)
+{
+    const int64_t c0 = S.cptr[b];
+    const int nc = (int)(S.cptr[b + 1] - c0);
+    const int e = S.celem[c0 + p];
+    L.lc = V.elem_leaf[e];
+    const int C = V.leaf_box[L.lc];
+    const int cb0 = V.bbeg[C];
+    L.nC = V.bend[C] - cb0;
+    L.ncC = (int)(V.colptr[L.lc + 1] - V.colptr[L.lc]);
+    L.off = V.off[L.lc];
+    const int64_t r0 = V.rptr[L.lc];
+    const int nr = (int)(V.rptr[L.lc + 1] - r0);
+    if (e != cb0 || p + L.nC > nc || L.nC > 64 || nr > MAXR) {
+        if (threadIdx.x == 0) atomicExch(err, nr > MAXR ? 2 : 1);
+        return -1;
+    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        rbs[r] = V.rb[r0 + r];
+        res[r] = V.re[r0 + r];
+    }
+    __syncthreads();
+    int any = 0;
+    if (threadIdx.x < QC) {
+        const int q = q0 + (int)threadIdx.x;
+        int pos = -1;
+        if (q < nc) {
+            const int j = S.celem[c0 + q];
+            int o = 0;
+            for (int r = 0; r < nr; ++r) {
+                const int a = rbs[r], z = res[r];
+                if (j >= a && j < z) {
+                    pos = o + (j - a);
+                    break;
+                }
+                o += z - a;
+            }
+        }
+        map[threadIdx.x] = pos;
+        any = pos >= 0;
+    }
+    return __syncthreads_or(any) ? 1 : 0;
+}
+
+// R = M[B, C_B] A_near[C_B, C_B] - I[B, C_B] over QC-column chunks (each
+// thread a 4 x 4 register tile of the 64 x QC chunk), loss += scale ||R||^2;
+// R is stored (n_B x nc_B at moff[b]) unless Rg is null.  One CTA per block.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_sain_residual(sai_set S, near_view V, const cx<T> *A, const cx<T> *M,
+                                                      cx<T> *Rg, double *loss, T scale, int *err)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    cx<T> *Ms = reinterpret_cast<cx<T> *>(sm_raw);  // [64 rows of B][64 rows of C]
+    cx<T> *As = Ms + 64 * 64;                        // [64 rows of C][QS]
+    __shared__ int map[QC], rbs[MAXR], res[MAXR];
+    __shared__ double red[NT];
+    const int b = blockIdx.x, t = threadIdx.x, ti = t >> 4, tq = t & 15;
+    const int64_t r0 = S.bptr[b], c0 = S.cptr[b], mo = S.moff[b];
+    const int n = (int)(S.bptr[b + 1] - r0), nc = (int)(S.cptr[b + 1] - c0);
+    double part = 0.0;
+    bool bad = false;
+    for (int q0 = 0; q0 < nc && !bad; q0 += QC) {
+        cx<T> acc[4][4];
+        for (int p = 0; p < nc;) {
+            row_leaf L;
+            const int any = chunk_map(S, V, b, p, q0, L, map, rbs, res, err);
+            if (any < 0) {
+                bad = true;
+                break;
+            }
+            if (any) {
+                for (int x = t; x < 64 * 64; x += NT) {
+                    const int i = x >> 6, r = x & 63;
+                    Ms[x] = i < n && r < L.nC ? M[mo + (int64_t)i * nc + p + r] : cx<T>();
+                }
+                for (int x = t; x < 64 * QC; x += NT) {
+                    const int r = x / QC, qq = x % QC, m = map[qq];
+                    As[r * QS + qq] = r < L.nC && m >= 0 ? A[L.off + (int64_t)r * L.ncC + m] : cx<T>();
+                }
+                __syncthreads();
+                for (int r = 0; r < L.nC; ++r) {
+                    cx<T> mv[4], av[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) mv[u] = Ms[(ti * 4 + u) * 64 + r];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) av[v] = As[r * QS + tq * 4 + v];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) cfma(acc[u][v], mv[u], av[v]);
+                }
+            }
+            __syncthreads();  // map and tiles are rewritten for the next leaf
+            p += L.nC;
+        }
+        if (bad) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = ti * 4 + u, q = q0 + tq * 4 + v;
+                if (i < n && q < nc) {
+                    cx<T> r = acc[u][v];
+                    if (S.celem[c0 + q] == S.belem[r0 + i]) r.re -= (T)1;
+                    part += (double)r.re * r.re + (double)r.im * r.im;
+                    if (Rg) Rg[mo + (int64_t)i * nc + q] = r;
+                }
+            }
+    }
+    red[t] = part;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) atomicAdd(loss, (double)scale * red[0]);
+}
+
+// G[B, C] = 2 scale R[B, :] A_near[C, :]^H restricted to B's columns, for each
+// leaf C among B's columns (dL/dRe M + i dL/dIm M); one CTA per block, each
+// thread a 4 x 4 register tile of the 64 x 64 (row of B, row of C) block
+template <typename T>
+__global__ void __launch_bounds__(NT) k_sain_gradm(sai_set S, near_view V, const cx<T> *A, const cx<T> *Rg,
+                                                   cx<T> *G, T scale, int *err)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    cx<T> *Rs = reinterpret_cast<cx<T> *>(sm_raw);  // [64 rows of B][QC]
+    cx<T> *As = Rs + 64 * QC;                        // [64 rows of C][QS]
+    __shared__ int map[QC], rbs[MAXR], res[MAXR];
+    const int b = blockIdx.x, t = threadIdx.x, ti = t >> 4, tr = t & 15;
+    const int64_t r0 = S.bptr[b], c0 = S.cptr[b], mo = S.moff[b];
+    const int n = (int)(S.bptr[b + 1] - r0), nc = (int)(S.cptr[b + 1] - c0);
+    for (int p = 0; p < nc;) {
+        cx<T> acc[4][4];
+        row_leaf L{0, 0, 0, 0};
+        bool bad = false;
+        for (int q0 = 0; q0 < nc; q0 += QC) {
+            const int any = chunk_map(S, V, b, p, q0, L, map, rbs, res, err);
+            if (any < 0) {
+                bad = true;
+                break;
+            }
+            if (any) {
+                for (int x = t; x < 64 * QC; x += NT) {
+                    const int i = x / QC, qq = x % QC;
+                    Rs[x] = i < n && q0 + qq < nc ? Rg[mo + (int64_t)i * nc + q0 + qq] : cx<T>();
+                }
+                for (int x = t; x < 64 * QC; x += NT) {
+                    const int r = x / QC, qq = x % QC, m = map[qq];
+                    As[r * QS + qq] = r < L.nC && m >= 0 ? A[L.off + (int64_t)r * L.ncC + m] : cx<T>();
+                }
+                __syncthreads();
+                for (int qq = 0; qq < QC; ++qq) {
+                    cx<T> rv[4], av[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) rv[u] = Rs[(ti * 4 + u) * QC + qq];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const cx<T> a = As[(tr * 4 + v) * QS + qq];
+                        av[v] = cx<T>(a.re, -a.im);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) cfma(acc[u][v], rv[u], av[v]);
+                }
+            }
+            __syncthreads();
+        }
+        if (bad) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = ti * 4 + u, r = tr * 4 + v;
+                if (i < n && r < L.nC)
+                    G[mo + (int64_t)i * nc + p + r] =
+                        cx<T>((T)2 * scale * acc[u][v].re, (T)2 * scale * acc[u][v].im);
+            }
+        p += L.nC;
+    }
+}
+
+// leaf index of every element
+__global__ void k_elem_leaf(const int32_t *leaf_box, const int32_t *bbeg, const int32_t *bend, int NL, int32_t *out)
+{
+    const int li = blockIdx.x;
+    if (li >= NL) return;
+    const int B = leaf_box[li];
+    for (int e = bbeg[B] + threadIdx.x; e < bend[B]; e += blockDim.x) out[e] = li;
+}
+
+// the near-field columns of the chosen leaves, packed block after block
+__global__ void k_gather_cols(const int32_t *leaves, const int64_t *colptr, const int32_t *cols, const int64_t *cptr,
+                              int nb, int32_t *out)
+{
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int64_t src = colptr[leaves[b]], dst = cptr[b], n = cptr[b + 1] - dst;
+    for (int64_t q = threadIdx.x; q < n; q += blockDim.x) out[dst + q] = cols[src + q];
 }
 
 // leaf self blocks A_BB of the near-field matrix, row-major per leaf
@@ -331,7 +577,8 @@ void sai_from_handle(fda_handle *h, sai_data &D)
     D.nent = moff[NL];
     D.nrows = bptr[NL];
     D.S = sai_set{h->cent.as<double>(), h->nrm.as<double>(), h->area.as<double>(), D.bptr.as<int64_t>(),
-                  D.belem.as<int32_t>(), D.moff.as<int64_t>(), h->k, NL, maxn};
+                  D.belem.as<int32_t>(), D.bptr.as<int64_t>(), D.belem.as<int32_t>(), D.moff.as<int64_t>(), h->k,
+                  NL, maxn};
 }
 
 void sai_blocks_of_handle(fda_handle *h, sai_data &D)
@@ -373,6 +620,151 @@ void sai_loss_grad(const sai_set &S, const cx<T> *A, const T *W, cx<T> *M, cx<T>
     FDA_CUDA(cudaFuncSetAttribute(k_sai_backward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
     k_sai_backward<T><<<std::min(S.nb, 1024), BT, bs, s>>>(S, W, G, grad);
     FDA_CHECK_LAUNCH();
+}
+
+// ---- near-field pattern, host side
+
+// grow-only device buffer
+void ensure(dbuf &b, size_t bytes)
+{
+    if (b.bytes < bytes) b.alloc(bytes);
+}
+
+// a handle's leaf layout on the host and the element -> leaf map on the device
+struct near_host {
+    fda_handle *h = nullptr;
+    std::vector<int32_t> lb, bb, be;
+    std::vector<int64_t> colptr;
+    dbuf elem_leaf;
+    near_view V{};
+};
+
+void near_host_init(fda_handle *h, near_host &H)
+{
+    const int NL = h->nleaf;
+    H.h = h;
+    H.lb.resize(NL);
+    H.bb.resize(h->nbox_total);
+    H.be.resize(h->nbox_total);
+    H.colptr.resize(NL + 1);
+    FDA_CUDA(cudaMemcpy(H.lb.data(), h->leaf_box.p, 4 * (size_t)NL, cudaMemcpyDeviceToHost));
+    FDA_CUDA(cudaMemcpy(H.bb.data(), h->box_begin.p, 4 * H.bb.size(), cudaMemcpyDeviceToHost));
+    FDA_CUDA(cudaMemcpy(H.be.data(), h->box_end.p, 4 * H.be.size(), cudaMemcpyDeviceToHost));
+    FDA_CUDA(cudaMemcpy(H.colptr.data(), h->nf_colptr.p, 8 * H.colptr.size(), cudaMemcpyDeviceToHost));
+    for (int li = 0; li < NL; ++li)
+        if (H.be[H.lb[li]] - H.bb[H.lb[li]] > 64)
+            fda_fail(FDA_ERR_ARG, "the learned preconditioner needs leaves of at most 64 elements");
+    H.elem_leaf.alloc(4 * (size_t)std::max<int64_t>(h->N, 1));
+    k_elem_leaf<<<std::max(NL, 1), 128, 0, h->stream>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+                                                        h->box_end.as<int32_t>(), NL, H.elem_leaf.as<int32_t>());
+    FDA_CHECK_LAUNCH();
+    H.V = near_view{h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
+                    h->nf_colptr.as<int64_t>(), h->nr_ptr.as<int64_t>(), h->nr_begin.as<int32_t>(),
+                    h->nr_end.as<int32_t>(), h->nf_off.as<int64_t>(), H.elem_leaf.as<int32_t>()};
+}
+
+// the near-field blocks of the chosen leaves (rows of the leaf x its
+// near-field columns), packed; buffers grow and are reused across calls
+struct near_set {
+    dbuf leaves, bptr, belem, cptr, celem, moff;
+    sai_set S{};
+    int64_t nent = 0, nrows = 0;
+};
+
+void near_set_build(const near_host &H, const std::vector<int32_t> &leaves, near_set &D, cudaStream_t s)
+{
+    fda_handle *h = H.h;
+    const int nb = (int)leaves.size();
+    std::vector<int64_t> bptr(nb + 1, 0), cptr(nb + 1, 0), moff(nb + 1, 0);
+    std::vector<int32_t> belem;
+    int maxn = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int li = leaves[b];
+        if (li < 0 || li >= h->nleaf) fda_fail(FDA_ERR_ARG, "leaf index out of range");
+        const int b0 = H.bb[H.lb[li]], n = H.be[H.lb[li]] - b0;
+        const int64_t nc = H.colptr[li + 1] - H.colptr[li];
+        for (int q = 0; q < n; ++q) belem.push_back(b0 + q);
+        bptr[b + 1] = bptr[b] + n;
+        cptr[b + 1] = cptr[b] + nc;
+        moff[b + 1] = moff[b] + n * nc;
+        maxn = std::max(maxn, n);
+    }
+    ensure(D.leaves, 4 * (size_t)std::max(nb, 1));
+    ensure(D.bptr, 8 * (size_t)(nb + 1));
+    ensure(D.cptr, 8 * (size_t)(nb + 1));
+    ensure(D.moff, 8 * (size_t)(nb + 1));
+    ensure(D.belem, 4 * std::max<size_t>(belem.size(), 1));
+    ensure(D.celem, 4 * (size_t)std::max<int64_t>(cptr[nb], 1));
+    FDA_CUDA(cudaMemcpyAsync(D.leaves.p, leaves.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, s));
+    FDA_CUDA(cudaMemcpyAsync(D.bptr.p, bptr.data(), 8 * (size_t)(nb + 1), cudaMemcpyHostToDevice, s));
+    FDA_CUDA(cudaMemcpyAsync(D.cptr.p, cptr.data(), 8 * (size_t)(nb + 1), cudaMemcpyHostToDevice, s));
+    FDA_CUDA(cudaMemcpyAsync(D.moff.p, moff.data(), 8 * (size_t)(nb + 1), cudaMemcpyHostToDevice, s));
+    FDA_CUDA(cudaMemcpyAsync(D.belem.p, belem.data(), 4 * belem.size(), cudaMemcpyHostToDevice, s));
+    k_gather_cols<<<std::max(nb, 1), 128, 0, s>>>(D.leaves.as<int32_t>(), h->nf_colptr.as<int64_t>(),
+                                                  h->nf_cols.as<int32_t>(), D.cptr.as<int64_t>(), nb,
+                                                  D.celem.as<int32_t>());
+    FDA_CHECK_LAUNCH();
+    FDA_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    D.nent = moff[nb];
+    D.nrows = bptr[nb];
+    D.S = sai_set{h->cent.as<double>(), h->nrm.as<double>(), h->area.as<double>(), D.bptr.as<int64_t>(),
+                  D.belem.as<int32_t>(), D.cptr.as<int64_t>(), D.celem.as<int32_t>(), D.moff.as<int64_t>(), h->k,
+                  nb, maxn};
+}
+
+size_t near_smem(size_t esz) { return (size_t)(64 * 64 + 64 * QS) * esz; }
+
+template <typename T>
+void near_attrs()
+{
+    static bool done = false;
+    if (done) return;
+    FDA_CUDA(cudaFuncSetAttribute(k_sain_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)near_smem(sizeof(cx<T>))));
+    FDA_CUDA(cudaFuncSetAttribute(k_sain_gradm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)near_smem(sizeof(cx<T>))));
+    const size_t bs = backward_smem(sizeof(T));
+    FDA_CUDA(cudaFuncSetAttribute(k_sai_backward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
+    done = true;
+}
+
+// loss (and, with R and G given, dL/dW added into grad) of the near-field
+// objective over the blocks of S; A is the handle's near-field matrix
+template <typename T>
+void near_loss_grad(const sai_set &S, const near_view &V, const cx<T> *A, const T *W, cx<T> *M, cx<T> *R, cx<T> *G,
+                    double *loss, T *grad, T scale, int *err, cudaStream_t s)
+{
+    if (S.nb == 0) return;
+    near_attrs<T>();
+    k_sai_forward<T, T><<<S.nb, BT, 0, s>>>(S, W, M);
+    FDA_CHECK_LAUNCH();
+    const size_t ns = near_smem(sizeof(cx<T>));
+    k_sain_residual<T><<<S.nb, NT, ns, s>>>(S, V, A, M, R, loss, scale, err);
+    FDA_CHECK_LAUNCH();
+    if (!G) return;
+    k_sain_gradm<T><<<S.nb, NT, ns, s>>>(S, V, A, R, G, scale, err);
+    FDA_CHECK_LAUNCH();
+    k_sai_backward<T><<<std::min(S.nb, 1024), BT, backward_smem(sizeof(T)), s>>>(S, W, G, grad);
+    FDA_CHECK_LAUNCH();
+}
+
+void check_err(const dbuf &err, cudaStream_t s)
+{
+    int e = 0;
+    FDA_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FDA_CUDA(cudaStreamSynchronize(s));
+    if (e == 2) fda_fail(FDA_ERR_STATE, "a leaf has more near-field ranges than the kernels stage");
+    if (e) fda_fail(FDA_ERR_STATE, "near-field columns of a leaf are not whole leaves in element order");
+}
+
+// the near-field matrix of h in FP32 (the chosen form keeps one; else a copy)
+const c32f *near_f32(fda_handle *h, dbuf &tmp)
+{
+    if (h->op32.near.p) return h->op32.near.as<c32f>();
+    tmp.alloc(sizeof(c32f) * std::max<int64_t>(h->nnz_near, 1));
+    k_c64_to_c32_n<<<1024, 256, 0, h->stream>>>(h->op64.near.as<c64d>(), tmp.as<c32f>(), h->nnz_near);
+    FDA_CHECK_LAUNCH();
+    return tmp.as<c32f>();
 }
 
 // splitmix64: a fixed, documented generator for the initial weights
@@ -468,6 +860,8 @@ double fda_sai_set_impl(fda_handle *h, const float *W)
     dbuf dW, dl, G;
     dW.alloc(4 * SP);
     FDA_CUDA(cudaMemcpyAsync(dW.p, W, 4 * SP, cudaMemcpyHostToDevice, s));
+    h->sai_M32.release();
+    h->sai_pattern = 0;
     h->sai_M.alloc(sizeof(c64d) * std::max<int64_t>(D.nent, 1));
     h->sai_off.alloc(8 * (size_t)(h->nleaf + 1));
     FDA_CUDA(cudaMemcpyAsync(h->sai_off.p, D.moff.p, 8 * (size_t)(h->nleaf + 1), cudaMemcpyDeviceToDevice, s));
@@ -522,7 +916,8 @@ void fda_sai_loss_grad_impl(int64_t n, const double *cent, const double *nrm, co
     D.A64.alloc(sizeof(c64d) * std::max<int64_t>(D.nent, 1));
     FDA_CUDA(cudaMemcpy(D.A64.p, A, sizeof(c64d) * (size_t)D.nent, cudaMemcpyHostToDevice));
     D.S = sai_set{D.cent.as<double>(), D.nrm.as<double>(), D.area.as<double>(), D.bptr.as<int64_t>(),
-                  D.belem.as<int32_t>(), D.moff.as<int64_t>(), k, nb, maxn};
+                  D.belem.as<int32_t>(), D.bptr.as<int64_t>(), D.belem.as<int32_t>(), D.moff.as<int64_t>(), k, nb,
+                  maxn};
     dbuf dW, dG, Mb, Gb, dl, A32;
     dl.alloc(sizeof(double));
     FDA_CUDA(cudaMemset(dl.p, 0, sizeof(double)));
@@ -558,4 +953,199 @@ void fda_sai_loss_grad_impl(int64_t n, const double *cent, const double *nrm, co
         for (int p = 0; p < SP; ++p) grad[p] = g32[p];
     }
     FDA_CUDA(cudaMemcpy(loss, dl.p, sizeof(double), cudaMemcpyDeviceToHost));
+}
+
+// ---- near-field pattern: training, setting, loss and gradient
+
+namespace {
+
+// k distinct leaves of NL, uniformly (partial Fisher-Yates on splitmix64)
+std::vector<int32_t> sample_leaves(int NL, int k, uint64_t &st)
+{
+    std::vector<int32_t> all(NL);
+    for (int i = 0; i < NL; ++i) all[i] = i;
+    k = std::min(k, NL);
+    for (int i = 0; i < k; ++i) {
+        const int j = i + (int)(splitmix64(st) % (uint64_t)(NL - i));
+        std::swap(all[i], all[j]);
+    }
+    all.resize(k);
+    std::sort(all.begin(), all.end());
+    return all;
+}
+
+}  // namespace
+
+// Adam on the near-field objective: every step draws per_step leaves of each
+// handle; loss0 / loss1 are taken on one fixed draw before and after (FP32)
+void fda_sai_train_near_impl(fda_handle *const *hs, int nh, int epochs, double lr, int per_step, uint64_t seed,
+                             float *W, double *loss0, double *loss1, double *train_s)
+{
+    cudaStream_t s = hs[0]->stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<near_host> H(nh);
+    std::vector<dbuf> A32tmp(nh);
+    std::vector<const c32f *> A32(nh);
+    for (int q = 0; q < nh; ++q) {
+        near_host_init(hs[q], H[q]);
+        A32[q] = near_f32(hs[q], A32tmp[q]);
+        FDA_CUDA(cudaStreamSynchronize(hs[q]->stream));
+    }
+    std::vector<near_set> D(nh), E(nh);
+    uint64_t st = seed ^ 0x5A17C0DEull;
+    int64_t eval_rows = 0;
+    for (int q = 0; q < nh; ++q) {
+        near_set_build(H[q], sample_leaves(hs[q]->nleaf, per_step, st), E[q], s);
+        eval_rows += E[q].nrows;
+    }
+    dbuf dW, dG, m1, m2, Mb, Rb, Gb, dl, err;
+    dW.alloc(4 * SP);
+    dG.alloc(4 * SP);
+    m1.alloc(4 * SP);
+    m2.alloc(4 * SP);
+    dl.alloc(sizeof(double));
+    err.alloc(sizeof(int));
+    FDA_CUDA(cudaMemcpyAsync(dW.p, W, 4 * SP, cudaMemcpyHostToDevice, s));
+    FDA_CUDA(cudaMemsetAsync(m1.p, 0, 4 * SP, s));
+    FDA_CUDA(cudaMemsetAsync(m2.p, 0, 4 * SP, s));
+    FDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    auto evaluate = [&]() {
+        FDA_CUDA(cudaMemsetAsync(dl.p, 0, sizeof(double), s));
+        for (int q = 0; q < nh; ++q) {
+            ensure(Mb, sizeof(c32f) * (size_t)std::max<int64_t>(E[q].nent, 1));
+            near_loss_grad<float>(E[q].S, H[q].V, A32[q], dW.as<float>(), Mb.as<c32f>(), nullptr, nullptr,
+                                  dl.as<double>(), nullptr, (float)(1.0 / (double)std::max<int64_t>(eval_rows, 1)),
+                                  err.as<int>(), s);
+        }
+        double l = 0;
+        FDA_CUDA(cudaMemcpyAsync(&l, dl.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        check_err(err, s);
+        if (!std::isfinite(l)) fda_fail(FDA_ERR_NUMERIC, "learned preconditioner training diverged");
+        return l;
+    };
+    *loss0 = evaluate();
+    const float b1 = 0.9f, b2 = 0.999f;
+    double c1 = 1.0, c2 = 1.0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        int64_t rows = 0;
+        for (int q = 0; q < nh; ++q) {
+            near_set_build(H[q], sample_leaves(hs[q]->nleaf, per_step, st), D[q], s);
+            rows += D[q].nrows;
+        }
+        const float scale = (float)(1.0 / (double)std::max<int64_t>(rows, 1));
+        FDA_CUDA(cudaMemsetAsync(dG.p, 0, 4 * SP, s));
+        FDA_CUDA(cudaMemsetAsync(dl.p, 0, sizeof(double), s));
+        for (int q = 0; q < nh; ++q) {
+            const size_t eb = sizeof(c32f) * (size_t)std::max<int64_t>(D[q].nent, 1);
+            ensure(Mb, eb);
+            ensure(Rb, eb);
+            ensure(Gb, eb);
+            near_loss_grad<float>(D[q].S, H[q].V, A32[q], dW.as<float>(), Mb.as<c32f>(), Rb.as<c32f>(),
+                                  Gb.as<c32f>(), dl.as<double>(), dG.as<float>(), scale, err.as<int>(), s);
+        }
+        c1 *= b1;
+        c2 *= b2;
+        k_sai_adam<<<(SP + 255) / 256, 256, 0, s>>>(dW.as<float>(), dG.as<float>(), m1.as<float>(), m2.as<float>(),
+                                                     (float)lr, b1, b2, 1e-8f, (float)(1.0 - c1), (float)(1.0 - c2));
+        FDA_CHECK_LAUNCH();
+    }
+    check_err(err, s);
+    *loss1 = evaluate();
+    FDA_CUDA(cudaMemcpyAsync(W, dW.p, 4 * SP, cudaMemcpyDeviceToHost, s));
+    FDA_CUDA(cudaStreamSynchronize(s));
+    *train_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// network -> M on h's whole near-field pattern, FP32, in the near-field
+// matrix's own layout (the GMRES apply runs the near-field product with it);
+// with want_loss, the objective of the stored M over all leaves (FP32)
+double fda_sai_set_near_impl(fda_handle *h, const float *W, bool want_loss)
+{
+    cudaStream_t s = h->stream;
+    sai_data D;
+    sai_from_handle(h, D);  // rows of every leaf, in leaf order
+    if (D.S.nb == 0) fda_fail(FDA_ERR_STATE, "no leaves");
+    sai_set S = D.S;
+    S.cptr = h->nf_colptr.as<int64_t>();
+    S.celem = h->nf_cols.as<int32_t>();
+    S.moff = h->nf_off.as<int64_t>();
+    dbuf dW;
+    dW.alloc(4 * SP);
+    FDA_CUDA(cudaMemcpyAsync(dW.p, W, 4 * SP, cudaMemcpyHostToDevice, s));
+    h->sai_M.release();
+    h->sai_M32.alloc(sizeof(c32f) * std::max<int64_t>(h->nnz_near, 1));
+    k_sai_forward<float, float><<<S.nb, BT, 0, s>>>(S, dW.as<float>(), h->sai_M32.as<c32f>());
+    FDA_CHECK_LAUNCH();
+    h->sai_pattern = 1;
+    if (!want_loss) {
+        FDA_CUDA(cudaStreamSynchronize(s));
+        return 0.0;
+    }
+    near_host H;
+    near_host_init(h, H);
+    dbuf A32tmp, dl, err;
+    const c32f *A32 = near_f32(h, A32tmp);
+    dl.alloc(sizeof(double));
+    err.alloc(sizeof(int));
+    FDA_CUDA(cudaMemsetAsync(dl.p, 0, sizeof(double), s));
+    FDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    near_attrs<float>();
+    k_sain_residual<float><<<S.nb, NT, near_smem(sizeof(c32f)), s>>>(
+        S, H.V, A32, h->sai_M32.as<c32f>(), nullptr, dl.as<double>(), (float)(1.0 / (double)std::max<int64_t>(h->N, 1)),
+        err.as<int>());
+    FDA_CHECK_LAUNCH();
+    double l = 0;
+    FDA_CUDA(cudaMemcpyAsync(&l, dl.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    check_err(err, s);
+    return l;
+}
+
+// loss and gradient of the near-field objective over the given leaves of h,
+// FP64 (the handle's FP64 near-field matrix) or FP32 (the training kernels)
+void fda_sai_loss_grad_near_impl(fda_handle *h, const double *W, int nleaves, const int32_t *leaves, int fp32,
+                                 double *loss, double *grad)
+{
+    cudaStream_t s = h->stream;
+    near_host H;
+    near_host_init(h, H);
+    near_set D;
+    near_set_build(H, std::vector<int32_t>(leaves, leaves + nleaves), D, s);
+    const double scale = 1.0 / (double)std::max<int64_t>(D.nrows, 1);
+    dbuf dW, dG, Mb, Rb, Gb, dl, err, A32tmp;
+    dl.alloc(sizeof(double));
+    err.alloc(sizeof(int));
+    FDA_CUDA(cudaMemsetAsync(dl.p, 0, sizeof(double), s));
+    FDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    const size_t ne = (size_t)std::max<int64_t>(D.nent, 1);
+    if (!fp32) {
+        dW.alloc(8 * SP);
+        dG.alloc(8 * SP);
+        Mb.alloc(sizeof(c64d) * ne);
+        Rb.alloc(sizeof(c64d) * ne);
+        Gb.alloc(sizeof(c64d) * ne);
+        FDA_CUDA(cudaMemcpyAsync(dW.p, W, 8 * SP, cudaMemcpyHostToDevice, s));
+        FDA_CUDA(cudaMemsetAsync(dG.p, 0, 8 * SP, s));
+        near_loss_grad<double>(D.S, H.V, h->op64.near.as<c64d>(), dW.as<double>(), Mb.as<c64d>(), Rb.as<c64d>(),
+                               Gb.as<c64d>(), dl.as<double>(), dG.as<double>(), scale, err.as<int>(), s);
+        FDA_CUDA(cudaMemcpyAsync(grad, dG.p, 8 * SP, cudaMemcpyDeviceToHost, s));
+        check_err(err, s);
+    } else {
+        std::vector<float> w32(SP), g32(SP);
+        for (int p = 0; p < SP; ++p) w32[p] = (float)W[p];
+        const c32f *A32 = near_f32(h, A32tmp);
+        dW.alloc(4 * SP);
+        dG.alloc(4 * SP);
+        Mb.alloc(sizeof(c32f) * ne);
+        Rb.alloc(sizeof(c32f) * ne);
+        Gb.alloc(sizeof(c32f) * ne);
+        FDA_CUDA(cudaMemcpyAsync(dW.p, w32.data(), 4 * SP, cudaMemcpyHostToDevice, s));
+        FDA_CUDA(cudaMemsetAsync(dG.p, 0, 4 * SP, s));
+        near_loss_grad<float>(D.S, H.V, A32, dW.as<float>(), Mb.as<c32f>(), Rb.as<c32f>(), Gb.as<c32f>(),
+                              dl.as<double>(), dG.as<float>(), (float)scale, err.as<int>(), s);
+        FDA_CUDA(cudaMemcpyAsync(g32.data(), dG.p, 4 * SP, cudaMemcpyDeviceToHost, s));
+        check_err(err, s);
+        for (int p = 0; p < SP; ++p) grad[p] = g32[p];
+    }
+    FDA_CUDA(cudaMemcpyAsync(loss, dl.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FDA_CUDA(cudaStreamSynchronize(s));
 }

@@ -528,6 +528,7 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
         std::vector<tc_tile> tiles;
         for (int o = 0; o < nops; ++o) {
             int a = B.op_start[o] * mr, b = B.op_start[o + 1] * mr;
+            if (a == b) continue;
             for (int p0 = a; p0 < b; p0 += NC)
                 for (int rt = 0; rt < P.nrt; rt += R) tiles.push_back(tc_tile{o, p0, std::min(NC, b - p0), rt});
         }

@@ -46,7 +46,7 @@ def test_tile_shape_override_null_handle(lib):
     assert lib.fda_set_tc_tiles(None, 0, 0, 0) == 1
 
 
-@pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", 0.5), ("leaf_max", 0), ("leaf_max", 65),
+@pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", 0.5), ("eps", 1e-9), ("leaf_max", 0), ("leaf_max", 65),
                                          ("p_lf", 2), ("precision", 3), ("mode", 7), ("restart", 0), ("restart", 256),
                                          ("rho_min", 1.0), ("graphs", 2), ("autotune", 3), ("precond", 2)])
 def test_invalid_config_rejected_without_gpu(lib, field, value):
@@ -105,6 +105,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[name]) == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(out[name + "." + fname]) == getattr(cls, fname).offset, (name, fname)
+
+
+def test_struct_sizes_reported_by_the_library(lib):
+    from paper_1403_4747_gb300 import _lib
+    classes = (_lib.fda_config, _lib.fda_info, _lib.fda_stats, _lib.fda_sai_config, _lib.fda_sai_report,
+               _lib.fda_batch_stats)
+    for which, cls in enumerate(classes):
+        assert lib.fda_struct_size(which) == ctypes.sizeof(cls), cls.__name__
+    assert lib.fda_struct_size(-1) == 0 and lib.fda_struct_size(6) == 0
 
 
 def test_null_handle_calls_of_the_right_hand_sides_and_fields(lib):

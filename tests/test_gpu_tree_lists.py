@@ -23,12 +23,11 @@ import pytest
 
 import oracle
 from inputs import icosphere, ellipsoid_from_icosphere
+from tree_reference import reference_tree, reference_lists
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-
-MAXD = 20
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,82 +36,6 @@ def _cuda():
         pytest.skip("no CUDA device")
     from paper_1403_4747_gb300 import build
     build.build()
-
-
-def _reference_tree(v, f, k, leaf_max=64, rho_min=2.2):
-    """Boxes per level as {cell: sorted caller indices}, leaf flags, and the
-    level parameters (width, high-frequency flag, rho)."""
-    c = np.mean(v[f], axis=1)
-    lo, hi = c.min(axis=0), c.max(axis=0)
-    ext = float(np.max(hi - lo))
-    W = ext * (1.0 + 1e-6) if ext > 0 else 1.0
-    root = 0.5 * (lo + hi) - 0.5 * W
-    q = np.floor((c - root) * ((1 << MAXD) / W)).astype(np.int64)
-    q = np.clip(q, 0, (1 << MAXD) - 1)
-    lam = 2.0 * np.pi / k
-    active = np.ones(len(f), dtype=bool)
-    levels = []
-    for l in range(MAXD + 1):
-        idx = np.nonzero(active)[0]
-        if len(idx) == 0:
-            break
-        w = W / (1 << l)
-        hf = w >= lam
-        cells = q[idx] >> (MAXD - l)
-        boxes = {}
-        for i, cc in zip(idx, map(tuple, cells)):
-            boxes.setdefault(cc, []).append(int(i))
-        leaf = {}
-        for cc, el in boxes.items():
-            leaf[cc] = (l == MAXD) or ((not hf) and len(el) <= leaf_max)
-            if leaf[cc]:
-                active[el] = False
-        rho = max(rho_min, w / lam) if hf else 0.0
-        levels.append({"boxes": {cc: sorted(el) for cc, el in boxes.items()}, "leaf": leaf, "hf": hf, "rho": rho})
-    return levels
-
-
-def _near(L, d):
-    d = np.asarray(d)
-    if np.max(np.abs(d)) <= 1:
-        return True
-    return bool(L["hf"] and np.sqrt(np.sum(d * d)) < L["rho"])
-
-
-def _reference_lists(levels):
-    """Interaction lists {(level, cell): set of cells} and near-field element
-    sets {(level, cell) of a leaf: set of caller indices}."""
-    il = {}
-    for l in range(1, len(levels)):
-        L, Lp = levels[l], levels[l - 1]
-        cells = list(L["boxes"])
-        for b in cells:
-            pb = tuple(np.array(b) >> 1)
-            s = set()
-            for a in cells:
-                pa = tuple(np.array(a) >> 1)
-                if not _near(Lp, np.array(pa) - np.array(pb)):
-                    continue
-                if _near(L, np.array(a) - np.array(b)):
-                    continue
-                s.add(a)
-            il[(l, b)] = s
-    near = {}
-    for lb, L in enumerate(levels):
-        for b, isleaf in L["leaf"].items():
-            if not isleaf:
-                continue
-            s = set()
-            for l in range(lb + 1):
-                anc = np.array(b) >> (lb - l)
-                for x, xleaf in levels[l]["leaf"].items():
-                    if xleaf and _near(levels[l], np.array(x) - anc):
-                        s.update(levels[l]["boxes"][x])
-            for x, xleaf in L["leaf"].items():
-                if not xleaf and _near(L, np.array(x) - np.array(b)):
-                    s.update(L["boxes"][x])
-            near[(lb, b)] = s
-    return il, near
 
 
 @pytest.mark.parametrize("mesh,k", [("sphere3", 12.0), ("sphere4", 20.0), ("ellipsoid4", 15.0)])
@@ -128,7 +51,7 @@ def test_tree_and_lists_equal_reference_construction(mesh, k):
         P.close()
     perm = t["perm"]
     assert sorted(perm.tolist()) == list(range(n))
-    ref = _reference_tree(v, f, k)
+    ref = reference_tree(v, f, k)
     # boxes, element sets and leaf flags, level by level
     dev = {}
     for b in range(len(t["box_level"])):
@@ -146,7 +69,7 @@ def test_tree_and_lists_equal_reference_construction(mesh, k):
                 p = t["box_parent"][b]
                 assert (int(t["box_level"][p]), tuple(t["box_coord"][p])) == (l - 1, tuple(np.array(cc) >> 1))
     # interaction lists
-    il, near = _reference_lists(ref)
+    il, near = reference_lists(ref)
     for b in range(len(t["box_level"])):
         l = int(t["box_level"][b])
         cc = tuple(int(x) for x in t["box_coord"][b])
