@@ -58,37 +58,13 @@ constexpr int NRG = 8;
 
 constexpr int NRW = 2;  // rows per warp in the near-field product
 
+// NRW rows r0, r0 + AT / 32, ... of a leaf block (row-major, nc columns)
+// times x, written to y
 template <typename R, int NR, bool XS>
-__global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, const int32_t *bbeg,
-                                                   const int32_t *bend, const int64_t *colptr, const int32_t *cols,
-                                                   const int64_t *off, const cx<R> *A, const void *x, int x64,
-                                                   int64_t xstr, int mr, c64d *y, int64_t ldy)
+__device__ __forceinline__ void near_rows(int r0, int nB, int lane, const cx<R> *A, int nc, const int32_t *cl,
+                                          const cx<R> *xsm, const void *x, int x64, int64_t xstr, int m0, int nm,
+                                          c64d *y, int64_t ldy, int i0)
 {
-    // Each warp takes NRW rows of a leaf (rows r and r + 8 of its group of
-    // 8 NRW); the leaf's columns (its flattened near ranges, shared by all
-    // its rows) are streamed four 32-wide slices at a time, the last ones
-    // predicated, so every lane keeps 4 NRW independent matrix loads in
-    // flight and each x value serves NRW rows.  With XS (one right-hand
-    // side) the CTA first gathers x over the leaf's columns into shared
-    // memory, so the warps read it from there instead of through the column
-    // list.
-    extern __shared__ unsigned char xs_raw[];
-    cx<R> *xsm = reinterpret_cast<cx<R> *>(xs_raw);
-    int li = blockIdx.x;
-    int B = leaf_box[li];
-    int i0 = bbeg[B], nB = bend[B] - i0;
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = blockIdx.y * (AT / 32) * NRW + warp;
-    if (blockIdx.y * (AT / 32) * NRW >= nB) return;  // whole CTA
-    const int m0 = blockIdx.z * NR;
-    const int nm = min(NR, mr - m0);
-    const int64_t c0 = colptr[li];
-    const int nc = (int)(colptr[li + 1] - c0);
-    const int32_t *cl = cols + c0;
-    if (XS) {
-        for (int c = threadIdx.x; c < nc; c += AT) xsm[c] = ldx<R>(x, __ldg(cl + c), x64);
-        __syncthreads();
-    }
     if (r0 >= nB) return;
     const cx<R> *rowp[NRW];
     bool rv[NRW];
@@ -96,7 +72,7 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
     for (int w = 0; w < NRW; ++w) {
         const int r = r0 + w * (AT / 32);
         rv[w] = r < nB;
-        rowp[w] = A + off[li] + (int64_t)(rv[w] ? r : r0) * nc;
+        rowp[w] = A + (int64_t)(rv[w] ? r : r0) * nc;
     }
     cx<R> acc[NRW][NR];
     for (int cb = 0; cb < nc; cb += 128) {
@@ -140,6 +116,43 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
         }
     }
 }
+
+template <typename R, int NR, bool XS>
+__global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, const int32_t *bbeg,
+                                                   const int32_t *bend, const int64_t *colptr, const int32_t *cols,
+                                                   const int64_t *off, const cx<R> *A, const void *x, int x64,
+                                                   int64_t xstr, int mr, c64d *y, int64_t ldy)
+{
+    // Each warp takes NRW rows of a leaf (rows r and r + 8 of its group of
+    // 8 NRW); the leaf's columns (its flattened near ranges, shared by all
+    // its rows) are streamed four 32-wide slices at a time, the last ones
+    // predicated, so every lane keeps 4 NRW independent matrix loads in
+    // flight and each x value serves NRW rows.  With XS (one right-hand
+    // side) the CTA first gathers x over the leaf's columns into shared
+    // memory, so the warps read it from there instead of through the column
+    // list.
+    extern __shared__ unsigned char xs_raw[];
+    cx<R> *xsm = reinterpret_cast<cx<R> *>(xs_raw);
+    int li = blockIdx.x;
+    int B = leaf_box[li];
+    int i0 = bbeg[B], nB = bend[B] - i0;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (blockIdx.y * (AT / 32) * NRW >= nB) return;  // whole CTA
+    const int m0 = blockIdx.z * NR;
+    const int nm = min(NR, mr - m0);
+    const int64_t c0 = colptr[li];
+    const int nc = (int)(colptr[li + 1] - c0);
+    const int32_t *cl = cols + c0;
+    if (XS) {
+        for (int c = threadIdx.x; c < nc; c += AT) xsm[c] = ldx<R>(x, __ldg(cl + c), x64);
+        __syncthreads();
+    }
+    // groups of (AT / 32) x NRW rows: one group per CTA row, or all of the
+    // leaf's groups in one CTA when gridDim.y == 1 (x gathered once)
+    for (int g0 = blockIdx.y * (AT / 32) * NRW; g0 < nB; g0 += gridDim.y * (AT / 32) * NRW)
+        near_rows<R, NR, XS>(g0 + warp, nB, lane, A + off[li], nc, cl, xsm, x, x64, xstr, m0, nm, y, ldy, i0);
+}
+
 
 // ---- Step 2: S2M at leaves, q~ = S~ x_B
 // One CTA per leaf.  With T < blockDim the CTA splits the sum over the
@@ -226,9 +239,9 @@ __global__ void k_l2t(lvl_ptrs<R> P, const int32_t *leaf_box, const int32_t *ble
 // CTA), so that many leaves are in flight per SM
 constexpr int LPB = 8;
 
-// q~_B = S~_B x_B: lane t < T (in steps of 32, MAXR x 32 rows per pass) sums
-// over the leaf's elements; x_B (n_B <= 64) sits in two registers per lane
-// and is broadcast by shuffles
+// q~_B = S~_B x_B: lane t < T (rows lane, lane + 32, ...) sums over the
+// leaf's elements eight at a time; x_B (n_B <= 64) sits in two registers per
+// lane and is broadcast by shuffles
 template <typename R>
 __global__ void __launch_bounds__(32 * LPB) k_s2m_w(lvl_ptrs<R> P, int nleaf, const int32_t *leaf_box,
                                                      const int32_t *blev, const int32_t *bbeg, const int32_t *bend,
@@ -243,28 +256,30 @@ __global__ void __launch_bounds__(32 * LPB) k_s2m_w(lvl_ptrs<R> P, int nleaf, co
     const cx<R> x0 = lane < nB ? ldx<R>(x, j0 + lane, x64) : cx<R>();
     const cx<R> x1 = lane + 32 < nB ? ldx<R>(x, j0 + lane + 32, x64) : cx<R>();
     cx<R> *q = P.q[l] + (int64_t)(B - P.box0[l]) * T;
-    for (int t0 = 0; t0 < T; t0 += 32 * MAXR) {
-        cx<R> acc[MAXR];
-        for (int j = 0; j < nB; ++j) {
-            const cx<R> src = j < 32 ? x0 : x1;
-            const cx<R> xj(__shfl_sync(0xffffffffu, src.re, j & 31), __shfl_sync(0xffffffffu, src.im, j & 31));
+    constexpr int JU = 8;  // elements per step: their operator loads are issued before the products
+    for (int t0 = 0; t0 < T; t0 += 32) {  // every lane stays in the loop (the shuffles need all 32)
+        const int t = t0 + lane;
+        const bool on = t < T;
+        cx<R> acc;
+        for (int jb = 0; jb < nB; jb += JU) {
+            cx<R> sv[JU];
 #pragma unroll
-            for (int r = 0; r < MAXR; ++r) {
-                const int t = t0 + 32 * r + lane;
-                if (t < T) cfma(acc[r], S[(int64_t)j * T + t], xj);
+            for (int u = 0; u < JU; ++u) sv[u] = on && jb + u < nB ? S[(int64_t)(jb + u) * T + t] : cx<R>();
+#pragma unroll
+            for (int u = 0; u < JU; ++u) {
+                const int j = jb + u;  // past nB the operator values are 0
+                const cx<R> src = j < 32 ? x0 : x1;
+                const cx<R> xj(__shfl_sync(0xffffffffu, src.re, j & 31), __shfl_sync(0xffffffffu, src.im, j & 31));
+                cfma(acc, sv[u], xj);
             }
         }
-#pragma unroll
-        for (int r = 0; r < MAXR; ++r) {
-            const int t = t0 + 32 * r + lane;
-            if (t < T) q[t] = acc[r];
-        }
+        if (on) q[t] = acc;
     }
 }
 
 // y_B += T~_B p~_B: lane owns rows lane and lane + 32 of the leaf (n_B <= 64)
 // and sums over the T densities, read 32 at a time into registers and
-// broadcast by shuffles
+// broadcast by shuffles; the operator columns are loaded eight at a time
 template <typename R>
 __global__ void __launch_bounds__(32 * LPB) k_l2t_w(lvl_ptrs<R> P, int nleaf, const int32_t *leaf_box,
                                                      const int32_t *blev, const int32_t *bbeg, const int32_t *bend,
@@ -279,15 +294,27 @@ __global__ void __launch_bounds__(32 * LPB) k_l2t_w(lvl_ptrs<R> P, int nleaf, co
     const cx<R> *src = P.p[l] + (int64_t)(B - P.box0[l]) * T;
     const bool r0 = lane < nB, r1 = lane + 32 < nB;
     cx<R> a0, a1;
+    constexpr int UU = 8;  // densities per step: their operator loads are issued before the products
     for (int tb = 0; tb < T; tb += 32) {
         const cx<R> pv = tb + lane < T ? src[tb + lane] : cx<R>();
         const int nt = min(32, T - tb);
-#pragma unroll 8
-        for (int u = 0; u < nt; ++u) {
-            const cx<R> pt(__shfl_sync(0xffffffffu, pv.re, u), __shfl_sync(0xffffffffu, pv.im, u));
-            const cx<R> *col = Tm + (int64_t)(tb + u) * 64;
-            if (r0) cfma(a0, col[lane], pt);
-            if (r1) cfma(a1, col[lane + 32], pt);
+        for (int ub = 0; ub < nt; ub += UU) {
+            cx<R> c0[UU], c1[UU];
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                const cx<R> *col = Tm + (int64_t)(tb + ub + u) * 64;
+                const bool in = ub + u < nt;
+                c0[u] = in && r0 ? col[lane] : cx<R>();
+                c1[u] = in && r1 ? col[lane + 32] : cx<R>();
+            }
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                // past nt the operator values are 0 (pv of lanes past T is 0 too)
+                const cx<R> pt(__shfl_sync(0xffffffffu, pv.re, (ub + u) & 31),
+                               __shfl_sync(0xffffffffu, pv.im, (ub + u) & 31));
+                cfma(a0, c0[u], pt);
+                cfma(a1, c1[u], pt);
+            }
         }
     }
     if (r0) {
@@ -387,7 +414,7 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     if (leaf_tc) {
         fda_leaf_tc(h, 0, near, reinterpret_cast<const c32f *>(x), y, mr);
     } else if (mr == 1 && xs_bytes <= 160 * 1024) {
-        dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
+        dim3 gn(NL, 1, 1);  // one CTA per leaf: x gathered once, the CTA loops over the row groups
         static bool attr = false;
         if (!attr) {
             FDA_CUDA(cudaFuncSetAttribute(k_near_apply<R, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -510,6 +537,7 @@ void fda_near_product_f32(fda_handle *h, const c32f *A, const c64d *x, c64d *z)
     const size_t xs_bytes = sizeof(c32f) * (size_t)h->max_near_cols;
     dim3 gn(h->nleaf, (h->max_leaf_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
     if (xs_bytes <= 160 * 1024) {
+        gn.y = 1;  // one CTA per leaf (x gathered once)
         static bool attr = false;
         if (!attr) {
             FDA_CUDA(cudaFuncSetAttribute(k_near_apply<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
