@@ -58,25 +58,25 @@ constexpr int NRG = 8;
 
 constexpr int NRW = 2;  // rows per warp in the near-field product
 
-// NRW rows r0, r0 + AT / 32, ... of a leaf block (row-major, nc columns)
+// NW rows r0, r0 + AT / 32, ... of a leaf block (row-major, nc columns)
 // times x, written to y
-template <typename R, int NR, bool XS>
+template <typename R, int NR, bool XS, int NW>
 __device__ __forceinline__ void near_rows(int r0, int nB, int lane, const cx<R> *A, int nc, const int32_t *cl,
                                           const cx<R> *xsm, const void *x, int x64, int64_t xstr, int m0, int nm,
                                           c64d *y, int64_t ldy, int i0)
 {
     if (r0 >= nB) return;
-    const cx<R> *rowp[NRW];
-    bool rv[NRW];
+    const cx<R> *rowp[NW];
+    bool rv[NW];
 #pragma unroll
-    for (int w = 0; w < NRW; ++w) {
+    for (int w = 0; w < NW; ++w) {
         const int r = r0 + w * (AT / 32);
         rv[w] = r < nB;
         rowp[w] = A + (int64_t)(rv[w] ? r : r0) * nc;
     }
-    cx<R> acc[NRW][NR];
+    cx<R> acc[NW][NR];
     for (int cb = 0; cb < nc; cb += 128) {
-        cx<R> a[NRW][4];
+        cx<R> a[NW][4];
         int j[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -85,7 +85,7 @@ __device__ __forceinline__ void near_rows(int r0, int nB, int lane, const cx<R> 
             if (cc < nc) {
                 j[u] = XS ? cc : __ldg(cl + cc);
 #pragma unroll
-                for (int w = 0; w < NRW; ++w)
+                for (int w = 0; w < NW; ++w)
                     if (rv[w]) a[w][u] = rowp[w][cc];
             }
         }
@@ -97,11 +97,11 @@ __device__ __forceinline__ void near_rows(int r0, int nB, int lane, const cx<R> 
                     const cx<R> xv = XS ? (cb + 32 * u + lane < nc ? xsm[j[u]] : cx<R>())
                                         : ldx<R>(x, (int64_t)(m0 + mm) * xstr + j[u], x64);
 #pragma unroll
-                    for (int w = 0; w < NRW; ++w) cfma(acc[w][mm], a[w][u], xv);
+                    for (int w = 0; w < NW; ++w) cfma(acc[w][mm], a[w][u], xv);
                 }
     }
 #pragma unroll
-    for (int w = 0; w < NRW; ++w) {
+    for (int w = 0; w < NW; ++w) {
         if (!rv[w]) break;  // uniform across the warp
         const int r = r0 + w * (AT / 32);
 #pragma unroll
@@ -117,17 +117,17 @@ __device__ __forceinline__ void near_rows(int r0, int nB, int lane, const cx<R> 
     }
 }
 
-template <typename R, int NR, bool XS>
+template <typename R, int NR, bool XS, int NW = NRW>
 __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, const int32_t *bbeg,
                                                    const int32_t *bend, const int64_t *colptr, const int32_t *cols,
                                                    const int64_t *off, const cx<R> *A, const void *x, int x64,
                                                    int64_t xstr, int mr, c64d *y, int64_t ldy)
 {
-    // Each warp takes NRW rows of a leaf (rows r and r + 8 of its group of
-    // 8 NRW); the leaf's columns (its flattened near ranges, shared by all
+    // Each warp takes NW rows of a leaf (rows r, r + 8, ... of its group of
+    // 8 NW); the leaf's columns (its flattened near ranges, shared by all
     // its rows) are streamed four 32-wide slices at a time, the last ones
-    // predicated, so every lane keeps 4 NRW independent matrix loads in
-    // flight and each x value serves NRW rows.  With XS (one right-hand
+    // predicated, so every lane keeps 4 NW independent matrix loads in
+    // flight and each x value serves NW rows.  With XS (one right-hand
     // side) the CTA first gathers x over the leaf's columns into shared
     // memory, so the warps read it from there instead of through the column
     // list.
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
     int B = leaf_box[li];
     int i0 = bbeg[B], nB = bend[B] - i0;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (blockIdx.y * (AT / 32) * NRW >= nB) return;  // whole CTA
+    if (blockIdx.y * (AT / 32) * NW >= nB) return;  // whole CTA
     const int m0 = blockIdx.z * NR;
     const int nm = min(NR, mr - m0);
     const int64_t c0 = colptr[li];
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
     }
     // groups of (AT / 32) x NRW rows: one group per CTA row, or all of the
     // leaf's groups in one CTA when gridDim.y == 1 (x gathered once)
-    for (int g0 = blockIdx.y * (AT / 32) * NRW; g0 < nB; g0 += gridDim.y * (AT / 32) * NRW)
-        near_rows<R, NR, XS>(g0 + warp, nB, lane, A + off[li], nc, cl, xsm, x, x64, xstr, m0, nm, y, ldy, i0);
+    for (int g0 = blockIdx.y * (AT / 32) * NW; g0 < nB; g0 += gridDim.y * (AT / 32) * NW)
+        near_rows<R, NR, XS, NW>(g0 + warp, nB, lane, A + off[li], nc, cl, xsm, x, x64, xstr, m0, nm, y, ldy, i0);
 }
 
 
@@ -417,11 +417,11 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         dim3 gn(NL, 1, 1);  // one CTA per leaf: x gathered once, the CTA loops over the row groups
         static bool attr = false;
         if (!attr) {
-            FDA_CUDA(cudaFuncSetAttribute(k_near_apply<R, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            FDA_CUDA(cudaFuncSetAttribute(k_near_apply<R, 1, true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           160 * 1024));
             attr = true;
         }
-        k_near_apply<R, 1, true><<<gn, AT, xs_bytes, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
+        k_near_apply<R, 1, true, 3><<<gn, AT, xs_bytes, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                           h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
                                                           h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
                                                           near.template as<cx<R>>(), x, x64, N, mr, y, N);
@@ -540,11 +540,11 @@ void fda_near_product_f32(fda_handle *h, const c32f *A, const c64d *x, c64d *z)
         gn.y = 1;  // one CTA per leaf (x gathered once)
         static bool attr = false;
         if (!attr) {
-            FDA_CUDA(cudaFuncSetAttribute(k_near_apply<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          160 * 1024));
+            FDA_CUDA(cudaFuncSetAttribute(k_near_apply<float, 1, true, 3>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
             attr = true;
         }
-        k_near_apply<float, 1, true><<<gn, AT, xs_bytes, h->stream>>>(
+        k_near_apply<float, 1, true, 3><<<gn, AT, xs_bytes, h->stream>>>(
             h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
             h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(), A, x, 1, h->N, 1, z, h->N);
     } else {
