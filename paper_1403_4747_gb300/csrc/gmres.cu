@@ -27,45 +27,51 @@ namespace {
 
 constexpr int RT = 256;
 constexpr int RCH = 1024;  // most chunks per vector for the two-stage dot products
-
-// partial[i * rch + c] = sum over chunk c of conj(V_i[n]) w[n].  A CTA takes
-// one chunk of the index range and a group of DVG vectors: every thread
-// reads its w values once and accumulates DVG products from them, then the
-// DVG sums are reduced across the CTA.
+constexpr int DEL = 4;     // elements per thread and chunk (chunks of RT x DEL elements)
+// partial[i * rch + c] = sum over chunk c of conj(V_i[n]) w[n] for the G
+// vectors of this CTA's group (blockIdx.y).  Every thread reads its w values
+// once and accumulates the G products from them in the type P, then sums
+// across its warp in P; the warps' sums are added in FP64.  P = double for
+// the FP64 solve; P = float for the inner solves of the chosen form, whose
+// tolerance (>= 1e-5) is far above FP32 rounding and whose result the FP64
+// residual of the outer loop judges: GB300's FP64 rate (about 1/64 of FP32)
+// would otherwise make these memory-sized passes compute-bound.
 constexpr int DVG = 8;  // vectors per CTA
-
+template <int G, typename P>
 __global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv, const c64d *w, int64_t n,
                                              c64d *partial, int rch)
 {
-    __shared__ double sr[RT / 32][DVG], si[RT / 32][DVG];
-    const int c = blockIdx.x, i0 = blockIdx.y * DVG, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ng = min(DVG, nv - i0);
+    __shared__ double sr[RT / 32][G], si[RT / 32][G];
+    const int c = blockIdx.x, i0 = blockIdx.y * G, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ng = min(G, nv - i0);
     const int64_t per = (n + rch - 1) / rch;
     const int64_t b = (int64_t)c * per, e = b + per < n ? b + per : n;
-    double ar[DVG], ai[DVG];
+    P ar[G], ai[G];
 #pragma unroll
-    for (int g = 0; g < DVG; ++g) ar[g] = ai[g] = 0.0;
+    for (int g = 0; g < G; ++g) ar[g] = ai[g] = (P)0;
     for (int64_t t = b + threadIdx.x; t < e; t += RT) {
-        const c64d x = w[t];
+        const c64d xd = w[t];
+        const P xr = (P)xd.re, xi = (P)xd.im;
 #pragma unroll
-        for (int g = 0; g < DVG; ++g)
+        for (int g = 0; g < G; ++g)
             if (g < ng) {
                 const c64d a = V[(int64_t)(i0 + g) * ldv + t];
-                ar[g] += a.re * x.re + a.im * x.im;
-                ai[g] += a.re * x.im - a.im * x.re;
+                const P vr = (P)a.re, vi = (P)a.im;
+                ar[g] += vr * xr + vi * xi;
+                ai[g] += vr * xi - vi * xr;
             }
     }
 #pragma unroll
-    for (int g = 0; g < DVG; ++g)
+    for (int g = 0; g < G; ++g)
         for (int o = 16; o > 0; o >>= 1) {
             ar[g] += __shfl_xor_sync(0xffffffffu, ar[g], o);
             ai[g] += __shfl_xor_sync(0xffffffffu, ai[g], o);
         }
     if (lane == 0)
 #pragma unroll
-        for (int g = 0; g < DVG; ++g) {
-            sr[warp][g] = ar[g];
-            si[warp][g] = ai[g];
+        for (int g = 0; g < G; ++g) {
+            sr[warp][g] = (double)ar[g];
+            si[warp][g] = (double)ai[g];
         }
     __syncthreads();
     if (threadIdx.x < ng) {
@@ -77,7 +83,6 @@ __global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv,
         partial[(int64_t)(i0 + threadIdx.x) * rch + c] = c64d(r, im);
     }
 }
-
 __global__ void k_dots_finish(const c64d *partial, int nv, c64d *out, int rch)
 {
     __shared__ double sr[RT], si[RT];
@@ -101,27 +106,32 @@ __global__ void k_dots_finish(const c64d *partial, int nv, c64d *out, int rch)
 }
 
 // w[n] += sign * sum_i V_i[n] c[i]; the coefficients are staged in shared
-// memory and the vectors read four at a time
+// memory and the vectors read four at a time; the sum is formed in P (as in
+// k_dots) and added to w in FP64
+template <typename P>
 __global__ void __launch_bounds__(RT) k_combine(const c64d *V, int64_t ldv, int nv, const c64d *c, double sign,
                                                 c64d *w, int64_t n)
 {
-    __shared__ c64d cs[256];
-    for (int i = threadIdx.x; i < nv && i < 256; i += RT) cs[i] = c[i];
+    __shared__ cx<P> cs[256];
+    for (int i = threadIdx.x; i < nv && i < 256; i += RT) cs[i] = cx<P>((P)c[i].re, (P)c[i].im);
     __syncthreads();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
-    c64d acc;
+    auto ld = [&](int i) {
+        const c64d a = V[(int64_t)i * ldv + t];
+        return cx<P>((P)a.re, (P)a.im);
+    };
+    cx<P> acc;
     int i = 0;
     for (; i + 3 < nv; i += 4) {
-        const c64d a0 = V[(int64_t)i * ldv + t], a1 = V[(int64_t)(i + 1) * ldv + t];
-        const c64d a2 = V[(int64_t)(i + 2) * ldv + t], a3 = V[(int64_t)(i + 3) * ldv + t];
+        const cx<P> a0 = ld(i), a1 = ld(i + 1), a2 = ld(i + 2), a3 = ld(i + 3);
         cfma(acc, a0, cs[i]);
         cfma(acc, a1, cs[i + 1]);
         cfma(acc, a2, cs[i + 2]);
         cfma(acc, a3, cs[i + 3]);
     }
-    for (; i < nv; ++i) cfma(acc, V[(int64_t)i * ldv + t], cs[i]);
-    w[t] = c64d(w[t].re + sign * acc.re, w[t].im + sign * acc.im);
+    for (; i < nv; ++i) cfma(acc, ld(i), cs[i]);
+    w[t] = c64d(w[t].re + sign * (double)acc.re, w[t].im + sign * (double)acc.im);
 }
 
 // Device state of one Arnoldi step, copied to pinned host memory after the
@@ -268,13 +278,22 @@ struct solver {
     }
 
     // out[0 .. nv) = V^H w on the device (two-stage reduction)
-    void dots_dev(const c64d *V, int nv, const c64d *w, c64d *out)
+    // out[i] = V_i^H w for i < nv; lowp: products in FP32 (inner solves of
+    // the chosen form), else FP64
+    void dots_dev(const c64d *V, int nv, const c64d *w, c64d *out, bool lowp = false)
     {
-        // about 2048 CTAs whatever the number of vectors (groups of DVG)
-        const int ng = (nv + DVG - 1) / DVG;
-        const int rch = std::max(128, std::min(RCH, 2048 / ng));
+        // chunks of RT x DEL elements, at most 2048 CTAs over all groups
+        const int ng = nv == 1 ? 1 : (nv + DVG - 1) / DVG;
+        const int64_t want = (n + (int64_t)RT * DEL - 1) / ((int64_t)RT * DEL);
+        const int rch = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min(RCH, std::max(1, 2048 / ng))));
         dim3 g(rch, ng);
-        k_dots<<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>(), rch);
+        if (nv == 1) {
+            if (lowp) k_dots<1, float><<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>(), rch);
+            else k_dots<1, double><<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>(), rch);
+        } else {
+            if (lowp) k_dots<DVG, float><<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>(), rch);
+            else k_dots<DVG, double><<<g, RT, 0, h->stream>>>(V, n, nv, w, n, partial.as<c64d>(), rch);
+        }
         FDA_CHECK_LAUNCH();
         k_dots_finish<<<nv, RT, 0, h->stream>>>(partial.as<c64d>(), nv, out, rch);
         FDA_CHECK_LAUNCH();
@@ -289,9 +308,10 @@ struct solver {
         return sqrt(std::max(d.re, 0.0));
     }
     // w += sign * V c, coefficients c on the device
-    void combine_dev(const c64d *V, int nv, const c64d *c, double sign, c64d *w)
+    void combine_dev(const c64d *V, int nv, const c64d *c, double sign, c64d *w, bool lowp = false)
     {
-        k_combine<<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, n, nv, c, sign, w, n);
+        if (lowp) k_combine<float><<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, n, nv, c, sign, w, n);
+        else k_combine<double><<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, n, nv, c, sign, w, n);
         FDA_CHECK_LAUNCH();
     }
     void collect_matvec_times()
@@ -337,11 +357,12 @@ struct solver {
     void arnoldi_step(c64d *V, int j, double rnorm0, double beta, int precision)
     {
         c64d *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
+        const bool lowp = precision == FDA_CHOSEN_FP32;
         apply_op(vj, vn, precision);
-        dots_dev(V, j + 1, vn, c1d.as<c64d>());
-        combine_dev(V, j + 1, c1d.as<c64d>(), -1.0, vn);
-        dots_dev(V, j + 1, vn, c2d.as<c64d>());
-        combine_dev(V, j + 1, c2d.as<c64d>(), -1.0, vn);
+        dots_dev(V, j + 1, vn, c1d.as<c64d>(), lowp);
+        combine_dev(V, j + 1, c1d.as<c64d>(), -1.0, vn, lowp);
+        dots_dev(V, j + 1, vn, c2d.as<c64d>(), lowp);
+        combine_dev(V, j + 1, c2d.as<c64d>(), -1.0, vn, lowp);
         dots_dev(vn, 1, vn, nrm2d.as<c64d>());
         k_arnoldi_step<<<1, 32, 0, h->stream>>>(j, ldh, c1d.as<c64d>(), c2d.as<c64d>(), nrm2d.as<c64d>(),
                                                 Hd.as<c64d>(), csd.as<c64d>(), snd.as<c64d>(), gd.as<c64d>(),
