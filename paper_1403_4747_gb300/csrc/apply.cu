@@ -694,23 +694,28 @@ void fda_autotune_tc(fda_handle *h)
             fclose(f);
         }
     }
-    auto tune = [&](const char *pass, int l, tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst,
-                    int64_t ds) {
+    const int mmax = std::max(1, h->cfg.max_rhs);
+    // one batch at mr right-hand sides (1 or max_rhs); at max_rhs only the
+    // shapes of 64 or more columns are timed, each launch then being long
+    auto tune1 = [&](const char *pass, int l, tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst,
+                     int64_t ds, int mr) {
         if (B.npairs == 0 || !T.A.p) return;
+        int &tnc = mr == 1 ? B.nc_tuned : B.nc_tm, &tr = mr == 1 ? B.r_tuned : B.r_tm,
+            &tst = mr == 1 ? B.st_tuned : B.st_tm;
         std::string key;
         if (!gpu.empty()) {
             key = gpu + "|" + pass + "|" + std::to_string(l) + "|" + std::to_string(T.Tout) + "|" +
                   std::to_string(T.Tin) + "|" + std::to_string(B.op_start.empty() ? 0 : B.op_start.size() - 1) +
-                  "|" + std::to_string(B.npairs);
+                  "|" + std::to_string(B.npairs) + (mr > 1 ? "|rhs" + std::to_string(mr) : std::string());
             auto it = cache.find(key);
             if (it != cache.end()) {
                 const auto &c = it->second;
                 bool known = false;
                 for (const auto &k : cand) known |= k[0] == c[0] && k[1] == c[1] && k[2] == c[2];
                 if (known && c[1] <= T.nrt) {
-                    B.nc_tuned = c[0];
-                    B.r_tuned = c[1];
-                    B.st_tuned = c[2];
+                    tnc = c[0];
+                    tr = c[1];
+                    tst = c[2];
                     ++h->autotune_cached;
                     return;
                 }
@@ -719,24 +724,28 @@ void fda_autotune_tc(fda_handle *h)
         ++h->autotune_timed;
         float best = 1e30f;
         for (const auto &c : cand) {
-            if (c[1] > T.nrt) continue;
+            if (c[1] > T.nrt || (mr > 1 && c[0] < 64)) continue;
             // an untimed launch builds the shape's tile list; then the
-            // fastest of three launches, each after L2 is flushed
-            fda_run_tc(h, B, T, src, sv, reinterpret_cast<c32f *>(dst), 1, ds, c[0], c[1], c[2]);
+            // fastest of three launches (two at max_rhs), each after L2 is flushed
+            fda_run_tc(h, B, T, src, sv, reinterpret_cast<c32f *>(dst), mr, ds, c[0], c[1], c[2]);
             float ms = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) ms = std::min(ms, timed([&] {
-                fda_run_tc(h, B, T, src, sv, reinterpret_cast<c32f *>(dst), 1, ds, c[0], c[1], c[2]);
+            for (int rep = 0; rep < (mr == 1 ? 3 : 2); ++rep) ms = std::min(ms, timed([&] {
+                fda_run_tc(h, B, T, src, sv, reinterpret_cast<c32f *>(dst), mr, ds, c[0], c[1], c[2]);
             }));
             if (ms < best) {
                 best = ms;
-                B.nc_tuned = c[0];
-                B.r_tuned = c[1];
-                B.st_tuned = c[2];
+                tnc = c[0];
+                tr = c[1];
+                tst = c[2];
             }
         }
         if (!key.empty())
-            added += key + " " + std::to_string(B.nc_tuned) + " " + std::to_string(B.r_tuned) + " " +
-                     std::to_string(B.st_tuned) + "\n";
+            added += key + " " + std::to_string(tnc) + " " + std::to_string(tr) + " " + std::to_string(tst) + "\n";
+    };
+    auto tune = [&](const char *pass, int l, tr_batch &B, tc_ops &T, const dbuf &src, int64_t sv, float *dst,
+                    int64_t ds) {
+        tune1(pass, l, B, T, src, sv, dst, ds, 1);
+        if (mmax > 1) tune1(pass, l, B, T, src, sv, dst, ds, mmax);
     };
     auto sv = [&](int l) { return P.stride[l] / std::max(1, h->lev[l].T); };
     for (int l = h->lev_lo; l < h->nlev; ++l) {
@@ -756,7 +765,6 @@ void fda_autotune_tc(fda_handle *h)
             // the level's M2L in full form against the low-rank form (Sec. 4.2),
             // tuned shapes, for one right-hand side and for max_rhs; the faster
             // form is kept for each
-            const int mmax = std::max(1, h->cfg.max_rhs);
             for (int mr = 1; mr <= mmax; mr = mr == mmax ? mmax + 1 : mmax) {
                 auto full = [&] {
                     fda_run_tc(h, h->b_m2l_all[l], h->tc_m2l[l], h->qs[l], sv(l), reinterpret_cast<c32f *>(P.p[l]),

@@ -152,7 +152,8 @@ struct tr_batch {
     // tensor-core form of the batch: tile lists per (right-hand sides, columns,
     // row tiles) and the autotuner's shape for one right-hand side (0 = rule)
     std::deque<tile_set> tc_tilesets;
-    int nc_tuned = 0, r_tuned = 1, st_tuned = 0;
+    int nc_tuned = 0, r_tuned = 1, st_tuned = 0;  // tuned tile shape at one right-hand side
+    int nc_tm = 0, r_tm = 1, st_tm = 0;           // and at max_rhs right-hand sides
 };
 
 // tensor-core form of a set of translation operators: bf16 hi/lo panels

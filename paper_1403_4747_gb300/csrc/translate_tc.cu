@@ -498,13 +498,17 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     const int nops = (int)B.op_start.size() - 1;
     const double avg_cols = (double)B.npairs * mr / std::max(1, nops);
     // tile shape (columns, row tiles, ring stages): the caller's, else the
-    // tuned one (one right-hand side), else narrow tiles where an operator
-    // has few columns, one row tile, four stages
+    // tuned one (at one or at max_rhs right-hand sides), else narrow tiles
+    // where an operator has few columns, one row tile, four stages
     int NC = avg_cols < 48.0 ? 32 : (avg_cols < 256.0 ? 64 : 128), R = 1, ST = NC == 128 ? 3 : 4;
     if (mr == 1 && B.nc_tuned) {
         NC = B.nc_tuned;
         R = B.r_tuned;
         ST = B.st_tuned;
+    } else if (mr > 1 && B.nc_tm) {
+        NC = B.nc_tm;
+        R = B.r_tm;
+        ST = B.st_tm;
     }
     if (!nc && !rows && !st && h->tc_force[0]) {
         nc = h->tc_force[0];
