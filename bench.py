@@ -34,6 +34,15 @@ METRIC = "FDA matvec/s & GMRES solve s, kD=100 N=327,680, plain vs chosen form @
 WORKLOAD = "rigid unit sphere, icosphere level 7 (327,680 triangles), k=50 (kD=100), plane wave +z, eps=1e-4"
 
 
+def _workload(args, n):
+    """The headline workload's name, or the same description for another
+    --level / --k / --eps."""
+    if (args.level, args.k, args.eps) == (7, 50.0, 1e-4):
+        return WORKLOAD
+    return "rigid unit sphere, icosphere level %d (%s triangles), k=%g (kD=%g), plane wave +z, eps=%g" % (
+        args.level, format(n, ","), args.k, 2 * args.k, args.eps)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -186,7 +195,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": n, "k": args.k},
+            "config": {"workload": _workload(args, n), "N": n, "k": args.k},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "matvec/s", "cores": cores,
                              "sample": "%d sampled rows of the dense FP64 oracle matvec per step (of %d)" % (rows_n, n)},
             "e2e": {"value": value, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -479,7 +488,7 @@ def run_native(args):
     line = {"metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": n, "k": k, "eps": args.eps, "leaf_max": 64,
+            "config": {"workload": _workload(args, n), "N": n, "k": k, "eps": args.eps, "leaf_max": 64,
                        "form": "chosen (FP32 far field and near storage, FP64 setup)",
                        "l2": "inputs larger than L2 (near-field matrix %.2f GB FP32)" % (st.bytes_near / 2 / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},

@@ -87,7 +87,7 @@ __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv
 // overlap the MMAs of tile j + 1.  Every wait is bounded and also gives up
 // once another role has recorded an error; the CTA then waits (bounded) for
 // its copies and MMAs in flight, frees its tensor memory and returns.
-constexpr int EPC = 16;          // epilogue chunk: accumulator columns staged per pass
+constexpr int EPC = 16;          // epilogue chunk: accumulator columns read from tensor memory per pass
 constexpr int WS_THREADS = 288;  // 9 warps
 constexpr int NPROD = 128;       // producer threads (warps 5-8)
 
@@ -108,7 +108,6 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
     constexpr int TALLOC = NSLOT * SLOT <= 128 ? 128 : (NSLOT * SLOT <= 256 ? 256 : 512);  // power of two
     static_assert(NSLOT * SLOT <= 512, "accumulators exceed tensor memory");
     static_assert(NC <= NPROD, "one tile column per producer thread");
-    float2 *stg = reinterpret_cast<float2 *>(smem + ST * STAGE);  // epilogue staging [EPC][128 lanes]
     __shared__ long long srcv[NC];             // producers: source vector per column of the current tile
     __shared__ int stage_nr[ST];               // row tiles present in the tile of each stage
     __shared__ long long tgt[NC];              // epilogue: target offset per column of the current tile
@@ -282,11 +281,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
         __syncwarp();
     } else {
         // ---------------- epilogue (warps 0-3 = TMEM lanes 0-127)
-        // lane r < 64 holds Ar rows (D1 -> Re, D2 -> Im); lane r >= 64 holds
-        // Ai rows (D1 -> Im, D2 -> -Re).  Per chunk of EPC columns every lane
-        // stages (D1, D2) column-major; then thread (row, half) combines the
-        // two lanes of its row for EPC / 2 columns and adds them to the target.
-        const int row = (warp & 1) * 32 + lane, half = warp >> 1;
+        // The panels interleave the real and imaginary rows: lane 2i holds
+        // Ar_i (D1 = Ar xr, D2 = Ar xi), lane 2i + 1 holds Ai_i (D1 = Ai xr,
+        // D2 = Ai xi), so the two lanes of complex row i are neighbours in one
+        // warp.  Of each pair of columns the even lane finishes the first and
+        // the odd lane the second after one exchange of two values
+        // (Re = Ar xr - Ai xi, Im = Ar xi + Ai xr), and adds it to the target.
+        const int odd = lane & 1, row = warp * 16 + (lane >> 1);
         for (int j = 0; j < my_tiles; ++j) {
             const int slot = j % NSLOT;
             const tc_tile t = tiles[blockIdx.x + (int64_t)j * gridDim.x];
@@ -316,21 +317,21 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_btr_tc(const tc_tile *tiles, 
                     uint32_t v1[16], v2[16];
                     tmem_ld16x2(d1 + c0, d2 + c0, v1, v2);
 #pragma unroll
-                    for (int jj = 0; jj < EPC; ++jj)
-                        stg[jj * 128 + tid] = make_float2(__uint_as_float(v1[jj]), __uint_as_float(v2[jj]));
-                    asm volatile("bar.sync 2, 128;");
-                    if (rowg < Tout) {
-#pragma unroll
-                        for (int jj = half * (EPC / 2); jj < (half + 1) * (EPC / 2); ++jj) {
-                            const int n = c0 + jj;
-                            if (n < t.npair) {
-                                const float2 top = stg[jj * 128 + row], bot = stg[jj * 128 + 64 + row];
-                                atomicAdd(reinterpret_cast<float2 *>(dst + tgt[n] + rowg),
-                                          make_float2(top.x - bot.y, top.y + bot.x));
-                            }
+                    for (int jj = 0; jj < EPC; jj += 2) {
+                        // the even lane needs the odd lane's column jj, the odd lane the even lane's jj + 1
+                        const float s1 = __uint_as_float(odd ? v1[jj] : v1[jj + 1]);
+                        const float s2 = __uint_as_float(odd ? v2[jj] : v2[jj + 1]);
+                        const float p1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+                        const float p2 = __shfl_xor_sync(0xffffffffu, s2, 1);
+                        const int n = c0 + jj + odd;
+                        if (rowg < Tout && n < t.npair) {
+                            const float2 v = odd ? make_float2(p1 - __uint_as_float(v2[jj + 1]),
+                                                               p2 + __uint_as_float(v1[jj + 1]))
+                                                 : make_float2(__uint_as_float(v1[jj]) - p2,
+                                                               __uint_as_float(v2[jj]) + p1);
+                            atomicAdd(reinterpret_cast<float2 *>(dst + tgt[n] + rowg), v);
                         }
                     }
-                    asm volatile("bar.sync 2, 128;");
                 }
             }
             // this slot is read: the MMAs of tile j + NSLOT may overwrite it
@@ -366,8 +367,8 @@ __global__ void k_pack_tc(const c64d *ops, int nops, int Tout, int Tin, int nrt,
         int64_t r3 = r2 / nkc;
         int rt = (int)(r3 % nrt);
         int op = (int)(r3 / nrt);
-        int part = r >> 6;                  // rows 0-63: Re(A), rows 64-127: Im(A)
-        int i = rt * 64 + (r & 63);         // complex row
+        int part = r & 1;                   // even rows Re(A), odd rows Im(A) of the same complex row
+        int i = rt * 64 + (r >> 1);         // complex row
         int j = kc * KC + k;                // complex column
         double v = 0.0;
         if (i < Tout && j < Tin) {
@@ -401,7 +402,7 @@ template <int NC, int R, int ST>
 void launch_tc(const tc_args &a, int ntiles, cudaStream_t s)
 {
     const size_t stage = (size_t)R * 2 * ABYTES + 4 * (size_t)NC * KC * 2;
-    const size_t smem = 128 + ST * stage + (size_t)EPC * 128 * sizeof(float2);
+    const size_t smem = 128 + ST * stage;
     static int per_sm = 0, nsm = 0;  // resident CTAs per SM for this instantiation
     if (!per_sm) {
         int dev = 0;
@@ -520,9 +521,9 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (st) ST = st;
     // the instantiated shapes (columns, row tiles, stages):
     // (32,1,2) (32,1,4) (64,1,2) (64,1,4) (128,1,3) (128,1,4) (32,2,4) (64,2,3) (64,2,4) (128,2,2)
-    // (32,3,3) (64,4,2)
+    // (32,3,3) (32,3,4) (64,4,2)
     if (R > P.nrt) R = 1;
-    if (R == 3) NC = 32, ST = 3;
+    if (R == 3) NC = 32, ST = ST == 4 ? 4 : 3;
     if (R == 4) NC = 64, ST = 2;
     if (R == 2) ST = NC == 32 ? 4 : (NC == 64 ? (ST == 4 ? 4 : 3) : 2);
     if (R == 1) ST = NC == 128 ? (ST == 4 ? 4 : 3) : (ST == 2 ? 2 : 4);
@@ -554,7 +555,8 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (R == 4) {
         launch_tc<64, 4, 2>(a, ts->n, h->stream);
     } else if (R == 3) {
-        launch_tc<32, 3, 3>(a, ts->n, h->stream);
+        if (ST == 4) launch_tc<32, 3, 4>(a, ts->n, h->stream);
+        else launch_tc<32, 3, 3>(a, ts->n, h->stream);
     } else if (R == 2) {
         if (NC == 32) launch_tc<32, 2, 4>(a, ts->n, h->stream);
         else if (NC == 64 && ST == 4) launch_tc<64, 2, 4>(a, ts->n, h->stream);
