@@ -327,8 +327,8 @@ fda_status fda_get_tree(fda_handle *h, int32_t *box_level, int32_t *box_coord, i
  * Steps 2-3 on the tensor cores) for later calls, in place of the
  * autotuner's choice: (columns per tile, 64-row tiles per CTA tile, ring
  * stages) one of (32,1,2), (32,1,4), (64,1,2), (64,1,4), (32,2,4), (64,2,3),
- * (64,2,4), (32,3,3), (32,3,4), (128,1,3), (128,1,4), (128,2,2), (64,4,2) (the last two with one
- * accumulator slot); (0,0,0) returns to the tuned shapes.  A shape with
+ * (64,2,4), (32,3,3), (32,3,4), (128,1,3), (128,1,4), (128,2,2), (128,2,3), (64,3,3),
+ * (64,4,2) (the last four with one accumulator slot); (0,0,0) returns to the tuned shapes.  A shape with
  * more row tiles than an operator has falls back to one row tile there.
  * Captured graphs are released (the next applies capture again).  Results
  * equal the tuned shapes' up to the rounding order of the float atomics.

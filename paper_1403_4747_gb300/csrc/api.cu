@@ -659,9 +659,9 @@ fda_status fda_get_tree(fda_handle *h, int32_t *box_level, int32_t *box_coord, i
 fda_status fda_set_tc_tiles(fda_handle *h, int columns, int row_tiles, int stages)
 {
     if (!h) return FDA_ERR_ARG;
-    static const int shapes[13][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4}, {64, 2, 3},
-                                      {64, 2, 4}, {32, 3, 3}, {32, 3, 4}, {128, 1, 3}, {128, 1, 4}, {128, 2, 2},
-                                      {64, 4, 2}};
+    static const int shapes[15][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4},
+                                      {64, 2, 3}, {64, 2, 4}, {32, 3, 3}, {32, 3, 4}, {128, 1, 3},
+                                      {128, 1, 4}, {128, 2, 2}, {128, 2, 3}, {64, 3, 3}, {64, 4, 2}};
     bool known = columns == 0 && row_tiles == 0 && stages == 0;
     for (const auto &c : shapes) known |= c[0] == columns && c[1] == row_tiles && c[2] == stages;
     if (!known) {

@@ -660,8 +660,9 @@ void fda_autotune_tc(fda_handle *h)
     FDA_CUDA(cudaEventCreate(&e1));
     lvl_ptrs<float> P = make_ptrs<float>(h, h->op32, h->q32, h->p32);
     // (columns, row tiles, stages)
-    static const int cand[13][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4}, {64, 2, 3}, {64, 2, 4},
-                                    {32, 3, 3}, {32, 3, 4}, {128, 1, 3}, {128, 1, 4}, {128, 2, 2}, {64, 4, 2}};
+    static const int cand[15][3] = {{32, 1, 2}, {32, 1, 4}, {64, 1, 2}, {64, 1, 4}, {32, 2, 4},
+                                    {64, 2, 3}, {64, 2, 4}, {32, 3, 3}, {32, 3, 4}, {128, 1, 3},
+                                    {128, 1, 4}, {128, 2, 2}, {128, 2, 3}, {64, 3, 3}, {64, 4, 2}};
     // launches are timed from a cold L2, as in an apply, where the other
     // passes evict the operators between two launches of one batch
     dbuf flush;

@@ -521,11 +521,14 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (st) ST = st;
     // the instantiated shapes (columns, row tiles, stages):
     // (32,1,2) (32,1,4) (64,1,2) (64,1,4) (128,1,3) (128,1,4) (32,2,4) (64,2,3) (64,2,4) (128,2,2)
-    // (32,3,3) (32,3,4) (64,4,2)
+    // (128,2,3) (32,3,3) (32,3,4) (64,3,3) (64,4,2)
     if (R > P.nrt) R = 1;
-    if (R == 3) NC = 32, ST = ST == 4 ? 4 : 3;
+    if (R == 3) {
+        if (NC == 64) ST = 3;
+        else NC = 32, ST = ST == 4 ? 4 : 3;
+    }
     if (R == 4) NC = 64, ST = 2;
-    if (R == 2) ST = NC == 32 ? 4 : (NC == 64 ? (ST == 4 ? 4 : 3) : 2);
+    if (R == 2) ST = NC == 32 ? 4 : (NC == 64 ? (ST == 4 ? 4 : 3) : (ST == 3 ? 3 : 2));
     if (R == 1) ST = NC == 128 ? (ST == 4 ? 4 : 3) : (ST == 2 ? 2 : 4);
     const tile_set *ts = nullptr;
     for (const auto &t : B.tc_tilesets)
@@ -555,12 +558,14 @@ void fda_run_tc(fda_handle *h, tr_batch &B, tc_ops &P, const dbuf &src, int64_t 
     if (R == 4) {
         launch_tc<64, 4, 2>(a, ts->n, h->stream);
     } else if (R == 3) {
-        if (ST == 4) launch_tc<32, 3, 4>(a, ts->n, h->stream);
+        if (NC == 64) launch_tc<64, 3, 3>(a, ts->n, h->stream);
+        else if (ST == 4) launch_tc<32, 3, 4>(a, ts->n, h->stream);
         else launch_tc<32, 3, 3>(a, ts->n, h->stream);
     } else if (R == 2) {
         if (NC == 32) launch_tc<32, 2, 4>(a, ts->n, h->stream);
         else if (NC == 64 && ST == 4) launch_tc<64, 2, 4>(a, ts->n, h->stream);
         else if (NC == 64) launch_tc<64, 2, 3>(a, ts->n, h->stream);
+        else if (ST == 3) launch_tc<128, 2, 3>(a, ts->n, h->stream);
         else launch_tc<128, 2, 2>(a, ts->n, h->stream);
     } else if (NC == 128) {
         if (ST == 4) launch_tc<128, 1, 4>(a, ts->n, h->stream);

@@ -9,7 +9,7 @@ per operator), which no smaller mesh reaches.  The reference is 256 rows
 the FDA's accuracy eps = 1e-4 (Eq. epsg) as a relative L2 error over the
 sampled rows, for
   - the chosen form with the autotuned tile shapes and with each of the
-    thirteen tile shapes the tensor-core translation kernel can launch, forced
+    fifteen tile shapes the tensor-core translation kernel can launch, forced
     through fda_set_tc_tiles (these also agree with the tuned result to the
     rounding order of the float atomics);
   - the plain FP64 form;
@@ -34,7 +34,7 @@ torch = pytest.importorskip("torch")
 K = 50.0
 ROWS = 256
 SHAPES = [(32, 1, 2), (32, 1, 4), (64, 1, 2), (64, 1, 4), (32, 2, 4), (64, 2, 3), (64, 2, 4), (32, 3, 3),
-          (32, 3, 4), (128, 1, 3), (128, 1, 4), (128, 2, 2), (64, 4, 2)]
+          (32, 3, 4), (128, 1, 3), (128, 1, 4), (128, 2, 2), (128, 2, 3), (64, 3, 3), (64, 4, 2)]
 
 
 @pytest.fixture(scope="module", autouse=True)
