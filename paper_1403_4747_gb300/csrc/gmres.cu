@@ -38,11 +38,11 @@ constexpr int DEL = 4;     // elements per thread and chunk (chunks of RT x DEL 
 // would otherwise make these memory-sized passes compute-bound.
 constexpr int DVG = 8;  // vectors per CTA
 template <int G, typename P>
-__global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv, const c64d *w, int64_t n,
-                                             c64d *partial, int rch)
+__device__ __forceinline__ void dots_group(const c64d *V, int64_t ldv, int nv, const c64d *w, int64_t n,
+                                           c64d *partial, int rch, int i0)
 {
     __shared__ double sr[RT / 32][G], si[RT / 32][G];
-    const int c = blockIdx.x, i0 = blockIdx.y * G, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ng = min(G, nv - i0);
     const int64_t per = (n + rch - 1) / rch;
     const int64_t b = (int64_t)c * per, e = b + per < n ? b + per : n;
@@ -83,10 +83,16 @@ __global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv,
         partial[(int64_t)(i0 + threadIdx.x) * rch + c] = c64d(r, im);
     }
 }
-__global__ void k_dots_finish(const c64d *partial, int nv, c64d *out, int rch)
+template <int G, typename P>
+__global__ void __launch_bounds__(RT) k_dots(const c64d *V, int64_t ldv, int nv, const c64d *w, int64_t n,
+                                             c64d *partial, int rch)
+{
+    dots_group<G, P>(V, ldv, nv, w, n, partial, rch, blockIdx.y * G);
+}
+
+__device__ __forceinline__ void finish_one(const c64d *partial, int i, c64d *out, int rch)
 {
     __shared__ double sr[RT], si[RT];
-    int i = blockIdx.x;
     double ar = 0.0, ai = 0.0;
     for (int c = threadIdx.x; c < rch; c += RT) {
         ar += partial[(int64_t)i * rch + c].re;
@@ -105,16 +111,25 @@ __global__ void k_dots_finish(const c64d *partial, int nv, c64d *out, int rch)
     if (threadIdx.x == 0) out[i] = c64d(sr[0], si[0]);
 }
 
+__global__ void k_dots_finish(const c64d *partial, int nv, c64d *out, int rch)
+{
+    finish_one(partial, blockIdx.x, out, rch);
+}
+
 // w[n] += sign * sum_i V_i[n] c[i]; the coefficients are staged in shared
 // memory and the vectors read four at a time; the sum is formed in P (as in
 // k_dots) and added to w in FP64
 template <typename P>
-__global__ void __launch_bounds__(RT) k_combine(const c64d *V, int64_t ldv, int nv, const c64d *c, double sign,
-                                                c64d *w, int64_t n)
+__device__ __forceinline__ void combine_body(const c64d *V, int64_t ldv, int nv, const c64d *c, double sign,
+                                             c64d *w, int64_t n)
 {
-    __shared__ cx<P> cs[256];
-    for (int i = threadIdx.x; i < nv && i < 256; i += RT) cs[i] = cx<P>((P)c[i].re, (P)c[i].im);
+    __shared__ P csr[256], csi[256];
+    for (int i = threadIdx.x; i < nv && i < 256; i += RT) {
+        csr[i] = (P)c[i].re;
+        csi[i] = (P)c[i].im;
+    }
     __syncthreads();
+    auto cs = [&](int i) { return cx<P>(csr[i], csi[i]); };
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     auto ld = [&](int i) {
@@ -125,13 +140,50 @@ __global__ void __launch_bounds__(RT) k_combine(const c64d *V, int64_t ldv, int 
     int i = 0;
     for (; i + 3 < nv; i += 4) {
         const cx<P> a0 = ld(i), a1 = ld(i + 1), a2 = ld(i + 2), a3 = ld(i + 3);
-        cfma(acc, a0, cs[i]);
-        cfma(acc, a1, cs[i + 1]);
-        cfma(acc, a2, cs[i + 2]);
-        cfma(acc, a3, cs[i + 3]);
+        cfma(acc, a0, cs(i));
+        cfma(acc, a1, cs(i + 1));
+        cfma(acc, a2, cs(i + 2));
+        cfma(acc, a3, cs(i + 3));
     }
-    for (; i < nv; ++i) cfma(acc, ld(i), cs[i]);
+    for (; i < nv; ++i) cfma(acc, ld(i), cs(i));
     w[t] = c64d(w[t].re + sign * (double)acc.re, w[t].im + sign * (double)acc.im);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(RT) k_combine(const c64d *V, int64_t ldv, int nv, const c64d *c, double sign,
+                                                c64d *w, int64_t n)
+{
+    combine_body<P>(V, ldv, nv, c, sign, w, n);
+}
+
+// ---- the Gram-Schmidt part of Arnoldi step j with j read from device
+// memory (*jd), so that one captured graph serves every step of a cycle:
+// w = V_{j+1} (the new product), nv = j + 1 basis vectors (1 with self: the
+// dot product of w with itself)
+template <int G, typename P>
+__global__ void __launch_bounds__(RT) k_dots_j(const c64d *V, int64_t n, const int *jd, int self, c64d *partial,
+                                               int rch)
+{
+    const int j = *jd;
+    const c64d *w = V + (int64_t)(j + 1) * n;
+    const int nv = self ? 1 : j + 1;
+    for (int i0 = 0; i0 < nv; i0 += G) {  // the groups one after another: w is re-read from L2
+        dots_group<G, P>(self ? w : V, n, nv, w, n, partial, rch, i0);
+        __syncthreads();
+    }
+}
+
+__global__ void k_dots_finish_j(const c64d *partial, const int *jd, int self, c64d *out, int rch)
+{
+    const int nv = self ? 1 : *jd + 1;
+    if ((int)blockIdx.x < nv) finish_one(partial, blockIdx.x, out, rch);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(RT) k_combine_j(c64d *V, int64_t n, const int *jd, const c64d *c, double sign)
+{
+    const int j = *jd;
+    combine_body<P>(V, n, j + 1, c, sign, V + (int64_t)(j + 1) * n, n);
 }
 
 // Device state of one Arnoldi step, copied to pinned host memory after the
@@ -147,10 +199,9 @@ struct gm_status {
 // previous Givens rotations applied to it, the new rotation that zeroes
 // h_{j+1}, and the rotated right-hand side g of the least-squares problem.
 // H is column-major with leading dimension ldh; *scale receives 1/||w||.
-__global__ void k_arnoldi_step(int j, int ldh, const c64d *c1, const c64d *c2, const c64d *nrm2, c64d *H, c64d *cs,
-                               c64d *sn, c64d *g, double rnorm0, double beta, double *scale, gm_status *st)
+__device__ void arnoldi_body(int j, int ldh, const c64d *c1, const c64d *c2, const c64d *nrm2, c64d *H, c64d *cs,
+                             c64d *sn, c64d *g, double rnorm0, double beta, double *scale, gm_status *st)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     c64d *hc = H + (int64_t)j * ldh;
     int bad = 0;
     for (int i = 0; i <= j; ++i) {
@@ -189,19 +240,39 @@ __global__ void k_arnoldi_step(int j, int ldh, const c64d *c1, const c64d *c2, c
     st->j = j;
 }
 
-__global__ void k_gmres_init(c64d *g, int n, double beta)
+// the same with j read from *jd and its status in slot j % ring of st; the
+// step then advances *jd (the next step's Gram-Schmidt kernels read it)
+__global__ void k_arnoldi_step_j(int *jd, int ldh, const c64d *c1, const c64d *c2, const c64d *nrm2, c64d *H,
+                                 c64d *cs, c64d *sn, c64d *g, const double *rb, double *scale, gm_status *st,
+                                 int ring)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) g[t] = c64d(t == 0 ? beta : 0.0, 0.0);
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = *jd;
+    arnoldi_body(j, ldh, c1, c2, nrm2, H, cs, sn, g, rb[0], rb[1], scale, st + j % ring);
+    *jd = j + 1;
 }
 
-// x *= *s (a scale the device computed)
-__global__ void k_scale_dev(c64d *x, const double *s, int64_t n)
+// V_{*jd} *= *s (the new basis vector, after the step advanced *jd)
+__global__ void k_scale_j(c64d *V, int64_t n, const int *jd, const double *s)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < n) {
+        c64d *x = V + (int64_t)(*jd) * n;
         const double f = *s;
         x[t] = c64d(x[t].re * f, x[t].im * f);
+    }
+}
+
+// start of a restart cycle: g = beta e_1, step index 0, and the cycle's
+// ||r_0|| and beta for the Arnoldi kernel (rb)
+__global__ void k_gmres_init(c64d *g, int n, double beta, int *jd, double *rb, double rnorm0)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) g[t] = c64d(t == 0 ? beta : 0.0, 0.0);
+    if (t == 0) {
+        *jd = 0;
+        rb[0] = rnorm0;
+        rb[1] = beta;
     }
 }
 
@@ -226,7 +297,12 @@ struct solver {
     // device state of the current restart cycle: Hessenberg columns (ldh =
     // m + 1), Givens rotations, rotated right-hand side, Gram-Schmidt
     // coefficients of the two passes, ||w||^2, 1/||w||, step status
-    dbuf Hd, csd, snd, gd, c1d, c2d, nrm2d, scaled, std_, yd;
+    dbuf Hd, csd, snd, gd, c1d, c2d, nrm2d, scaled, st_ring, yd, jd, rb;
+    // the Gram-Schmidt part of a step as one graph per basis (V) and
+    // product arithmetic (FP64, FP32), captured on a private stream
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gsx[2] = {};
+    const c64d *gsV[2] = {};
     gm_status *hst = nullptr;   // pinned: status of the last RING steps
     c64d *hH = nullptr, *hg = nullptr, *hy = nullptr;  // pinned: H, g, y of a cycle
     static constexpr int RING = 4;
@@ -245,6 +321,9 @@ struct solver {
             if (mv0[i]) cudaEventDestroy(mv0[i]);
             if (mv1[i]) cudaEventDestroy(mv1[i]);
         }
+        for (int i = 0; i < 2; ++i)
+            if (gsx[i]) cudaGraphExecDestroy(gsx[i]);
+        if (cap) cudaStreamDestroy(cap);
         if (hst) cudaFreeHost(hst);
         if (hH) cudaFreeHost(hH);
         if (hg) cudaFreeHost(hg);
@@ -264,7 +343,10 @@ struct solver {
         c2d.alloc(sizeof(c64d) * (m + 1));
         nrm2d.alloc(sizeof(c64d));
         scaled.alloc(sizeof(double));
-        std_.alloc(sizeof(gm_status));
+        st_ring.alloc(sizeof(gm_status) * RING);
+        jd.alloc(sizeof(int));
+        rb.alloc(2 * sizeof(double));
+        FDA_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         yd.alloc(sizeof(c64d) * (m + 1));
         FDA_CUDA(cudaMallocHost(&hst, sizeof(gm_status) * RING));
         FDA_CUDA(cudaMallocHost(&hH, sizeof(c64d) * (size_t)ldh * m));
@@ -277,7 +359,6 @@ struct solver {
         }
     }
 
-    // out[0 .. nv) = V^H w on the device (two-stage reduction)
     // out[i] = V_i^H w for i < nv; lowp: products in FP32 (inner solves of
     // the chosen form), else FP64
     void dots_dev(const c64d *V, int nv, const c64d *w, c64d *out, bool lowp = false)
@@ -352,25 +433,73 @@ struct solver {
         ++nmatvec;
     }
 
+    // the Gram-Schmidt part of the step whose product is V_{*jd + 1}: two
+    // CGS passes, ||w||, the Hessenberg column and Givens rotation, the
+    // scaling of the new basis vector, and the status ring to the host
+    void gs_launch(cudaStream_t s, c64d *V, bool lowp)
+    {
+        const int rch = (int)std::max<int64_t>(1, std::min<int64_t>(RCH, (n + (int64_t)RT * DEL - 1) /
+                                                                             ((int64_t)RT * DEL)));
+        for (int pass = 0; pass < 2; ++pass) {
+            c64d *c = (pass ? c2d : c1d).as<c64d>();
+            if (lowp) k_dots_j<DVG, float><<<rch, RT, 0, s>>>(V, n, jd.as<int>(), 0, partial.as<c64d>(), rch);
+            else k_dots_j<DVG, double><<<rch, RT, 0, s>>>(V, n, jd.as<int>(), 0, partial.as<c64d>(), rch);
+            FDA_CHECK_LAUNCH();
+            k_dots_finish_j<<<ldh, RT, 0, s>>>(partial.as<c64d>(), jd.as<int>(), 0, c, rch);
+            FDA_CHECK_LAUNCH();
+            if (lowp) k_combine_j<float><<<fda_blocks(n, RT), RT, 0, s>>>(V, n, jd.as<int>(), c, -1.0);
+            else k_combine_j<double><<<fda_blocks(n, RT), RT, 0, s>>>(V, n, jd.as<int>(), c, -1.0);
+            FDA_CHECK_LAUNCH();
+        }
+        k_dots_j<1, double><<<rch, RT, 0, s>>>(V, n, jd.as<int>(), 1, partial.as<c64d>(), rch);
+        FDA_CHECK_LAUNCH();
+        k_dots_finish_j<<<1, RT, 0, s>>>(partial.as<c64d>(), jd.as<int>(), 1, nrm2d.as<c64d>(), rch);
+        FDA_CHECK_LAUNCH();
+        k_arnoldi_step_j<<<1, 32, 0, s>>>(jd.as<int>(), ldh, c1d.as<c64d>(), c2d.as<c64d>(), nrm2d.as<c64d>(),
+                                          Hd.as<c64d>(), csd.as<c64d>(), snd.as<c64d>(), gd.as<c64d>(),
+                                          rb.as<double>(), scaled.as<double>(), st_ring.as<gm_status>(), RING);
+        FDA_CHECK_LAUNCH();
+        k_scale_j<<<fda_blocks(n, RT), RT, 0, s>>>(V, n, jd.as<int>(), scaled.as<double>());
+        FDA_CHECK_LAUNCH();
+        FDA_CUDA(cudaMemcpyAsync(hst, st_ring.p, sizeof(gm_status) * RING, cudaMemcpyDeviceToHost, s));
+    }
+    // capture gs_launch for this basis once; on failure the kernels are
+    // launched one by one
+    void gs_graph(c64d *V, bool lowp)
+    {
+        const int i = lowp ? 1 : 0;
+        if (gsV[i] == V && gsx[i]) return;
+        if (gsx[i]) cudaGraphExecDestroy(gsx[i]);
+        gsx[i] = nullptr;
+        gsV[i] = V;
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            try {
+                gs_launch(cap, V, lowp);
+            } catch (...) {
+                ok = false;
+            }
+            ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && ok && g;
+        }
+        if (ok) ok = cudaGraphInstantiate(&gsx[i], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            (void)cudaGetLastError();
+            gsx[i] = nullptr;
+        }
+    }
+
     // one Arnoldi step j of the current cycle, enqueued without
-    // synchronisation; its status lands in hst[j % RING], signalled by sev[]
-    void arnoldi_step(c64d *V, int j, double rnorm0, double beta, int precision)
+    // synchronisation; the status ring lands in hst, signalled by sev[j % RING]
+    void arnoldi_step(c64d *V, int j, int precision)
     {
         c64d *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
         const bool lowp = precision == FDA_CHOSEN_FP32;
         apply_op(vj, vn, precision);
-        dots_dev(V, j + 1, vn, c1d.as<c64d>(), lowp);
-        combine_dev(V, j + 1, c1d.as<c64d>(), -1.0, vn, lowp);
-        dots_dev(V, j + 1, vn, c2d.as<c64d>(), lowp);
-        combine_dev(V, j + 1, c2d.as<c64d>(), -1.0, vn, lowp);
-        dots_dev(vn, 1, vn, nrm2d.as<c64d>());
-        k_arnoldi_step<<<1, 32, 0, h->stream>>>(j, ldh, c1d.as<c64d>(), c2d.as<c64d>(), nrm2d.as<c64d>(),
-                                                Hd.as<c64d>(), csd.as<c64d>(), snd.as<c64d>(), gd.as<c64d>(),
-                                                rnorm0, beta, scaled.as<double>(), std_.as<gm_status>());
-        FDA_CHECK_LAUNCH();
-        k_scale_dev<<<fda_blocks(n, RT), RT, 0, h->stream>>>(vn, scaled.as<double>(), n);
-        FDA_CHECK_LAUNCH();
-        FDA_CUDA(cudaMemcpyAsync(hst + j % RING, std_.p, sizeof(gm_status), cudaMemcpyDeviceToHost, h->stream));
+        const int i = lowp ? 1 : 0;
+        if (gsx[i] && gsV[i] == V) FDA_CUDA(cudaGraphLaunch(gsx[i], h->stream));
+        else gs_launch(h->stream, V, lowp);
         FDA_CUDA(cudaEventRecord(sev[j % RING], h->stream));
     }
     const gm_status &status(int j)
@@ -392,6 +521,7 @@ struct solver {
         Vb.alloc(sizeof(c64d) * (size_t)(m + 1) * n);
         w.alloc(sizeof(c64d) * n);
         c64d *V = Vb.as<c64d>();
+        gs_graph(V, precision == FDA_CHOSEN_FP32);
         double rnorm0 = norm(r);
         iters_out = 0;
         est = 0.0;
@@ -418,7 +548,8 @@ struct solver {
             if (it >= maxit) return 1;
             k_scale<<<fda_blocks(n, RT), RT, 0, h->stream>>>(V, 1.0 / beta, n);
             FDA_CHECK_LAUNCH();
-            k_gmres_init<<<1, 256, 0, h->stream>>>(gd.as<c64d>(), m + 1, beta);
+            k_gmres_init<<<1, 256, 0, h->stream>>>(gd.as<c64d>(), m + 1, beta, jd.as<int>(), rb.as<double>(),
+                                                   rnorm0);
             FDA_CHECK_LAUNCH();
             // Arnoldi steps: step j is enqueued before the host waits for the
             // status of step j - 1, so the device always has work queued; once
@@ -428,7 +559,7 @@ struct solver {
             bool eager = false;    // wait for each step's own status
             double e_prev = est, e_prev2 = est;
             for (int j = 0; j < m && it < maxit; ++j) {
-                arnoldi_step(V, j, rnorm0, beta, precision);
+                arnoldi_step(V, j, precision);
                 ++it;
                 ++iters_out;
                 jend = j + 1;
