@@ -5,8 +5,10 @@
 // restart cycle stays on the device in FP64: the Krylov basis, the operator,
 // the Gram-Schmidt coefficients, the Hessenberg column, the Givens rotations
 // and the residual estimate |g_{j+1}| / ||r_0|| of the small least-squares
-// problem.  The host only enqueues each Arnoldi step and reads the estimate
-// of the step before (so the GPU always has the next step queued); once the
+// problem.  The host only enqueues each Arnoldi step (two graph launches: the
+// product, then the rest of the step, whose kernels read the step index from
+// device memory) and reads the estimate of the step before (so the GPU
+// always has the next step queued); once the
 // estimate predicts convergence within a step it reads every step's estimate
 // as soon as that step ends.  A restart cycle ends with one synchronisation:
 // the back substitution on the (at most 255 x 255) triangular system and the
@@ -14,7 +16,8 @@
 //
 // Chosen precision: GMRES runs on the FP32 FDA operator, inside an outer
 // loop that re-evaluates the true residual b - A x with the FP64 operator
-// (iterative refinement); convergence is judged on that FP64 residual.
+// (iterative refinement); convergence is judged on that FP64 residual.  The
+// inner solves form their Gram-Schmidt products in FP32 (summed in FP64).
 #include <math.h>
 
 #include <chrono>
