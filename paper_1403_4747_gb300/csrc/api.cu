@@ -85,7 +85,7 @@ size_t handle_bytes(const fda_handle *h)
                           &h->nr_begin, &h->nr_end, &h->nf_colptr, &h->nf_cols, &h->nf_off, &h->leaf_op_off,
                           &h->op64.St, &h->op64.Tt, &h->op64.near, &h->op32.St, &h->op32.Tt, &h->op32.near,
                           &h->op64.St1, &h->op64.near1, &h->op32.St1, &h->op32.near1,
-                          &h->xs, &h->ys, &h->xs32};
+                          &h->xs, &h->ys, &h->xs32, &h->tt32c, &h->tt_c_off, &h->sai_M, &h->sai_M32, &h->pc_M};
     for (const dbuf *b : bufs) s += b->bytes;
     for (int l = 0; l < FDA_MAX_LEVELS; ++l) {
         s += h->eq_up[l].bytes + h->chk_up[l].bytes + h->rot[l].bytes + h->Uup[l].bytes + h->Vup[l].bytes +

@@ -283,13 +283,14 @@ __global__ void __launch_bounds__(32 * LPB) k_s2m_w(lvl_ptrs<R> P, int nleaf, co
 template <typename R>
 __global__ void __launch_bounds__(32 * LPB) k_l2t_w(lvl_ptrs<R> P, int nleaf, const int32_t *leaf_box,
                                                      const int32_t *blev, const int32_t *bbeg, const int32_t *bend,
-                                                     const int64_t *loff, const cx<R> *Tt, c64d *y)
+                                                     const int64_t *loff, const cx<R> *Tt, c64d *y, int compact)
 {
     const int li = blockIdx.x * LPB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (li >= nleaf) return;
     const int B = leaf_box[li], l = blev[B], T = P.T[l];
     if (T == 0) return;
     const int i0 = bbeg[B], nB = bend[B] - i0;
+    const int ld = compact ? nB : 64;  // column stride of the leaf's operator
     const cx<R> *Tm = Tt + loff[li];
     const cx<R> *src = P.p[l] + (int64_t)(B - P.box0[l]) * T;
     const bool r0 = lane < nB, r1 = lane + 32 < nB;
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(32 * LPB) k_l2t_w(lvl_ptrs<R> P, int nleaf, co
             cx<R> c0[UU], c1[UU];
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
-                const cx<R> *col = Tm + (int64_t)(tb + ub + u) * 64;
+                const cx<R> *col = Tm + (int64_t)(tb + ub + u) * ld;
                 const bool in = ub + u < nt;
                 c0[u] = in && r0 ? col[lane] : cx<R>();
                 c1[u] = in && r1 ? col[lane + 32] : cx<R>();
@@ -516,10 +517,13 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     if (leaf_tc) {
         fda_leaf_tc(h, 2, ops.Tt, nullptr, y, mr);
     } else if (mr == 1) {
+        // FP32: the operators without the 64-row padding (fewer DRAM bytes)
+        const bool cpt = sizeof(R) == 4 && h->tt32c.p;
+        const int64_t *lo = cpt ? h->tt_c_off.as<int64_t>() : h->leaf_op_off.as<int64_t>();
+        const cx<R> *tt = cpt ? reinterpret_cast<const cx<R> *>(h->tt32c.p) : ops.Tt.template as<cx<R>>();
         k_l2t_w<R><<<(NL + LPB - 1) / LPB, 32 * LPB, 0, s>>>(P, NL, h->leaf_box.as<int32_t>(),
                                                               h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
-                                                              h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(),
-                                                              ops.Tt.template as<cx<R>>(), y);
+                                                              h->box_end.as<int32_t>(), lo, tt, y, cpt ? 1 : 0);
         FDA_CHECK_LAUNCH();
     } else {
         k_l2t<R><<<NL, AT, 0, s>>>(P, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(),

@@ -255,6 +255,9 @@ struct fda_handle {
     dbuf sig[FDA_MAX_LEVELS];  // [T]
     std::vector<int> leaf_T_off;   // per leaf: offset into St / Tt (elements)
     dbuf leaf_op_off;          // int64 [nleaf]
+    // FP32 L2T operators without the 64-row padding (leaf li: [T][n_B] at
+    // tt_c_off[li]), read by the one-right-hand-side L2T kernel
+    dbuf tt32c, tt_c_off;
 
     far_ops<double> op64;
     far_ops<float> op32;

@@ -1198,6 +1198,21 @@ void fda_rhs_layers_prepare(fda_handle *h)
     h->rhs_layers = 1;
 }
 
+// the FP32 L2T operators without the 64-row padding: leaf li's T columns of
+// n_B rows, one after another from coff[li]
+__global__ void k_compact_l2t(const c32f *Tt, const int64_t *off, const int64_t *coff, const int32_t *leaf_box,
+                              const int32_t *bbeg, const int32_t *bend, int nleaf, c32f *out)
+{
+    const int li = blockIdx.x;
+    if (li >= nleaf) return;
+    const int B = leaf_box[li], nB = bend[B] - bbeg[B];
+    const int T = (int)((off[li + 1] - off[li]) / 64);
+    for (int e = threadIdx.x; e < T * nB; e += blockDim.x) {
+        const int t = e / nB, i = e - t * nB;
+        out[coff[li] + e] = Tt[off[li] + (int64_t)t * 64 + i];
+    }
+}
+
 // FP32 copies of every far-field operator (chosen precision)
 void fda_far_convert_f32(fda_handle *h)
 {
@@ -1220,5 +1235,24 @@ void fda_far_convert_f32(fda_handle *h)
     }
     conv(h->op64.St, h->op32.St);
     conv(h->op64.Tt, h->op32.Tt);
+    if (h->op32.Tt.p && h->nleaf > 0) {
+        const int NL = h->nleaf;
+        std::vector<int32_t> lb(NL), bb(h->nbox_total), be(h->nbox_total);
+        std::vector<int64_t> off(NL + 1), coff(NL + 1, 0);
+        FDA_CUDA(cudaMemcpy(lb.data(), h->leaf_box.p, 4 * (size_t)NL, cudaMemcpyDeviceToHost));
+        FDA_CUDA(cudaMemcpy(bb.data(), h->box_begin.p, 4 * bb.size(), cudaMemcpyDeviceToHost));
+        FDA_CUDA(cudaMemcpy(be.data(), h->box_end.p, 4 * be.size(), cudaMemcpyDeviceToHost));
+        FDA_CUDA(cudaMemcpy(off.data(), h->leaf_op_off.p, 8 * off.size(), cudaMemcpyDeviceToHost));
+        for (int li = 0; li < NL; ++li)
+            coff[li + 1] = coff[li] + (off[li + 1] - off[li]) / 64 * (be[lb[li]] - bb[lb[li]]);
+        h->tt_c_off.alloc(8 * coff.size());
+        FDA_CUDA(cudaMemcpy(h->tt_c_off.p, coff.data(), 8 * coff.size(), cudaMemcpyHostToDevice));
+        h->tt32c.alloc(sizeof(c32f) * std::max<int64_t>(coff[NL], 1));
+        k_compact_l2t<<<NL, 256, 0, s>>>(h->op32.Tt.as<c32f>(), h->leaf_op_off.as<int64_t>(),
+                                         h->tt_c_off.as<int64_t>(), h->leaf_box.as<int32_t>(),
+                                         h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(), NL,
+                                         h->tt32c.as<c32f>());
+        FDA_CHECK_LAUNCH();
+    }
     FDA_CUDA(cudaStreamSynchronize(s));
 }
