@@ -121,7 +121,7 @@ template <typename R, int NR, bool XS, int NW = NRW>
 __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, const int32_t *bbeg,
                                                    const int32_t *bend, const int64_t *colptr, const int32_t *cols,
                                                    const int64_t *off, const cx<R> *A, const void *x, int x64,
-                                                   int64_t xstr, int mr, c64d *y, int64_t ldy)
+                                                   int64_t xstr, int mr, c64d *y, int64_t ldy, int64_t nnz)
 {
     // Each warp takes NW rows of a leaf (rows r, r + 8, ... of its group of
     // 8 NW); the leaf's columns (its flattened near ranges, shared by all
@@ -143,6 +143,16 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
     const int64_t c0 = colptr[li];
     const int nc = (int)(colptr[li + 1] - c0);
     const int32_t *cl = cols + c0;
+    if (XS && gridDim.y == 1 && threadIdx.x == 0) {
+        // the leaf's whole block (contiguous) into L2 while x is gathered:
+        // 16-byte aligned start, size a multiple of 16 within the nnz entries
+        const uintptr_t b = reinterpret_cast<uintptr_t>(A + off[li]) & ~uintptr_t(15);
+        uintptr_t e = (reinterpret_cast<uintptr_t>(A + off[li + 1]) + 15) & ~uintptr_t(15);
+        const uintptr_t lim = reinterpret_cast<uintptr_t>(A + nnz) & ~uintptr_t(15);
+        if (e > lim) e = lim;
+        if (e > b)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
+    }
     if (XS) {
         for (int c = threadIdx.x; c < nc; c += AT) xsm[c] = ldx<R>(x, __ldg(cl + c), x64);
         __syncthreads();
@@ -425,19 +435,19 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         k_near_apply<R, 1, true, 3><<<gn, AT, xs_bytes, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                           h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
                                                           h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                                          near.template as<cx<R>>(), x, x64, N, mr, y, N);
+                                                          near.template as<cx<R>>(), x, x64, N, mr, y, N, h->nnz_near);
     } else if (mr == 1) {
         dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), 1);
         k_near_apply<R, 1, false><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                     h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
                                                     h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                                    near.template as<cx<R>>(), x, x64, N, mr, y, N);
+                                                    near.template as<cx<R>>(), x, x64, N, mr, y, N, h->nnz_near);
     } else {
         dim3 gn(NL, (max_rows + NRW * AT / 32 - 1) / (NRW * AT / 32), (mr + NRG - 1) / NRG);
         k_near_apply<R, NRG, false><<<gn, AT, 0, s>>>(h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(),
                                                       h->box_end.as<int32_t>(), h->nf_colptr.as<int64_t>(),
                                                       h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(),
-                                                      near.template as<cx<R>>(), x, x64, N, mr, y, N);
+                                                      near.template as<cx<R>>(), x, x64, N, mr, y, N, h->nnz_near);
     }
     FDA_CHECK_LAUNCH();
     mark(1);
@@ -550,11 +560,11 @@ void fda_near_product_f32(fda_handle *h, const c32f *A, const c64d *x, c64d *z)
         }
         k_near_apply<float, 1, true, 3><<<gn, AT, xs_bytes, h->stream>>>(
             h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
-            h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(), A, x, 1, h->N, 1, z, h->N);
+            h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(), A, x, 1, h->N, 1, z, h->N, h->nnz_near);
     } else {
         k_near_apply<float, 1, false><<<gn, AT, 0, h->stream>>>(
             h->leaf_box.as<int32_t>(), h->box_begin.as<int32_t>(), h->box_end.as<int32_t>(),
-            h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(), A, x, 1, h->N, 1, z, h->N);
+            h->nf_colptr.as<int64_t>(), h->nf_cols.as<int32_t>(), h->nf_off.as<int64_t>(), A, x, 1, h->N, 1, z, h->N, h->nnz_near);
     }
     FDA_CHECK_LAUNCH();
 }
