@@ -58,6 +58,18 @@ constexpr int NRG = 8;
 
 constexpr int NRW = 2;  // rows per warp in the near-field product
 
+// one thread's L2 prefetch of entries [b, e) of an array that ends at lim
+// (16-byte aligned start, size a multiple of 16, never past lim)
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T *b, const T *e, const T *lim)
+{
+    const uintptr_t pb = reinterpret_cast<uintptr_t>(b) & ~uintptr_t(15);
+    uintptr_t pe = (reinterpret_cast<uintptr_t>(e) + 15) & ~uintptr_t(15);
+    const uintptr_t pl = reinterpret_cast<uintptr_t>(lim) & ~uintptr_t(15);
+    if (pe > pl) pe = pl;
+    if (pe > pb) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pb), "r"((uint32_t)(pe - pb)) : "memory");
+}
+
 // NW rows r0, r0 + AT / 32, ... of a leaf block (row-major, nc columns)
 // times x, written to y
 template <typename R, int NR, bool XS, int NW>
@@ -143,16 +155,8 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
     const int64_t c0 = colptr[li];
     const int nc = (int)(colptr[li + 1] - c0);
     const int32_t *cl = cols + c0;
-    if (XS && gridDim.y == 1 && threadIdx.x == 0) {
-        // the leaf's whole block (contiguous) into L2 while x is gathered:
-        // 16-byte aligned start, size a multiple of 16 within the nnz entries
-        const uintptr_t b = reinterpret_cast<uintptr_t>(A + off[li]) & ~uintptr_t(15);
-        uintptr_t e = (reinterpret_cast<uintptr_t>(A + off[li + 1]) + 15) & ~uintptr_t(15);
-        const uintptr_t lim = reinterpret_cast<uintptr_t>(A + nnz) & ~uintptr_t(15);
-        if (e > lim) e = lim;
-        if (e > b)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
-    }
+    // the leaf's whole block (contiguous) into L2 while x is gathered
+    if (XS && gridDim.y == 1 && threadIdx.x == 0) prefetch_l2(A + off[li], A + off[li + 1], A + nnz);
     if (XS) {
         for (int c = threadIdx.x; c < nc; c += AT) xsm[c] = ldx<R>(x, __ldg(cl + c), x64);
         __syncthreads();
@@ -302,6 +306,7 @@ __global__ void __launch_bounds__(32 * LPB) k_l2t_w(lvl_ptrs<R> P, int nleaf, co
     const int i0 = bbeg[B], nB = bend[B] - i0;
     const int ld = compact ? nB : 64;  // column stride of the leaf's operator
     const cx<R> *Tm = Tt + loff[li];
+    if (compact && lane == 0) prefetch_l2(Tm, Tm + (int64_t)T * nB, Tt + loff[nleaf]);  // the leaf's block
     const cx<R> *src = P.p[l] + (int64_t)(B - P.box0[l]) * T;
     const bool r0 = lane < nB, r1 = lane + 32 < nB;
     cx<R> a0, a1;
