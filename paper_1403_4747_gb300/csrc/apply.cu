@@ -168,6 +168,18 @@ __global__ void __launch_bounds__(AT) k_near_apply(const int32_t *leaf_box, cons
 }
 
 
+// q~ and p~ of level lev_lo + blockIdx.y / 2 (even: q~, odd: p~) set to zero
+// for mr right-hand sides
+template <typename R>
+__global__ void k_zero_levels(lvl_ptrs<R> P, int lev_lo, int mr)
+{
+    const int l = lev_lo + (int)blockIdx.y / 2;
+    cx<R> *v = (blockIdx.y & 1) ? P.p[l] : P.q[l];
+    const int64_t n = P.stride[l] * mr;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        v[e] = cx<R>();
+}
+
 // ---- Step 2: S2M at leaves, q~ = S~ x_B
 // One CTA per leaf.  With T < blockDim the CTA splits the sum over the
 // leaf's elements into blockDim / T interleaved groups (every thread has a
@@ -461,11 +473,11 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         return;
     }
     lvl_ptrs<R> P = make_ptrs<R>(h, ops, q, p);
-    for (int l = h->lev_lo; l < h->nlev; ++l) {
-        const level_info &L = h->lev[l];
-        size_t bytes = sizeof(cx<R>) * (size_t)L.nbox * L.ncones * L.T * mr;
-        FDA_CUDA(cudaMemsetAsync(q[l].p, 0, bytes, s));
-        FDA_CUDA(cudaMemsetAsync(p[l].p, 0, bytes, s));
+    {
+        // every level's multipole and local densities to zero, one launch
+        const int nl = h->nlev - h->lev_lo;
+        k_zero_levels<R><<<dim3(64, 2 * nl), 256, 0, s>>>(P, h->lev_lo, mr);
+        FDA_CHECK_LAUNCH();
     }
     if (leaf_tc) {
         fda_leaf_tc(h, 1, St, reinterpret_cast<const c32f *>(x), y, mr);
