@@ -475,8 +475,12 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
     lvl_ptrs<R> P = make_ptrs<R>(h, ops, q, p);
     {
         // every level's multipole and local densities to zero, one launch
+        // (blocks per array from the largest one, about 2,048 elements each)
         const int nl = h->nlev - h->lev_lo;
-        k_zero_levels<R><<<dim3(64, 2 * nl), 256, 0, s>>>(P, h->lev_lo, mr);
+        int64_t maxn = 0;
+        for (int l = h->lev_lo; l < h->nlev; ++l) maxn = std::max(maxn, P.stride[l] * mr);
+        const int gx = (int)std::min<int64_t>(2048, std::max<int64_t>(16, maxn / 2048));
+        k_zero_levels<R><<<dim3(gx, 2 * nl), 256, 0, s>>>(P, h->lev_lo, mr);
         FDA_CHECK_LAUNCH();
     }
     if (leaf_tc) {
