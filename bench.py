@@ -569,14 +569,19 @@ def _precond_block(F, P, b, args):
 def _m2l_traffic(args):
     """DRAM bytes of the M2L pass per matvec from the committed ncu summary
     (sphere level 7, k = 50, eps 1e-4), or None for another workload or if the
-    kernel source changed since the counters were taken."""
+    kernel's source (the k_btr_tc template and the tcgen05 helpers) changed
+    since the counters were taken."""
     import hashlib
     if (args.level, args.k, args.eps) != (7, 50.0, 1e-4):
         return None
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "k_btr_tc_traffic_sphere_l7_k50.json")))
-        src = open(os.path.join(ROOT, "paper_1403_4747_gb300", "csrc", "translate_tc.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+        csrc = os.path.join(ROOT, "paper_1403_4747_gb300", "csrc")
+        lines = open(os.path.join(csrc, "translate_tc.cu")).read().split("\n")
+        i = [j for j, s in enumerate(lines) if "k_btr_tc(const tc_tile" in s][0] - 1
+        e = next(j for j in range(i, len(lines)) if lines[j] == "}")
+        src = "\n".join(lines[i:e + 1]) + "\n" + open(os.path.join(csrc, "tc_util.cuh")).read()
+        if hashlib.sha256(src.encode()).hexdigest()[:16] != rec["source_sha256_16"]:
             return None
         return rec["m2l_dram_bytes_per_matvec"]
     except Exception:
@@ -964,8 +969,10 @@ def run_precond_study(args):
 def run_far_field(args):
     """Far-field pattern of the headline sphere (level 7, N = 327,680,
     k = 50, plane wave along +z, chosen form, tol 1e-4) on 720 directions in
-    the xz-plane against the Mie series, and reciprocity on the ellipsoid of
-    the same level.  Not the headline workload (--workload far_field)."""
+    the xz-plane against the Mie series, the scattered field on a grid of
+    the xz-plane directly and through the fast algorithm, and reciprocity on
+    the ellipsoid of the same level.  Not the headline workload
+    (--workload far_field)."""
     import numpy as np
     import torch
     from scipy import special
@@ -1004,6 +1011,25 @@ def run_far_field(args):
     Ff = Ff.cpu().numpy()
     fast = {"ms": t_fast * 1e3, "rel_l2_vs_direct": float(np.linalg.norm(Ff - Fp) / np.linalg.norm(Fp)),
             "rel_l2_error_vs_mie": float(np.linalg.norm(Ff - mie) / np.linalg.norm(mie))}
+    # the scattered field on a 40 x 40 grid of the xz-plane over [-2.5, 2.5]^2
+    # (points with r >= 1.05), directly and through the fast algorithm
+    g = np.linspace(-2.5, 2.5, 40)
+    X, Z = np.meshgrid(g, g)
+    pts = np.stack([X.ravel(), np.zeros(X.size), Z.ravel()], axis=1)
+    pts = pts[np.linalg.norm(pts, axis=1) >= 1.05]
+    times = {}
+    vals = {}
+    for name, fl in (("direct", False), ("fast", True)):
+        P.scattered_field(u, pts[:8], fast=fl)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vals[name] = P.scattered_field(u, pts, fast=fl)
+        torch.cuda.synchronize()
+        times[name] = (time.perf_counter() - t0) * 1e3
+        vals[name] = vals[name].cpu().numpy()
+    field = {"points": int(len(pts)), "direct_ms": times["direct"], "fast_ms": times["fast"],
+             "fast_rel_l2_vs_direct": float(np.linalg.norm(vals["fast"] - vals["direct"])
+                                           / np.linalg.norm(vals["direct"]))}
     P.close()
     ve, fe = ellipsoid_from_icosphere(7)
     Q = F.FDAProblem(ve, fe, k, precision=F.FDA_CHOSEN_FP32, alpha_sign=args.alpha_sign)
@@ -1018,7 +1044,8 @@ def run_far_field(args):
             "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "icosphere level 7 (N = 327,680), k = 50, plane wave +z; ellipsoid level 7 "
                                    "reciprocity", "alpha_sign": args.alpha_sign},
-            "pattern_rel_l2_error_vs_mie": err, "fast_pattern": fast, "solve_iters": info.iters,
+            "pattern_rel_l2_error_vs_mie": err, "fast_pattern": fast, "scattered_field": field,
+            "solve_iters": info.iters,
             "solve_s": info.solve_s,
             "reciprocity": {"F(a;d)": [f1.real, f1.imag], "F(-d;-a)": [f2.real, f2.imag],
                             "rel_gap": abs(f1 - f2) / abs(f1)}}

@@ -49,21 +49,33 @@ struct tc_tile {
 // rounded up to 32, zero beyond T.
 __global__ void k_split_density(const c32f *q, int64_t nvec, int T, int Tp, __nv_bfloat16 *out)
 {
-    const int64_t total = nvec * 2 * Tp;  // (vector, Re/Im, j)
+    // each thread: entries j, j + 1 (j even) of one vector; their Re hi, Im hi,
+    // Re lo, Im lo go out as four bf16 pairs (4-byte stores: j and j + 1 share
+    // a K chunk, KC being even). Two 8-byte loads, since v * T + j is odd for
+    // odd T and odd v.
+    const int hp = Tp / 2;  // entry pairs per vector
+    const int64_t total = nvec * hp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t v = e / (2 * Tp);
-        int r = (int)(e % (2 * Tp));
-        int im = r / Tp, j = r - im * Tp;
-        float x = 0.0f;
-        if (j < T) {
-            c32f c = q[v * T + j];
-            x = im ? c.im : c.re;
-        }
-        __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-        __nv_bfloat16 *o = out + v * 4 * Tp + (j / KC) * 4 * KC + im * KC + (j % KC);
-        o[0] = hi;
-        o[2 * KC] = lo;
+        const int64_t v = e / hp;
+        const int j = 2 * (int)(e - v * hp);
+        c32f c0(0.0f, 0.0f), c1(0.0f, 0.0f);
+        if (j < T) c0 = q[v * T + j];
+        if (j + 1 < T) c1 = q[v * T + j + 1];
+        auto split = [](float x0, float x1, uint32_t &hi, uint32_t &lo) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        };
+        uint32_t rh, rl, ih, il;
+        split(c0.re, c1.re, rh, rl);
+        split(c0.im, c1.im, ih, il);
+        __nv_bfloat16 *o = out + v * 4 * Tp + (j / KC) * 4 * KC + (j % KC);
+        *reinterpret_cast<uint32_t *>(o) = rh;
+        *reinterpret_cast<uint32_t *>(o + KC) = ih;
+        *reinterpret_cast<uint32_t *>(o + 2 * KC) = rl;
+        *reinterpret_cast<uint32_t *>(o + 3 * KC) = il;
     }
 }
 
