@@ -238,6 +238,34 @@ fda_status fda_scattered_field(fda_handle *h, const fda_c128 *u, const fda_c128 
  * Arguments, errors and synchronisation as fda_far_field. */
 fda_status fda_far_field_fast(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *dirs, int ndir,
                               fda_c128 *F);
+/* The same scattered field u_sc at points through the fast algorithm
+ * (Sec. 3.3 Steps 2-3 with the points as L2T targets): the outgoing densities
+ * of -D[u] + S[q] by S2M and M2M, the local densities by M2L and L2L (all in
+ * FP64, once per call), then per point:
+ *   * the point is placed in the deepest box of the tree whose cube contains
+ *     it; if that box A is a low-frequency box with local densities, the
+ *     field of every source A's local density covers (the interaction lists
+ *     of A and its ancestors) is A's L2T at the point (Eq. l2t with the
+ *     value of G as the target kernel);
+ *   * the rest of the sources (A's near field as if A were a leaf, or the
+ *     whole tree for a point outside every low-frequency box) are walked
+ *     top-down: a box that is not near the point's cube of its level (the
+ *     interaction-list test, directional at a high-frequency level) adds
+ *     sum_e G(x, y_e) phi_e over its equivalent sources phi = V q~ (the
+ *     cone towards the point at a high-frequency level), a near leaf is
+ *     summed element by element by the six-point rule, a near box with
+ *     children is opened.
+ * Agrees with fda_scattered_field to about the operator's eps relative to the
+ * field's scale (the same six-point rule on the near elements), so points
+ * closer to the surface than about two element sizes lose accuracy in the
+ * same way; a point on an element's quadrature point gives a non-finite
+ * value.  Work per point: the L2T (n_chk x T) plus the boxes and elements
+ * it walks, instead of N x 6.  FDA_ERR_STATE if more than 2,048 boxes of one
+ * level are near one point (the values are then NaN).  A non-NULL q builds
+ * the right-hand side's layers on first use, as fda_rhs_neumann.  Arguments,
+ * errors and synchronisation as fda_scattered_field. */
+fda_status fda_scattered_field_fast(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *pts,
+                                    int64_t npts, fda_c128 *out);
 
 /* Right-hand side of Eq. eq_bm for a radiating body with given Neumann data
  * q = du/dn (no incident field), the layers of the equation's right-hand

@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.fda_far_field.argtypes = [H, vp, vp, vp, cint, vp]
     lib.fda_scattered_field.argtypes = [H, vp, vp, vp, i64, vp]
     lib.fda_far_field_fast.argtypes = [H, vp, vp, vp, cint, vp]
+    lib.fda_scattered_field_fast.argtypes = [H, vp, vp, vp, i64, vp]
     lib.fda_solve.argtypes = [H, vp, vp, cint, dbl, ctypes.POINTER(fda_info)]
     lib.fda_get_stats.argtypes = [H, ctypes.POINTER(fda_stats)]
     lib.fda_set_timing.argtypes = [H, cint]
@@ -147,7 +148,7 @@ def load(path: str = LIB_PATH):
     lib.fda_destroy.argtypes = [H]
     lib.fda_destroy.restype = None
     for name in ("fda_create", "fda_build_tree", "fda_precompute_translations", "fda_apply", "fda_apply_host",
-                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_far_field", "fda_far_field_fast", "fda_scattered_field", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
+                 "fda_rhs_plane_wave", "fda_rhs_plane_wave_noalloc", "fda_rhs_neumann", "fda_rhs_point_source", "fda_far_field", "fda_far_field_fast", "fda_scattered_field", "fda_scattered_field_fast", "fda_solve", "fda_get_stats", "fda_set_timing", "fda_get_pass_times",
                  "fda_set_precision", "fda_set_precond", "fda_set_tensor_cores", "fda_set_tc_tiles",
                  "fda_tree_sizes", "fda_get_tree"):
         getattr(lib, name).restype = cint
@@ -235,6 +236,13 @@ def fda_scattered_field(h, u_ptr, q_ptr, points, out_ptr):
     import numpy as np
     p = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
     _check(h, load().fda_scattered_field(h, u_ptr, q_ptr or None, p.ctypes.data, p.shape[0], out_ptr))
+
+
+def fda_scattered_field_fast(h, u_ptr, q_ptr, points, out_ptr):
+    """Scattered field at host points [M, 3] through the fast algorithm (same arguments as fda_scattered_field)."""
+    import numpy as np
+    p = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    _check(h, load().fda_scattered_field_fast(h, u_ptr, q_ptr or None, p.ctypes.data, p.shape[0], out_ptr))
 
 
 def fda_rhs_neumann(h, q_ptr, b_ptr, nrhs, ld):

@@ -363,8 +363,8 @@ fda_status field_call(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const
     for (int64_t i = 0; i < ntgt; ++i) {
         const double *t = tgt + 3 * i;
         if (!std::isfinite(t[0]) || !std::isfinite(t[1]) || !std::isfinite(t[2]) ||
-            (far && !(fabs(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] - 1.0) < 1e-6))) {
-            h->err = far ? "far-field directions must be unit vectors" : "non-finite field point";
+            ((far == 1 || far == 2) && !(fabs(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] - 1.0) < 1e-6))) {
+            h->err = (far == 1 || far == 2) ? "far-field directions must be unit vectors" : "non-finite field point";
             return FDA_ERR_ARG;
         }
     }
@@ -375,6 +375,9 @@ fda_status field_call(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const
         if (far == 2)
             fda_far_field_upward(h, reinterpret_cast<const c64d *>(u), reinterpret_cast<const c64d *>(q),
                                  dt.as<double>(), (int)ntgt, reinterpret_cast<c64d *>(out));
+        else if (far == 3)
+            fda_field_fast(h, reinterpret_cast<const c64d *>(u), reinterpret_cast<const c64d *>(q), dt.as<double>(),
+                           ntgt, reinterpret_cast<c64d *>(out));
         else
             fda_field(h, reinterpret_cast<const c64d *>(u), reinterpret_cast<const c64d *>(q), dt.as<double>(),
                       ntgt, far, reinterpret_cast<c64d *>(out));
@@ -399,6 +402,12 @@ fda_status fda_scattered_field(fda_handle *h, const fda_c128 *u, const fda_c128 
                                fda_c128 *out)
 {
     return field_call(h, u, q, pts, npts, 0, out, "fda_scattered_field");
+}
+
+fda_status fda_scattered_field_fast(fda_handle *h, const fda_c128 *u, const fda_c128 *q, const double *pts,
+                                    int64_t npts, fda_c128 *out)
+{
+    return field_call(h, u, q, pts, npts, 3, out, "fda_scattered_field_fast");
 }
 
 fda_status fda_rhs_plane_wave_noalloc(fda_handle *h, const double *dirs, int nrhs, fda_c128 *b)

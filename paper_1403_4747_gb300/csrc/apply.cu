@@ -635,6 +635,27 @@ void fda_m2m_fp64(fda_handle *h)
                               Q.stride[l + 1], Q.stride[l], h->stream);
 }
 
+// Downward pass only, FP64 (Sec. 3.3 Step 3 without L2T), on the outgoing
+// densities in q64 (after fda_upward_fp64 and fda_m2m_fp64): M2L at every
+// level (the low-rank operators of Sec. 4.2 in two stages) and L2L top-down,
+// leaving every box's complete local density in p64.
+void fda_downward_fp64(fda_handle *h)
+{
+    if (h->lev_lo < 0) return;
+    cudaStream_t s = h->stream;
+    lvl_ptrs<double> P = make_ptrs<double>(h, h->op64, h->q64, h->p64);
+    for (int l = h->lev_lo; l < h->nlev; ++l)
+        if (P.stride[l] > 0 && P.T[l] > 0) FDA_CUDA(cudaMemsetAsync(P.p[l], 0, sizeof(c64d) * P.stride[l], s));
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        fda_run_batch<double>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], 1, P.stride[l],
+                              P.stride[l], s);
+        for (lr_bucket &B : h->lr[l]) lowrank_m2l<double>(h, B, l, P, 1, false);
+    }
+    for (int l = h->lev_lo; l + 1 < h->nlev; ++l)
+        fda_run_batch<double>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], 1,
+                              P.stride[l], P.stride[l + 1], s);
+}
+
 void fda_alloc_densities(fda_handle *h, int want32)
 {
     for (int l = 0; l < h->nlev; ++l) {

@@ -364,10 +364,16 @@ void fda_rhs_point(fda_handle *h, const double *src_dev, int nrhs, c64d *b);
 void fda_field(fda_handle *h, const c64d *u, const c64d *q, const double *tgt_dev, int64_t ntgt, int far, c64d *out);
 // far-field pattern through the fast algorithm's upward pass (device directions [ndir][3])
 void fda_far_field_upward(fda_handle *h, const c64d *u, const c64d *q, const double *dirs_dev, int ndir, c64d *out);
+// scattered field at points through the fast algorithm (local densities by
+// the downward pass, L2T at each point's box, equivalent sources and direct
+// sums for what those do not cover); device points [ntgt][3]
+void fda_field_fast(fda_handle *h, const c64d *u, const c64d *q, const double *tgt_dev, int64_t ntgt, c64d *out);
 // FP64 upward pass: S2M of side 0 (double layer) or 1 (single layer) of xs
 // (Morton order) into q64 (add = 1: added to q64), then M2M on q64
 void fda_upward_fp64(fda_handle *h, const c64d *xs, int side, int add);
 void fda_m2m_fp64(fda_handle *h);
+// FP64 downward pass on q64: M2L at every level and L2L, local densities in p64
+void fda_downward_fp64(fda_handle *h);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
 void fda_gather_cols(fda_handle *h, const c64d *x, int64_t ld, c64d *xs, int nrhs, cudaStream_t s);

@@ -7,12 +7,14 @@
 // Direct summation over all elements for every target (no fast algorithm):
 // N x M x 6 FP64 kernel evaluations, sincos-bound.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <utility>
 #include <vector>
 
 #include "fda_internal.cuh"
+#include "tree_util.cuh"
 
 namespace {
 
@@ -182,6 +184,309 @@ __global__ void k_negate(c64d *x, int64_t n)
     if (t < n) x[t] = c64d(-x[t].re, -x[t].im);
 }
 
+// ---- scattered field at points through the fast algorithm
+//
+// A target x is placed in the deepest box A of the tree whose cube contains
+// it.  If A is a low-frequency box with local densities, x is treated as one
+// more collocation point of A: its field from the sources that A's local
+// density covers (the interaction lists of A and its ancestors) is the L2T
+// of A's density at x, sum_m G(x, y_m) psi_m with psi = conj(U) S^-1 p~_A on
+// A's equivalent points y_m (as the L2T operators of the leaves, Eq. l2t,
+// with the value of G in place of the Burton-Miller kernel); what remains is
+// A's near field as if A were a leaf (leaves near A's ancestors and every
+// box near A).  Otherwise (x outside every low-frequency box) nothing is
+// covered by local densities and the whole tree is what remains.  What
+// remains is walked top-down: a box whose cube is not near x's cube of its
+// level (the interaction-list test of the tree, directional at a
+// high-frequency level) contributes through its equivalent sources,
+// sum_e G(x, c + R_u y_e) phi_e with phi = V q~ of the cone u containing the
+// direction towards x (the evaluation behind M2L); a near leaf is summed
+// directly by the six-point rule; a near box with children is opened.
+constexpr int FF = 128;         // threads per target
+constexpr int FSET = 2048;      // boxes of one level near a target (capacity)
+constexpr int FCH = 128;        // near boxes opened per round
+constexpr int FLIST = 8 * FCH;  // equivalent-source and direct lists of a round
+
+struct ff_level {
+    int box0, nbox, T, ncones, nc, hf, n_eq, n_chk, far;  // far: outgoing densities at this level
+    double w, rho2;
+    const c64d *phi;    // [nbox][ncones][n_eq] equivalent sources V q~
+    const c64d *p;      // [nbox][T] local densities (low frequency; null elsewhere)
+    const double *eq;   // [n_eq][3] equivalent points, box-relative (cone frame at high frequency)
+    const double *chk;  // [n_chk][3] the L2T's equivalent points (the upward check points)
+    const double *rot;  // [ncones][9] row-major cone rotations (high frequency)
+    const c64d *U;      // [T][n_chk] left singular vectors of the level
+    const double *sig;  // [T]
+};
+
+struct ff_tree {
+    ff_level L[FDA_MAX_LEVELS];
+    int nlev, lev_lo, max_chk;
+    double lo[3];
+    const uint64_t *key;
+    const int32_t *coord, *leaf, *c0, *c1, *bbeg, *bend;
+};
+
+__device__ inline int ff_cell(double x, double lo, double w)
+{
+    double c = floor((x - lo) / w);
+    c = c < -268435456.0 ? -268435456.0 : (c > 268435456.0 ? 268435456.0 : c);
+    return (int)c;
+}
+
+__device__ inline bool ff_near(const ff_level &L, int dx, int dy, int dz)
+{
+    const int m = max(abs(dx), max(abs(dy), abs(dz)));
+    if (m <= 1) return true;
+    if (L.hf) return (double)dx * dx + (double)dy * dy + (double)dz * dz < L.rho2;
+    return false;
+}
+
+// a += G(x, y) b, G = e^{ikR}/(4 pi R)
+__device__ inline void ff_acc_g(double &are, double &aim, const double *x, double y0, double y1, double y2, double k,
+                                c64d b)
+{
+    const double r0 = x[0] - y0, r1 = x[1] - y1, r2 = x[2] - y2;
+    const double R = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    const double g = 1.0 / (4.0 * FDA_PI * R);
+    const double gre = g * cs, gim = g * sn;
+    are += gre * b.re - gim * b.im;
+    aim += gre * b.im + gim * b.re;
+}
+
+// one warp: the six-point sums of the elements [j0, j1) of a leaf,
+// w [G q + dG/dn_y un] with un = -u
+__device__ inline void ff_direct(int j0, int j1, const double *qpt, const double *qw, const double *nrm,
+                                 const c64d *un, const c64d *q, const double *x, double k, int lane, double &are,
+                                 double &aim)
+{
+    for (int t = j0 * 6 + lane; t < j1 * 6; t += 32) {
+        const int j = t / 6, g = t - 6 * (t / 6);
+        const double *y = qpt + 18 * (int64_t)j + 3 * g, *ny = nrm + 3 * (int64_t)j;
+        const double w = qw[6 * (int64_t)j + g];
+        const double r0 = x[0] - y[0], r1 = x[1] - y[1], r2 = x[2] - y[2];
+        const double R2 = r0 * r0 + r1 * r1 + r2 * r2, R = sqrt(R2);
+        double sn, cs;
+        sincos(k * R, &sn, &cs);
+        const double gw = w / (4.0 * FDA_PI * R);
+        // dG/dn_y = e^{ikR}(1 - ikR)(r.n_y)/(4 pi R^3)
+        const double f = gw * (r0 * ny[0] + r1 * ny[1] + r2 * ny[2]) / R2;
+        const double dre = f * (cs + k * R * sn), dim = f * (sn - k * R * cs);
+        const double gre = gw * cs, gim = gw * sn;
+        const c64d uj = un[j], qj = q ? q[j] : c64d(0.0, 0.0);
+        are += gre * qj.re - gim * qj.im + dre * uj.re - dim * uj.im;
+        aim += gre * qj.im + gim * qj.re + dre * uj.im + dim * uj.re;
+    }
+}
+
+// one warp: box b of level l through its equivalent sources of cone u
+__device__ inline void ff_m2t(const ff_tree &t, int l, int b, int u, const double *x, double k, int lane,
+                              double &are, double &aim)
+{
+    const ff_level &L = t.L[l];
+    const c64d *phi = L.phi + ((int64_t)(b - L.box0) * L.ncones + u) * L.n_eq;
+    const int32_t *cb = t.coord + 3 * (int64_t)b;
+    const double c0 = t.lo[0] + (cb[0] + 0.5) * L.w, c1 = t.lo[1] + (cb[1] + 0.5) * L.w,
+                 c2 = t.lo[2] + (cb[2] + 0.5) * L.w;
+    const double *R = L.hf ? L.rot + 9 * u : nullptr;
+    for (int e = lane; e < L.n_eq; e += 32) {
+        const double *f = L.eq + 3 * e;
+        double y0 = f[0], y1 = f[1], y2 = f[2];
+        if (R) {
+            y0 = R[0] * f[0] + R[1] * f[1] + R[2] * f[2];
+            y1 = R[3] * f[0] + R[4] * f[1] + R[5] * f[2];
+            y2 = R[6] * f[0] + R[7] * f[1] + R[8] * f[2];
+        }
+        ff_acc_g(are, aim, x, c0 + y0, c1 + y1, c2 + y2, k, phi[e]);
+    }
+}
+
+// One CTA per target.  err[0] records a near set above its capacity (the
+// target's value is then left at NaN and the host reports the error).
+__global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt, const double *qw,
+                                                   const double *nrm, const c64d *un, const c64d *q,
+                                                   const double *tgt, int64_t ntgt, double k, int *err, c64d *out)
+{
+    extern __shared__ c64d psi[];  // [max_chk]
+    __shared__ int sset[2][FSET];
+    __shared__ int mlist[FLIST], mcone[FLIST], dlist[FLIST];
+    __shared__ int ns, nn, nm, nd, overflow, lA, A;
+    __shared__ int anc[FDA_MAX_LEVELS];
+    __shared__ double red[FF / 32][2];
+    const int64_t ti = blockIdx.x;
+    if (ti >= ntgt) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double x[3] = {tgt[3 * ti], tgt[3 * ti + 1], tgt[3 * ti + 2]};
+    double are = 0.0, aim = 0.0;
+    // the chain of boxes containing x, down to a leaf or an empty cube
+    if (threadIdx.x == 0) {
+        A = -1;
+        lA = -1;
+        overflow = 0;
+        for (int l = 0; l < t.nlev; ++l) {
+            const ff_level &L = t.L[l];
+            const int b = find_box_at(t.key, L.box0, L.nbox, l, ff_cell(x[0], t.lo[0], L.w),
+                                      ff_cell(x[1], t.lo[1], L.w), ff_cell(x[2], t.lo[2], L.w));
+            if (b < 0) break;
+            anc[l] = b;
+            A = b;
+            lA = l;
+            if (t.leaf[b]) break;
+        }
+        ns = 0;
+        nd = 0;
+    }
+    __syncthreads();
+    int l0 = 0;  // level of the first near set
+    const bool l2t = A >= 0 && !t.L[lA].hf && t.L[lA].far && t.L[lA].p && lA >= t.lev_lo;
+    if (l2t) {
+        // L2T at x from A's local density
+        const ff_level &L = t.L[lA];
+        const c64d *pA = L.p + (int64_t)(A - L.box0) * L.T;
+        for (int m = threadIdx.x; m < L.n_chk; m += FF) {
+            c64d a;
+            for (int s = 0; s < L.T; ++s) {
+                const c64d uv = L.U[m + (int64_t)s * L.n_chk];
+                const double f = 1.0 / L.sig[s];
+                cfma_conj(a, uv, c64d(f * pA[s].re, f * pA[s].im));
+            }
+            psi[m] = a;
+        }
+        __syncthreads();
+        const int32_t *cA = t.coord + 3 * (int64_t)A;
+        const double a0 = t.lo[0] + (cA[0] + 0.5) * L.w, a1 = t.lo[1] + (cA[1] + 0.5) * L.w,
+                     a2 = t.lo[2] + (cA[2] + 0.5) * L.w;
+        for (int m = threadIdx.x; m < L.n_chk; m += FF)
+            ff_acc_g(are, aim, x, a0 + L.chk[3 * m], a1 + L.chk[3 * m + 1], a2 + L.chk[3 * m + 2], k, psi[m]);
+        // A's near field as if A were a leaf: leaves near A's ancestors at
+        // coarser low-frequency levels, and every box near A (opened below)
+        for (int l = 0; l <= lA; ++l) {
+            if (t.L[l].hf && l != lA) continue;
+            const ff_level &Ll = t.L[l];
+            const int32_t *ca = t.coord + 3 * (int64_t)anc[l];
+            for (int o = threadIdx.x; o < 27; o += FF) {
+                const int X = find_box_at(t.key, Ll.box0, Ll.nbox, l, ca[0] + o % 3 - 1, ca[1] + (o / 3) % 3 - 1,
+                                          ca[2] + o / 9 - 1);
+                if (X < 0) continue;
+                if (t.leaf[X]) {
+                    const int i = atomicAdd(&nd, 1);
+                    if (i < FLIST) dlist[i] = X; else overflow = 1;
+                } else if (l == lA) {
+                    const int i = atomicAdd(&ns, 1);
+                    if (i < FSET) sset[0][i] = X; else overflow = 1;
+                }
+            }
+        }
+        l0 = lA;
+    } else if (threadIdx.x == 0 && t.L[0].nbox > 0) {
+        sset[0][0] = t.L[0].box0;  // the whole tree from the root
+        ns = 1;
+    }
+    __syncthreads();
+    // direct sums of the leaves found so far
+    for (int i = warp; i < min(nd, FLIST); i += FF / 32) {
+        const int X = dlist[i];
+        ff_direct(t.bbeg[X], t.bend[X], qpt, qw, nrm, un, q, x, k, lane, are, aim);
+    }
+    int cur = 0;
+    for (int l = l0; l < t.nlev; ++l) {
+        __syncthreads();
+        const int nset = min(ns, FSET);
+        if (nset == 0 || overflow) break;
+        if (threadIdx.x == 0) nn = 0;
+        const bool child_far = l + 1 < t.nlev && t.L[l + 1].far && l + 1 >= t.lev_lo;
+        int cx = 0, cy = 0, cz = 0;
+        if (l + 1 < t.nlev) {
+            const double w1 = t.L[l + 1].w;
+            cx = ff_cell(x[0], t.lo[0], w1);
+            cy = ff_cell(x[1], t.lo[1], w1);
+            cz = ff_cell(x[2], t.lo[2], w1);
+        }
+        for (int r0 = 0; r0 < nset; r0 += FCH) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                nm = 0;
+                nd = 0;
+            }
+            __syncthreads();
+            for (int i = r0 + threadIdx.x; i < min(nset, r0 + FCH); i += FF) {
+                const int B = sset[cur][i];
+                if (t.leaf[B]) {
+                    const int j = atomicAdd(&nd, 1);
+                    if (j < FLIST) dlist[j] = B; else overflow = 1;
+                    continue;
+                }
+                for (int C = t.c0[B]; C < t.c1[B]; ++C) {
+                    const int32_t *cc = t.coord + 3 * (int64_t)C;
+                    const int dx = cx - cc[0], dy = cy - cc[1], dz = cz - cc[2];
+                    if (child_far && !ff_near(t.L[l + 1], dx, dy, dz)) {
+                        const int j = atomicAdd(&nm, 1);
+                        if (j < FLIST) {
+                            mlist[j] = C;
+                            mcone[j] = t.L[l + 1].hf ? cone_index(dx, dy, dz, t.L[l + 1].nc) : 0;
+                        } else {
+                            overflow = 1;
+                        }
+                    } else {
+                        const int j = atomicAdd(&nn, 1);
+                        if (j < FSET) sset[cur ^ 1][j] = C; else overflow = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = warp; i < min(nm, FLIST); i += FF / 32) ff_m2t(t, l + 1, mlist[i], mcone[i], x, k, lane, are, aim);
+            for (int i = warp; i < min(nd, FLIST); i += FF / 32) {
+                const int X = dlist[i];
+                ff_direct(t.bbeg[X], t.bend[X], qpt, qw, nrm, un, q, x, k, lane, are, aim);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) ns = nn;
+        cur ^= 1;
+    }
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        are += __shfl_xor_sync(0xffffffffu, are, o);
+        aim += __shfl_xor_sync(0xffffffffu, aim, o);
+    }
+    if (lane == 0) {
+        red[warp][0] = are;
+        red[warp][1] = aim;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < FF / 32; ++i) {
+            a += red[i][0];
+            b += red[i][1];
+        }
+        if (overflow) {
+            atomicExch(err, 1);
+            a = b = nan("");
+        }
+        out[ti] = c64d(a, b);
+    }
+}
+
+// equivalent sources phi = V q~ of every box and cone of one level
+// (one block per box and cone)
+__global__ void k_equiv_sources(const c64d *qd, const c64d *V, int T, int n_eq, int64_t nvec, c64d *phi)
+{
+    extern __shared__ c64d qsm[];  // [T]
+    for (int64_t v = blockIdx.x; v < nvec; v += gridDim.x) {
+        __syncthreads();
+        for (int s = threadIdx.x; s < T; s += blockDim.x) qsm[s] = qd[v * T + s];
+        __syncthreads();
+        for (int e = threadIdx.x; e < n_eq; e += blockDim.x) {
+            c64d a;
+            for (int s = 0; s < T; ++s) cfma(a, V[e + (int64_t)s * n_eq], qsm[s]);
+            phi[v * n_eq + e] = a;
+        }
+    }
+}
+
 }  // namespace
 
 // u, q: caller order (device, q may be null); tgt: device [ntgt][3]; out:
@@ -273,4 +578,99 @@ void fda_far_field_upward(fda_handle *h, const c64d *u, const c64d *q, const dou
                                              h->box_coord.as<int32_t>(), h->root_lo[0], h->root_lo[1], h->root_lo[2],
                                              V.w, h->k, 1.0, out);
     FDA_CHECK_LAUNCH();
+}
+
+// Scattered field at points through the fast algorithm (see k_field_fast):
+// the outgoing densities of -D[u] + S[q] by S2M and M2M in FP64, the local
+// densities by M2L and L2L in FP64, the equivalent sources of every box, then
+// one CTA per point.  u, q: caller order (device, q may be null); tgt:
+// device [ntgt][3]; out: device [ntgt], overwritten.
+void fda_field_fast(fda_handle *h, const c64d *u, const c64d *q, const double *tgt_dev, int64_t ntgt, c64d *out)
+{
+    cudaStream_t s = h->stream;
+    if (ntgt == 0 || h->N == 0) {
+        FDA_CUDA(cudaMemsetAsync(out, 0, sizeof(c64d) * ntgt, s));
+        return;
+    }
+    // no level with interaction lists: every pair is near and the direct sum is the method
+    if (h->lev_lo < 0) {
+        fda_field(h, u, q, tgt_dev, ntgt, 0, out);
+        return;
+    }
+    c64d *us = h->xs.as<c64d>(), *qs = q ? h->ys.as<c64d>() : nullptr;
+    fda_gather_cols(h, u, h->N, us, 1, s);
+    if (q) fda_gather_cols(h, q, h->N, qs, 1, s);
+    k_negate<<<fda_blocks(h->N, 256), 256, 0, s>>>(us, h->N);
+    FDA_CHECK_LAUNCH();
+    fda_upward_fp64(h, us, 0, 0);
+    if (q) {
+        fda_rhs_layers_prepare(h);
+        fda_upward_fp64(h, qs, 1, 1);
+    }
+    fda_m2m_fp64(h);
+    fda_downward_fp64(h);
+    ff_tree t;
+    memset(&t, 0, sizeof(t));
+    t.nlev = h->nlev;
+    t.lev_lo = h->lev_lo;
+    for (int d = 0; d < 3; ++d) t.lo[d] = h->root_lo[d];
+    t.key = h->box_key.as<uint64_t>();
+    t.coord = h->box_coord.as<int32_t>();
+    t.leaf = h->box_leaf.as<int32_t>();
+    t.c0 = h->box_child0.as<int32_t>();
+    t.c1 = h->box_child1.as<int32_t>();
+    t.bbeg = h->box_begin.as<int32_t>();
+    t.bend = h->box_end.as<int32_t>();
+    // equivalent sources of every level with outgoing densities, in one buffer
+    std::vector<int64_t> phi_off(h->nlev + 1, 0);
+    for (int l = 0; l < h->nlev; ++l) {
+        const level_info &L = h->lev[l];
+        const bool far = l >= h->lev_lo && L.active && L.T > 0 && h->q64[l].p;
+        phi_off[l + 1] = phi_off[l] + (far ? (int64_t)L.nbox * L.ncones * L.n_eq : 0);
+    }
+    dbuf phi, derr;
+    phi.alloc(sizeof(c64d) * (size_t)std::max<int64_t>(1, phi_off[h->nlev]));
+    derr.alloc(sizeof(int));
+    FDA_CUDA(cudaMemsetAsync(derr.p, 0, sizeof(int), s));
+    for (int l = 0; l < h->nlev; ++l) {
+        const level_info &L = h->lev[l];
+        ff_level &F = t.L[l];
+        F.box0 = L.box0;
+        F.nbox = L.nbox;
+        F.T = L.T;
+        F.ncones = L.ncones;
+        F.nc = L.nc;
+        F.hf = L.hf;
+        F.n_eq = L.n_eq;
+        F.n_chk = L.n_chk;
+        F.w = L.w;
+        F.rho2 = L.rho * L.rho;
+        F.far = phi_off[l + 1] > phi_off[l] ? 1 : 0;
+        if (!F.far) continue;
+        F.phi = phi.as<c64d>() + phi_off[l];
+        F.eq = h->eq_up[l].as<double>();
+        F.chk = h->chk_up[l].as<double>();
+        F.rot = L.hf ? h->rot[l].as<double>() : nullptr;
+        F.U = h->Uup[l].as<c64d>();
+        F.sig = h->sig[l].as<double>();
+        F.p = L.hf ? nullptr : h->p64[l].as<c64d>();
+        if (!L.hf) t.max_chk = std::max(t.max_chk, L.n_chk);
+        const int64_t nvec = (int64_t)L.nbox * L.ncones;
+        k_equiv_sources<<<(unsigned)std::min<int64_t>(nvec, 65535), 128, sizeof(c64d) * L.T, s>>>(
+            h->q64[l].as<c64d>(), h->Vup[l].as<c64d>(), L.T, L.n_eq, nvec, phi.as<c64d>() + phi_off[l]);
+        FDA_CHECK_LAUNCH();
+    }
+    const size_t dyn = sizeof(c64d) * (size_t)std::max(1, t.max_chk);
+    if (dyn > 96 * 1024) fda_fail(FDA_ERR_STATE, "fast field: more than 6,144 equivalent points at a level");
+    FDA_CUDA(cudaFuncSetAttribute(k_field_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    for (int64_t t0 = 0; t0 < ntgt; t0 += (1ll << 30)) {
+        const int64_t nb = std::min<int64_t>(1ll << 30, ntgt - t0);
+        k_field_fast<<<(unsigned)nb, FF, dyn, s>>>(t, h->qpt.as<double>(), h->qw.as<double>(), h->nrm.as<double>(),
+                                                   us, qs, tgt_dev + 3 * t0, nb, h->k, derr.as<int>(), out + t0);
+        FDA_CHECK_LAUNCH();
+    }
+    int herr = 0;
+    FDA_CUDA(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FDA_CUDA(cudaStreamSynchronize(s));
+    if (herr) fda_fail(FDA_ERR_STATE, "fast field: more than 2,048 boxes of one level near a point");
 }

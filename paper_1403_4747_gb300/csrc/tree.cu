@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "fda_internal.cuh"
+#include "tree_util.cuh"
 
 namespace {
 
@@ -42,17 +43,6 @@ __device__ __host__ inline uint64_t compact3(uint64_t v)
     v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
     v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
     v = (v ^ (v >> 32)) & 0x1fffffull;
-    return v;
-}
-
-__device__ __host__ inline uint64_t spread3h(uint64_t v)
-{
-    v &= 0x1fffffull;
-    v = (v | (v << 32)) & 0x1f00000000ffffull;
-    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
-    v = (v | (v << 8)) & 0x100f00f00f00f00full;
-    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
-    v = (v | (v << 2)) & 0x1249249249249249ull;
     return v;
 }
 
@@ -130,17 +120,7 @@ struct dev_levels {
 
 __device__ int find_box(const dev_levels &L, const uint64_t *bkey, int level, int x, int y, int z)
 {
-    int side = 1 << level;
-    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) return -1;
-    uint64_t key = (spread3h((uint64_t)x) << 2) | (spread3h((uint64_t)y) << 1) | spread3h((uint64_t)z);
-    int lo = L.box0[level], hi = L.box0[level] + L.nbox[level] - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        uint64_t k = bkey[mid];
-        if (k == key) return mid;
-        if (k < key) lo = mid + 1; else hi = mid - 1;
-    }
-    return -1;
+    return find_box_at(bkey, L.box0[level], L.nbox[level], level, x, y, z);
 }
 
 __device__ inline bool is_near(const dev_levels &L, int level, int dx, int dy, int dz)
@@ -149,23 +129,6 @@ __device__ inline bool is_near(const dev_levels &L, int level, int dx, int dy, i
     if (m <= 1) return true;
     if (L.hf[level]) return (double)(dx * dx + dy * dy + dz * dz) < L.rho2[level];
     return false;
-}
-
-// cone index of direction (dx, dy, dz): face (2 axis + sign), cell (a, b)
-__device__ __host__ inline int cone_index(double dx, double dy, double dz, int nc)
-{
-    double d[3] = {dx, dy, dz};
-    double ad[3] = {fabs(dx), fabs(dy), fabs(dz)};
-    int ax = 0;
-    if (ad[1] > ad[ax]) ax = 1;
-    if (ad[2] > ad[ax]) ax = 2;
-    int s = d[ax] > 0 ? 1 : 0;
-    int o0 = ax == 0 ? 1 : 0, o1 = ax == 2 ? 1 : 2;
-    double u = d[o0] / ad[ax], v = d[o1] / ad[ax];
-    int a = (int)floor((u + 1.0) * 0.5 * nc), b = (int)floor((v + 1.0) * 0.5 * nc);
-    a = a < 0 ? 0 : (a > nc - 1 ? nc - 1 : a);
-    b = b < 0 ? 0 : (b > nc - 1 ? nc - 1 : b);
-    return (2 * ax + s) * nc * nc + a * nc + b;
 }
 
 // interaction lists: pass 0 counts, pass 1 fills (cnt holds CSR offsets then)

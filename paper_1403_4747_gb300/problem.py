@@ -61,13 +61,16 @@ class FDAProblem:
         fn(self.h, self._c(u), self._c(q) if q is not None else None, d, F.data_ptr())
         return F
 
-    def scattered_field(self, u, points, q=None):
-        """Scattered field at host points [M, 3] off the surface."""
+    def scattered_field(self, u, points, q=None, fast=False):
+        """Scattered field at host points [M, 3] off the surface; fast=True
+        through the fast algorithm (L2T at each point's box, equivalent
+        sources and direct sums for the rest)."""
         import numpy as np
         import torch
         p = np.atleast_2d(np.asarray(points, dtype=np.float64))
         out = torch.empty(p.shape[0], dtype=torch.complex128, device="cuda")
-        _lib.fda_scattered_field(self.h, self._c(u), self._c(q) if q is not None else None, p, out.data_ptr())
+        fn = _lib.fda_scattered_field_fast if fast else _lib.fda_scattered_field
+        fn(self.h, self._c(u), self._c(q) if q is not None else None, p, out.data_ptr())
         return out
 
     def rhs_neumann(self, q, b=None):

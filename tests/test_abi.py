@@ -122,3 +122,4 @@ def test_null_handle_calls_of_the_right_hand_sides_and_fields(lib):
     assert lib.fda_rhs_point_source(None, None, 1, None) == FDA_ERR_ARG
     assert lib.fda_far_field(None, None, None, None, 1, None) == FDA_ERR_ARG
     assert lib.fda_scattered_field(None, None, None, None, 1, None) == FDA_ERR_ARG
+    assert lib.fda_scattered_field_fast(None, None, None, None, 1, None) == FDA_ERR_ARG

@@ -114,3 +114,70 @@ def test_fast_pattern_without_far_field_is_the_direct_sum():
     u = _dev(complex_normal(len(f), seed=43))
     dirs = fibonacci_directions(9)
     assert _rel(P.far_field(u, dirs, fast=True).cpu().numpy(), P.far_field(u, dirs).cpu().numpy()) < 1e-13
+
+
+def _field_points(seed):
+    """Points of every kind the fast field distinguishes: just off the
+    surface (inside leaf boxes: L2T at the point's leaf), a shell in the
+    empty part of the tree's cubes, inside the body, and outside the root
+    cube at growing distance (the whole tree through equivalent sources)."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(96, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    radii = np.concatenate([np.full(24, 1.04), np.full(24, 1.3), np.full(16, 0.45), np.full(16, 2.5),
+                            np.full(16, 9.0)])
+    return d * radii[:, None], radii
+
+
+@pytest.mark.parametrize("mesh,k", [("sphere4", 20.0), ("ellipsoid4", 15.0), ("sphere5", 25.0)])
+@pytest.mark.parametrize("with_q", [False, True])
+def test_fast_field_matches_direct_and_oracle(mesh, k, with_q):
+    """fda_scattered_field_fast (L2T at the point's low-frequency box from
+    the FP64 downward pass, equivalent sources of the boxes the point is
+    not near, six-point sums of the near leaves) agrees with the direct
+    six-point sums and the oracle's field, group by group of points.  Bound
+    1e-3 relative per group: the translations are truncated at eps = 1e-4
+    relative to each box's field."""
+    from paper_1403_4747_gb300 import FDAProblem
+    level = int(mesh[-1])
+    v, f = icosphere(level) if mesh.startswith("sphere") else ellipsoid_from_icosphere(level)
+    P = FDAProblem(v, f, k)
+    st = P.stats()
+    assert any(st.level_regime[l] == 1 for l in range(st.n_levels))
+    u = complex_normal(len(f), seed=51)
+    q = complex_normal(len(f), seed=52) if with_q else None
+    pts, radii = _field_points(53)
+    ud, qd = _dev(u), (_dev(q) if with_q else None)
+    fast = P.scattered_field(ud, pts, qd, fast=True).cpu().numpy()
+    direct = P.scattered_field(ud, pts, qd).cpu().numpy()
+    ref = oracle.scattered_field(v, f, k, u, pts, q=q)
+    for r in np.unique(radii):
+        m = radii == r
+        e_dir, e_ref = _rel(fast[m], direct[m]), _rel(fast[m], ref[m])
+        print("%s k %g q %s r %.2f: fast field vs direct %.2e, vs oracle %.2e" % (mesh, k, with_q, r, e_dir, e_ref))
+        assert e_dir < 1e-3 and e_ref < 1e-3
+    P.close()
+
+
+def test_fast_field_of_gpu_solution_against_mie():
+    from paper_1403_4747_gb300 import FDAProblem
+    k = 5.0
+    v, f = icosphere(5)
+    P = FDAProblem(v, f, k, precision=1)
+    u, info = P.solve(P.rhs_plane_wave([0.0, 0.0, 1.0]), 1e-6)
+    dirs = fibonacci_directions(10)
+    us = P.scattered_field(u, dirs * 2.0, fast=True).cpu().numpy()
+    assert _rel(us, oracle.mie_scattered_field(k, 2.0, dirs[:, 2])) < 2e-3
+    assert _rel(us, P.scattered_field(u, dirs * 2.0).cpu().numpy()) < 1e-4
+    P.close()
+
+
+def test_fast_field_without_far_field_is_the_direct_sum():
+    """One leaf, no interaction lists: the fast field is the direct sum."""
+    from paper_1403_4747_gb300 import FDAProblem
+    v, f = icosphere(0)
+    P = FDAProblem(v, f, 3.0)
+    u = _dev(complex_normal(len(f), seed=54))
+    pts, _ = _field_points(55)
+    assert _rel(P.scattered_field(u, pts, fast=True).cpu().numpy(), P.scattered_field(u, pts).cpu().numpy()) < 1e-13
+    P.close()
