@@ -268,7 +268,7 @@ constexpr int LPB = 8;
 // q~_B = S~_B x_B: lane t < T (rows lane, lane + 32, ...) sums over the
 // leaf's elements eight at a time; x_B (n_B <= 64) sits in two registers per
 // lane and is broadcast by shuffles
-template <typename R>
+template <typename R, bool ADD = false>  // ADD: q~ += S~ x (a second layer of sources)
 __global__ void __launch_bounds__(32 * LPB) k_s2m_w(lvl_ptrs<R> P, int nleaf, const int32_t *leaf_box,
                                                      const int32_t *blev, const int32_t *bbeg, const int32_t *bend,
                                                      const int64_t *loff, const cx<R> *St, const void *x, int x64)
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(32 * LPB) k_s2m_w(lvl_ptrs<R> P, int nleaf, co
                 cfma(acc, sv[u], xj);
             }
         }
-        if (on) q[t] = acc;
+        if (on) q[t] = ADD ? q[t] + acc : acc;
     }
 }
 
@@ -417,6 +417,60 @@ void lowrank_m2l(fda_handle *h, lr_bucket &B, int l, const lvl_ptrs<R> &P, int m
     }
 }
 
+// M2M, M2L and L2L of one apply (Sec. 3.3 Steps 2-3) on the densities of P,
+// the leaves' q~ already in place; mark(i) records the pass boundaries 3-5.
+// With tc (FP32): every translation reads bf16 hi/lo splits of its source
+// level, made once that level is complete.
+template <typename R, typename Mark>
+void translate_passes(fda_handle *h, const lvl_ptrs<R> &P, int mr, bool tc, Mark mark)
+{
+    cudaStream_t s = h->stream;
+    auto c32 = [](auto *v) { return reinterpret_cast<c32f *>(v); };
+    // M2M bottom-up: q~_parent += M~ q~_child
+    for (int l = h->nlev - 2; l >= h->lev_lo; --l) {
+        if (tc) {
+            fda_split_tc(h, l + 1, c32(P.q[l + 1]), h->qs[l + 1], mr);
+            fda_run_tc(h, h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], P.stride[l + 1] / std::max(1, h->lev[l + 1].T),
+                       c32(P.q[l]), mr, P.stride[l]);
+        } else {
+            fda_run_batch<R>(h->b_m2m[l], P.Mt[l], h->lev[l].T, h->lev[l + 1].T, P.q[l + 1], P.q[l], mr,
+                             P.stride[l + 1], P.stride[l], s);
+        }
+    }
+    if (tc) fda_split_tc(h, h->lev_lo, c32(P.q[h->lev_lo]), h->qs[h->lev_lo], mr);
+    mark(3);
+    // M2L at every level: p~_target += K~ q~_source
+    // (the CUDA-core forms always apply the low-rank operators of Sec. 4.2
+    // in two stages; the tensor-core form does so where the autotuner found
+    // it faster, else it applies every operator in full)
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        const bool lr = !h->lr[l].empty() && (!tc || (mr == 1 ? h->lr_tc[l] : h->lr_tc_many[l]));
+        if (tc) {
+            tr_batch &F = lr || h->lr[l].empty() ? h->b_m2l[l] : h->b_m2l_all[l];
+            fda_run_tc(h, F, h->tc_m2l[l], h->qs[l], P.stride[l] / std::max(1, h->lev[l].T), c32(P.p[l]), mr,
+                       P.stride[l]);
+        } else {
+            fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
+                             P.stride[l], s);
+        }
+        if (lr)
+            for (lr_bucket &B : h->lr[l]) lowrank_m2l<R>(h, B, l, P, mr, tc);
+    }
+    mark(4);
+    // L2L top-down: p~_child += L~ p~_parent
+    for (int l = h->lev_lo; l + 1 < h->nlev; ++l) {
+        if (tc) {
+            fda_split_tc(h, l, c32(P.p[l]), h->ps[l], mr);
+            fda_run_tc(h, h->b_l2l[l], h->tc_l2l[l], h->ps[l], P.stride[l] / std::max(1, h->lev[l].T),
+                       c32(P.p[l + 1]), mr, P.stride[l + 1]);
+        } else {
+            fda_run_batch<R>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], mr,
+                             P.stride[l], P.stride[l + 1], s);
+        }
+    }
+    mark(5);
+}
+
 // side 0: the Burton-Miller operator of Eq. eq_sum applied to u; side 1: the
 // right-hand side's layers of Eq. eq_bm applied to q = du/dn (its own near
 // field and single-layer S2M; every translation and the L2T are shared)
@@ -498,53 +552,8 @@ void apply_impl(fda_handle *h, far_ops<R> &ops, dbuf *q, dbuf *p, const void *x,
         FDA_CHECK_LAUNCH();
     }
     mark(2);
-    // tensor cores (chosen precision): every translation reads bf16 hi/lo
-    // splits of its source level, made once that level is complete
     const bool tc = sizeof(R) == 4 && h->have_tc && h->cfg.tensor_cores;
-    auto c32 = [](auto *v) { return reinterpret_cast<c32f *>(v); };
-    // M2M bottom-up: q~_parent += M~ q~_child
-    for (int l = h->nlev - 2; l >= h->lev_lo; --l) {
-        if (tc) {
-            fda_split_tc(h, l + 1, c32(P.q[l + 1]), h->qs[l + 1], mr);
-            fda_run_tc(h, h->b_m2m[l], h->tc_m2m[l], h->qs[l + 1], P.stride[l + 1] / std::max(1, h->lev[l + 1].T),
-                       c32(P.q[l]), mr, P.stride[l]);
-        } else {
-            fda_run_batch<R>(h->b_m2m[l], P.Mt[l], h->lev[l].T, h->lev[l + 1].T, P.q[l + 1], P.q[l], mr,
-                             P.stride[l + 1], P.stride[l], s);
-        }
-    }
-    if (tc) fda_split_tc(h, h->lev_lo, c32(P.q[h->lev_lo]), h->qs[h->lev_lo], mr);
-    mark(3);
-    // M2L at every level: p~_target += K~ q~_source
-    // (the CUDA-core forms always apply the low-rank operators of Sec. 4.2
-    // in two stages; the tensor-core form does so where the autotuner found
-    // it faster, else it applies every operator in full)
-    for (int l = h->lev_lo; l < h->nlev; ++l) {
-        const bool lr = !h->lr[l].empty() && (!tc || (mr == 1 ? h->lr_tc[l] : h->lr_tc_many[l]));
-        if (tc) {
-            tr_batch &F = lr || h->lr[l].empty() ? h->b_m2l[l] : h->b_m2l_all[l];
-            fda_run_tc(h, F, h->tc_m2l[l], h->qs[l], P.stride[l] / std::max(1, h->lev[l].T), c32(P.p[l]), mr,
-                       P.stride[l]);
-        } else {
-            fda_run_batch<R>(h->b_m2l[l], P.Kt[l], h->lev[l].T, h->lev[l].T, P.q[l], P.p[l], mr, P.stride[l],
-                             P.stride[l], s);
-        }
-        if (lr)
-            for (lr_bucket &B : h->lr[l]) lowrank_m2l<R>(h, B, l, P, mr, tc);
-    }
-    mark(4);
-    // L2L top-down: p~_child += L~ p~_parent
-    for (int l = h->lev_lo; l + 1 < h->nlev; ++l) {
-        if (tc) {
-            fda_split_tc(h, l, c32(P.p[l]), h->ps[l], mr);
-            fda_run_tc(h, h->b_l2l[l], h->tc_l2l[l], h->ps[l], P.stride[l] / std::max(1, h->lev[l].T),
-                       c32(P.p[l + 1]), mr, P.stride[l + 1]);
-        } else {
-            fda_run_batch<R>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], mr,
-                             P.stride[l], P.stride[l + 1], s);
-        }
-    }
-    mark(5);
+    translate_passes<R>(h, P, mr, tc, mark);
     if (leaf_tc) {
         fda_leaf_tc(h, 2, ops.Tt, nullptr, y, mr);
     } else if (mr == 1) {
@@ -654,6 +663,63 @@ void fda_downward_fp64(fda_handle *h)
     for (int l = h->lev_lo; l + 1 < h->nlev; ++l)
         fda_run_batch<double>(h->b_l2l[l], P.Lt[l], h->lev[l + 1].T, h->lev[l].T, P.p[l], P.p[l + 1], 1,
                               P.stride[l], P.stride[l + 1], s);
+}
+
+__global__ void k_c32_to_c64(const c32f *a, c64d *b, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = c64d(a[i].re, a[i].im);
+}
+
+// Upward and downward passes in the chosen precision for the sources
+// -D[u] + S[q] (xs = -u, qs = q or null; FP64, Morton order): S2M of xs by
+// the operator's FP32 S2M and of qs by the right-hand side's (added), then
+// M2M, M2L and L2L exactly as in an apply (the tensor cores where the
+// handle uses them); the complete outgoing and local densities are then
+// copied into q64 and p64.
+void fda_translate_chosen(fda_handle *h, const c64d *xs, const c64d *qs)
+{
+    if (h->lev_lo < 0) return;
+    if (!h->have32) fda_fail(FDA_ERR_STATE, "FP32 operators were not built (precision = plain)");
+    if (qs && !h->op32.St1.p) fda_fail(FDA_ERR_STATE, "FP32 S2M operators of the right-hand side's layers missing");
+    cudaStream_t s = h->stream;
+    const int NL = h->nleaf;
+    const int64_t N = h->N;
+    if (!h->xs32.p) h->xs32.alloc(sizeof(c32f) * N * std::max(1, h->cfg.max_rhs));
+    dbuf q32;
+    lvl_ptrs<float> P = make_ptrs<float>(h, h->op32, h->q32, h->p32);
+    const int nl = h->nlev - h->lev_lo;
+    int64_t maxn = 0;
+    for (int l = h->lev_lo; l < h->nlev; ++l) maxn = std::max(maxn, P.stride[l]);
+    const int gx = (int)std::min<int64_t>(2048, std::max<int64_t>(16, maxn / 2048));
+    k_zero_levels<float><<<dim3(gx, 2 * nl), 256, 0, s>>>(P, h->lev_lo, 1);
+    FDA_CHECK_LAUNCH();
+    k_c64_to_c32<<<fda_blocks(N, 256), 256, 0, s>>>(xs, h->xs32.as<c32f>(), N);
+    FDA_CHECK_LAUNCH();
+    k_s2m_w<float><<<(NL + LPB - 1) / LPB, 32 * LPB, 0, s>>>(
+        P, NL, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
+        h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(), h->op32.St.as<c32f>(), h->xs32.p, 0);
+    FDA_CHECK_LAUNCH();
+    if (qs) {
+        q32.alloc(sizeof(c32f) * N);
+        k_c64_to_c32<<<fda_blocks(N, 256), 256, 0, s>>>(qs, q32.as<c32f>(), N);
+        FDA_CHECK_LAUNCH();
+        k_s2m_w<float, true><<<(NL + LPB - 1) / LPB, 32 * LPB, 0, s>>>(
+            P, NL, h->leaf_box.as<int32_t>(), h->box_level.as<int32_t>(), h->box_begin.as<int32_t>(),
+            h->box_end.as<int32_t>(), h->leaf_op_off.as<int64_t>(), h->op32.St1.as<c32f>(), q32.p, 0);
+        FDA_CHECK_LAUNCH();
+    }
+    translate_passes<float>(h, P, 1, h->have_tc && h->cfg.tensor_cores, [](int) {});
+    for (int l = h->lev_lo; l < h->nlev; ++l) {
+        if (P.T[l] == 0 || !h->q64[l].p || !h->p64[l].p) continue;
+        const int64_t n = P.stride[l];
+        k_c32_to_c64<<<(unsigned)std::min<int64_t>(2048, std::max<int64_t>(1, n / 256)), 256, 0, s>>>(
+            h->q32[l].as<c32f>(), h->q64[l].as<c64d>(), n);
+        k_c32_to_c64<<<(unsigned)std::min<int64_t>(2048, std::max<int64_t>(1, n / 256)), 256, 0, s>>>(
+            h->p32[l].as<c32f>(), h->p64[l].as<c64d>(), n);
+        FDA_CHECK_LAUNCH();
+    }
+    FDA_CUDA(cudaStreamSynchronize(s));  // q32 (scratch) is freed on return
 }
 
 void fda_alloc_densities(fda_handle *h, int want32)

@@ -374,6 +374,9 @@ void fda_upward_fp64(fda_handle *h, const c64d *xs, int side, int add);
 void fda_m2m_fp64(fda_handle *h);
 // FP64 downward pass on q64: M2L at every level and L2L, local densities in p64
 void fda_downward_fp64(fda_handle *h);
+// the same outgoing and local densities of -D[u] + S[q] in the chosen precision
+// (FP32 S2M, tensor-core translations), copied into q64 and p64; xs = -u, qs = q
+void fda_translate_chosen(fda_handle *h, const c64d *xs, const c64d *qs);
 void fda_gather_to_sorted(fda_handle *h, const c64d *x, c64d *xs);
 void fda_scatter_from_sorted(fda_handle *h, const c64d *ys, c64d *y);
 void fda_gather_cols(fda_handle *h, const c64d *x, int64_t ld, c64d *xs, int nrhs, cudaStream_t s);

@@ -581,9 +581,10 @@ void fda_far_field_upward(fda_handle *h, const c64d *u, const c64d *q, const dou
 }
 
 // Scattered field at points through the fast algorithm (see k_field_fast):
-// the outgoing densities of -D[u] + S[q] by S2M and M2M in FP64, the local
-// densities by M2L and L2L in FP64, the equivalent sources of every box, then
-// one CTA per point.  u, q: caller order (device, q may be null); tgt:
+// the outgoing densities of -D[u] + S[q] by S2M and M2M, the local densities
+// by M2L and L2L (in FP64, or as in the chosen form's apply when the handle
+// is in the chosen precision), the equivalent sources of every box, then one
+// CTA per point (FP64 arithmetic).  u, q: caller order (device, q may be null); tgt:
 // device [ntgt][3]; out: device [ntgt], overwritten.
 void fda_field_fast(fda_handle *h, const c64d *u, const c64d *q, const double *tgt_dev, int64_t ntgt, c64d *out)
 {
@@ -602,13 +603,16 @@ void fda_field_fast(fda_handle *h, const c64d *u, const c64d *q, const double *t
     if (q) fda_gather_cols(h, q, h->N, qs, 1, s);
     k_negate<<<fda_blocks(h->N, 256), 256, 0, s>>>(us, h->N);
     FDA_CHECK_LAUNCH();
-    fda_upward_fp64(h, us, 0, 0);
-    if (q) {
-        fda_rhs_layers_prepare(h);
-        fda_upward_fp64(h, qs, 1, 1);
+    if (q) fda_rhs_layers_prepare(h);
+    if (h->cfg.precision == FDA_CHOSEN_FP32 && h->have32) {
+        // the translations as in the chosen form's apply, densities then in FP64
+        fda_translate_chosen(h, us, qs);
+    } else {
+        fda_upward_fp64(h, us, 0, 0);
+        if (q) fda_upward_fp64(h, qs, 1, 1);
+        fda_m2m_fp64(h);
+        fda_downward_fp64(h);
     }
-    fda_m2m_fp64(h);
-    fda_downward_fp64(h);
     ff_tree t;
     memset(&t, 0, sizeof(t));
     t.nlev = h->nlev;

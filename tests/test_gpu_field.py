@@ -131,17 +131,19 @@ def _field_points(seed):
 
 @pytest.mark.parametrize("mesh,k", [("sphere4", 20.0), ("ellipsoid4", 15.0), ("sphere5", 25.0)])
 @pytest.mark.parametrize("with_q", [False, True])
-def test_fast_field_matches_direct_and_oracle(mesh, k, with_q):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fast_field_matches_direct_and_oracle(mesh, k, with_q, precision):
     """fda_scattered_field_fast (L2T at the point's low-frequency box from
-    the FP64 downward pass, equivalent sources of the boxes the point is
-    not near, six-point sums of the near leaves) agrees with the direct
-    six-point sums and the oracle's field, group by group of points.  Bound
-    1e-3 relative per group: the translations are truncated at eps = 1e-4
-    relative to each box's field."""
+    the downward pass, equivalent sources of the boxes the point is not
+    near, six-point sums of the near leaves) agrees with the direct
+    six-point sums and the oracle's field, group by group of points, with
+    the translations in FP64 (plain) and as in the chosen form's apply (FP32
+    S2M, tensor-core M2M / M2L / L2L).  Bound 1e-3 relative per group: the
+    translations are truncated at eps = 1e-4 relative to each box's field."""
     from paper_1403_4747_gb300 import FDAProblem
     level = int(mesh[-1])
     v, f = icosphere(level) if mesh.startswith("sphere") else ellipsoid_from_icosphere(level)
-    P = FDAProblem(v, f, k)
+    P = FDAProblem(v, f, k, precision=precision)
     st = P.stats()
     assert any(st.level_regime[l] == 1 for l in range(st.n_levels))
     u = complex_normal(len(f), seed=51)
@@ -154,7 +156,8 @@ def test_fast_field_matches_direct_and_oracle(mesh, k, with_q):
     for r in np.unique(radii):
         m = radii == r
         e_dir, e_ref = _rel(fast[m], direct[m]), _rel(fast[m], ref[m])
-        print("%s k %g q %s r %.2f: fast field vs direct %.2e, vs oracle %.2e" % (mesh, k, with_q, r, e_dir, e_ref))
+        print("%s k %g q %s precision %d r %.2f: fast field vs direct %.2e, vs oracle %.2e"
+              % (mesh, k, with_q, precision, r, e_dir, e_ref))
         assert e_dir < 1e-3 and e_ref < 1e-3
     P.close()
 
