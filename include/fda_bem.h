@@ -240,8 +240,10 @@ fda_status fda_far_field_fast(fda_handle *h, const fda_c128 *u, const fda_c128 *
                               fda_c128 *F);
 /* The same scattered field u_sc at points through the fast algorithm
  * (Sec. 3.3 Steps 2-3 with the points as L2T targets): the outgoing densities
- * of -D[u] + S[q] by S2M and M2M, the local densities by M2L and L2L (all in
- * FP64, once per call), then per point:
+ * of -D[u] + S[q] by S2M and M2M, the local densities by M2L and L2L (once
+ * per call: in FP64, or in the chosen precision as in its apply, FP32 S2M
+ * and tensor-core translations), then per point (FP64 arithmetic, FP32 in
+ * the chosen precision):
  *   * the point is placed in the deepest box of the tree whose cube contains
  *     it; if that box A is a low-frequency box with local densities, the
  *     field of every source A's local density covers (the interaction lists

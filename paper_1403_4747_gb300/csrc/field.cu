@@ -210,7 +210,7 @@ constexpr int FLIST = 8 * FCH;  // equivalent-source and direct lists of a round
 struct ff_level {
     int box0, nbox, T, ncones, nc, hf, n_eq, n_chk, far;  // far: outgoing densities at this level
     double w, rho2;
-    const c64d *phi;    // [nbox][ncones][n_eq] equivalent sources V q~
+    const void *phi;    // [nbox][ncones][n_eq] equivalent sources V q~ (in the arithmetic type)
     const c64d *p;      // [nbox][T] local densities (low frequency; null elsewhere)
     const double *eq;   // [n_eq][3] equivalent points, box-relative (cone frame at high frequency)
     const double *chk;  // [n_chk][3] the L2T's equivalent points (the upward check points)
@@ -242,51 +242,56 @@ __device__ inline bool ff_near(const ff_level &L, int dx, int dy, int dz)
     return false;
 }
 
-// a += G(x, y) b, G = e^{ikR}/(4 pi R)
-__device__ inline void ff_acc_g(double &are, double &aim, const double *x, double y0, double y1, double y2, double k,
-                                c64d b)
+__device__ inline void ff_sincos(double a, double *sn, double *cs) { sincos(a, sn, cs); }
+__device__ inline void ff_sincos(float a, float *sn, float *cs) { sincosf(a, sn, cs); }
+
+// a += G(x, y) b, G = e^{ikR}/(4 pi R), in the arithmetic type F (the
+// difference x - y in FP64)
+template <typename F>
+__device__ inline void ff_acc_g(F &are, F &aim, const double *x, double y0, double y1, double y2, F k, cx<F> b)
 {
-    const double r0 = x[0] - y0, r1 = x[1] - y1, r2 = x[2] - y2;
-    const double R = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-    double sn, cs;
-    sincos(k * R, &sn, &cs);
-    const double g = 1.0 / (4.0 * FDA_PI * R);
-    const double gre = g * cs, gim = g * sn;
+    const F r0 = (F)(x[0] - y0), r1 = (F)(x[1] - y1), r2 = (F)(x[2] - y2);
+    const F R = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    F sn, cs;
+    ff_sincos(k * R, &sn, &cs);
+    const F g = (F)1 / ((F)(4.0 * FDA_PI) * R);
+    const F gre = g * cs, gim = g * sn;
     are += gre * b.re - gim * b.im;
     aim += gre * b.im + gim * b.re;
 }
 
 // one warp: the six-point sums of the elements [j0, j1) of a leaf,
 // w [G q + dG/dn_y un] with un = -u
+template <typename F>
 __device__ inline void ff_direct(int j0, int j1, const double *qpt, const double *qw, const double *nrm,
-                                 const c64d *un, const c64d *q, const double *x, double k, int lane, double &are,
-                                 double &aim)
+                                 const c64d *un, const c64d *q, const double *x, F k, int lane, F &are, F &aim)
 {
     for (int t = j0 * 6 + lane; t < j1 * 6; t += 32) {
         const int j = t / 6, g = t - 6 * (t / 6);
         const double *y = qpt + 18 * (int64_t)j + 3 * g, *ny = nrm + 3 * (int64_t)j;
-        const double w = qw[6 * (int64_t)j + g];
-        const double r0 = x[0] - y[0], r1 = x[1] - y[1], r2 = x[2] - y[2];
-        const double R2 = r0 * r0 + r1 * r1 + r2 * r2, R = sqrt(R2);
-        double sn, cs;
-        sincos(k * R, &sn, &cs);
-        const double gw = w / (4.0 * FDA_PI * R);
+        const F w = (F)qw[6 * (int64_t)j + g];
+        const F r0 = (F)(x[0] - y[0]), r1 = (F)(x[1] - y[1]), r2 = (F)(x[2] - y[2]);
+        const F R2 = r0 * r0 + r1 * r1 + r2 * r2, R = sqrt(R2);
+        F sn, cs;
+        ff_sincos(k * R, &sn, &cs);
+        const F gw = w / ((F)(4.0 * FDA_PI) * R);
         // dG/dn_y = e^{ikR}(1 - ikR)(r.n_y)/(4 pi R^3)
-        const double f = gw * (r0 * ny[0] + r1 * ny[1] + r2 * ny[2]) / R2;
-        const double dre = f * (cs + k * R * sn), dim = f * (sn - k * R * cs);
-        const double gre = gw * cs, gim = gw * sn;
-        const c64d uj = un[j], qj = q ? q[j] : c64d(0.0, 0.0);
+        const F f = gw * (r0 * (F)ny[0] + r1 * (F)ny[1] + r2 * (F)ny[2]) / R2;
+        const F dre = f * (cs + k * R * sn), dim = f * (sn - k * R * cs);
+        const F gre = gw * cs, gim = gw * sn;
+        const c64d u64 = un[j], q64 = q ? q[j] : c64d(0.0, 0.0);
+        const cx<F> uj((F)u64.re, (F)u64.im), qj((F)q64.re, (F)q64.im);
         are += gre * qj.re - gim * qj.im + dre * uj.re - dim * uj.im;
         aim += gre * qj.im + gim * qj.re + dre * uj.im + dim * uj.re;
     }
 }
 
 // one warp: box b of level l through its equivalent sources of cone u
-__device__ inline void ff_m2t(const ff_tree &t, int l, int b, int u, const double *x, double k, int lane,
-                              double &are, double &aim)
+template <typename F>
+__device__ inline void ff_m2t(const ff_tree &t, int l, int b, int u, const double *x, F k, int lane, F &are, F &aim)
 {
     const ff_level &L = t.L[l];
-    const c64d *phi = L.phi + ((int64_t)(b - L.box0) * L.ncones + u) * L.n_eq;
+    const cx<F> *phi = reinterpret_cast<const cx<F> *>(L.phi) + ((int64_t)(b - L.box0) * L.ncones + u) * L.n_eq;
     const int32_t *cb = t.coord + 3 * (int64_t)b;
     const double c0 = t.lo[0] + (cb[0] + 0.5) * L.w, c1 = t.lo[1] + (cb[1] + 0.5) * L.w,
                  c2 = t.lo[2] + (cb[2] + 0.5) * L.w;
@@ -299,17 +304,20 @@ __device__ inline void ff_m2t(const ff_tree &t, int l, int b, int u, const doubl
             y1 = R[3] * f[0] + R[4] * f[1] + R[5] * f[2];
             y2 = R[6] * f[0] + R[7] * f[1] + R[8] * f[2];
         }
-        ff_acc_g(are, aim, x, c0 + y0, c1 + y1, c2 + y2, k, phi[e]);
+        ff_acc_g<F>(are, aim, x, c0 + y0, c1 + y1, c2 + y2, k, phi[e]);
     }
 }
 
 // One CTA per target.  err[0] records a near set above its capacity (the
 // target's value is then left at NaN and the host reports the error).
+template <typename F>
 __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt, const double *qw,
                                                    const double *nrm, const c64d *un, const c64d *q,
-                                                   const double *tgt, int64_t ntgt, double k, int *err, c64d *out)
+                                                   const double *tgt, int64_t ntgt, double kd, int *err, c64d *out)
 {
-    extern __shared__ c64d psi[];  // [max_chk]
+    extern __shared__ __align__(16) uint8_t psi_raw[];
+    cx<F> *psi = reinterpret_cast<cx<F> *>(psi_raw);  // [max_chk]
+    const F k = (F)kd;
     __shared__ int sset[2][FSET];
     __shared__ int mlist[FLIST], mcone[FLIST], dlist[FLIST];
     __shared__ int ns, nn, nm, nd, overflow, lA, A;
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt,
     if (ti >= ntgt) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double x[3] = {tgt[3 * ti], tgt[3 * ti + 1], tgt[3 * ti + 2]};
-    double are = 0.0, aim = 0.0;
+    F are = 0, aim = 0;
     // the chain of boxes containing x, down to a leaf or an empty cube
     if (threadIdx.x == 0) {
         A = -1;
@@ -346,11 +354,11 @@ __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt,
         const ff_level &L = t.L[lA];
         const c64d *pA = L.p + (int64_t)(A - L.box0) * L.T;
         for (int m = threadIdx.x; m < L.n_chk; m += FF) {
-            c64d a;
+            cx<F> a;
             for (int s = 0; s < L.T; ++s) {
                 const c64d uv = L.U[m + (int64_t)s * L.n_chk];
                 const double f = 1.0 / L.sig[s];
-                cfma_conj(a, uv, c64d(f * pA[s].re, f * pA[s].im));
+                cfma_conj(a, cx<F>((F)uv.re, (F)uv.im), cx<F>((F)(f * pA[s].re), (F)(f * pA[s].im)));
             }
             psi[m] = a;
         }
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt,
         const double a0 = t.lo[0] + (cA[0] + 0.5) * L.w, a1 = t.lo[1] + (cA[1] + 0.5) * L.w,
                      a2 = t.lo[2] + (cA[2] + 0.5) * L.w;
         for (int m = threadIdx.x; m < L.n_chk; m += FF)
-            ff_acc_g(are, aim, x, a0 + L.chk[3 * m], a1 + L.chk[3 * m + 1], a2 + L.chk[3 * m + 2], k, psi[m]);
+            ff_acc_g<F>(are, aim, x, a0 + L.chk[3 * m], a1 + L.chk[3 * m + 1], a2 + L.chk[3 * m + 2], k, psi[m]);
         // A's near field as if A were a leaf: leaves near A's ancestors at
         // coarser low-frequency levels, and every box near A (opened below)
         for (int l = 0; l <= lA; ++l) {
@@ -388,7 +396,7 @@ __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt,
     // direct sums of the leaves found so far
     for (int i = warp; i < min(nd, FLIST); i += FF / 32) {
         const int X = dlist[i];
-        ff_direct(t.bbeg[X], t.bend[X], qpt, qw, nrm, un, q, x, k, lane, are, aim);
+        ff_direct<F>(t.bbeg[X], t.bend[X], qpt, qw, nrm, un, q, x, k, lane, are, aim);
     }
     int cur = 0;
     for (int l = l0; l < t.nlev; ++l) {
@@ -436,10 +444,10 @@ __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt,
                 }
             }
             __syncthreads();
-            for (int i = warp; i < min(nm, FLIST); i += FF / 32) ff_m2t(t, l + 1, mlist[i], mcone[i], x, k, lane, are, aim);
+            for (int i = warp; i < min(nm, FLIST); i += FF / 32) ff_m2t<F>(t, l + 1, mlist[i], mcone[i], x, k, lane, are, aim);
             for (int i = warp; i < min(nd, FLIST); i += FF / 32) {
                 const int X = dlist[i];
-                ff_direct(t.bbeg[X], t.bend[X], qpt, qw, nrm, un, q, x, k, lane, are, aim);
+                ff_direct<F>(t.bbeg[X], t.bend[X], qpt, qw, nrm, un, q, x, k, lane, are, aim);
             }
         }
         __syncthreads();
@@ -447,13 +455,14 @@ __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt,
         cur ^= 1;
     }
     __syncthreads();
+    double dre = are, dim = aim;  // partial sums added in FP64
     for (int o = 16; o > 0; o >>= 1) {
-        are += __shfl_xor_sync(0xffffffffu, are, o);
-        aim += __shfl_xor_sync(0xffffffffu, aim, o);
+        dre += __shfl_xor_sync(0xffffffffu, dre, o);
+        dim += __shfl_xor_sync(0xffffffffu, dim, o);
     }
     if (lane == 0) {
-        red[warp][0] = are;
-        red[warp][1] = aim;
+        red[warp][0] = dre;
+        red[warp][1] = dim;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -472,16 +481,21 @@ __global__ void __launch_bounds__(FF) k_field_fast(ff_tree t, const double *qpt,
 
 // equivalent sources phi = V q~ of every box and cone of one level
 // (one block per box and cone)
-__global__ void k_equiv_sources(const c64d *qd, const c64d *V, int T, int n_eq, int64_t nvec, c64d *phi)
+template <typename F>
+__global__ void k_equiv_sources(const c64d *qd, const c64d *V, int T, int n_eq, int64_t nvec, cx<F> *phi)
 {
-    extern __shared__ c64d qsm[];  // [T]
+    extern __shared__ __align__(16) uint8_t qsm_raw[];
+    cx<F> *qsm = reinterpret_cast<cx<F> *>(qsm_raw);  // [T]
     for (int64_t v = blockIdx.x; v < nvec; v += gridDim.x) {
         __syncthreads();
-        for (int s = threadIdx.x; s < T; s += blockDim.x) qsm[s] = qd[v * T + s];
+        for (int s = threadIdx.x; s < T; s += blockDim.x) qsm[s] = cx<F>((F)qd[v * T + s].re, (F)qd[v * T + s].im);
         __syncthreads();
         for (int e = threadIdx.x; e < n_eq; e += blockDim.x) {
-            c64d a;
-            for (int s = 0; s < T; ++s) cfma(a, V[e + (int64_t)s * n_eq], qsm[s]);
+            cx<F> a;
+            for (int s = 0; s < T; ++s) {
+                const c64d vv = V[e + (int64_t)s * n_eq];
+                cfma(a, cx<F>((F)vv.re, (F)vv.im), qsm[s]);
+            }
             phi[v * n_eq + e] = a;
         }
     }
@@ -580,39 +594,14 @@ void fda_far_field_upward(fda_handle *h, const c64d *u, const c64d *q, const dou
     FDA_CHECK_LAUNCH();
 }
 
-// Scattered field at points through the fast algorithm (see k_field_fast):
-// the outgoing densities of -D[u] + S[q] by S2M and M2M, the local densities
-// by M2L and L2L (in FP64, or as in the chosen form's apply when the handle
-// is in the chosen precision), the equivalent sources of every box, then one
-// CTA per point (FP64 arithmetic).  u, q: caller order (device, q may be null); tgt:
-// device [ntgt][3]; out: device [ntgt], overwritten.
-void fda_field_fast(fda_handle *h, const c64d *u, const c64d *q, const double *tgt_dev, int64_t ntgt, c64d *out)
+namespace {
+
+// equivalent sources of every level and the point kernel, arithmetic type F
+// (the densities in q64 / p64 are complete; us = -u, qs = q, Morton order)
+template <typename F>
+void field_points(fda_handle *h, const c64d *us, const c64d *qs, const double *tgt_dev, int64_t ntgt, c64d *out)
 {
     cudaStream_t s = h->stream;
-    if (ntgt == 0 || h->N == 0) {
-        FDA_CUDA(cudaMemsetAsync(out, 0, sizeof(c64d) * ntgt, s));
-        return;
-    }
-    // no level with interaction lists: every pair is near and the direct sum is the method
-    if (h->lev_lo < 0) {
-        fda_field(h, u, q, tgt_dev, ntgt, 0, out);
-        return;
-    }
-    c64d *us = h->xs.as<c64d>(), *qs = q ? h->ys.as<c64d>() : nullptr;
-    fda_gather_cols(h, u, h->N, us, 1, s);
-    if (q) fda_gather_cols(h, q, h->N, qs, 1, s);
-    k_negate<<<fda_blocks(h->N, 256), 256, 0, s>>>(us, h->N);
-    FDA_CHECK_LAUNCH();
-    if (q) fda_rhs_layers_prepare(h);
-    if (h->cfg.precision == FDA_CHOSEN_FP32 && h->have32) {
-        // the translations as in the chosen form's apply, densities then in FP64
-        fda_translate_chosen(h, us, qs);
-    } else {
-        fda_upward_fp64(h, us, 0, 0);
-        if (q) fda_upward_fp64(h, qs, 1, 1);
-        fda_m2m_fp64(h);
-        fda_downward_fp64(h);
-    }
     ff_tree t;
     memset(&t, 0, sizeof(t));
     t.nlev = h->nlev;
@@ -633,48 +622,91 @@ void fda_field_fast(fda_handle *h, const c64d *u, const c64d *q, const double *t
         phi_off[l + 1] = phi_off[l] + (far ? (int64_t)L.nbox * L.ncones * L.n_eq : 0);
     }
     dbuf phi, derr;
-    phi.alloc(sizeof(c64d) * (size_t)std::max<int64_t>(1, phi_off[h->nlev]));
+    phi.alloc(sizeof(cx<F>) * (size_t)std::max<int64_t>(1, phi_off[h->nlev]));
     derr.alloc(sizeof(int));
     FDA_CUDA(cudaMemsetAsync(derr.p, 0, sizeof(int), s));
     for (int l = 0; l < h->nlev; ++l) {
         const level_info &L = h->lev[l];
-        ff_level &F = t.L[l];
-        F.box0 = L.box0;
-        F.nbox = L.nbox;
-        F.T = L.T;
-        F.ncones = L.ncones;
-        F.nc = L.nc;
-        F.hf = L.hf;
-        F.n_eq = L.n_eq;
-        F.n_chk = L.n_chk;
-        F.w = L.w;
-        F.rho2 = L.rho * L.rho;
-        F.far = phi_off[l + 1] > phi_off[l] ? 1 : 0;
-        if (!F.far) continue;
-        F.phi = phi.as<c64d>() + phi_off[l];
-        F.eq = h->eq_up[l].as<double>();
-        F.chk = h->chk_up[l].as<double>();
-        F.rot = L.hf ? h->rot[l].as<double>() : nullptr;
-        F.U = h->Uup[l].as<c64d>();
-        F.sig = h->sig[l].as<double>();
-        F.p = L.hf ? nullptr : h->p64[l].as<c64d>();
+        ff_level &V = t.L[l];
+        V.box0 = L.box0;
+        V.nbox = L.nbox;
+        V.T = L.T;
+        V.ncones = L.ncones;
+        V.nc = L.nc;
+        V.hf = L.hf;
+        V.n_eq = L.n_eq;
+        V.n_chk = L.n_chk;
+        V.w = L.w;
+        V.rho2 = L.rho * L.rho;
+        V.far = phi_off[l + 1] > phi_off[l] ? 1 : 0;
+        if (!V.far) continue;
+        V.phi = phi.as<cx<F>>() + phi_off[l];
+        V.eq = h->eq_up[l].as<double>();
+        V.chk = h->chk_up[l].as<double>();
+        V.rot = L.hf ? h->rot[l].as<double>() : nullptr;
+        V.U = h->Uup[l].as<c64d>();
+        V.sig = h->sig[l].as<double>();
+        V.p = L.hf ? nullptr : h->p64[l].as<c64d>();
         if (!L.hf) t.max_chk = std::max(t.max_chk, L.n_chk);
         const int64_t nvec = (int64_t)L.nbox * L.ncones;
-        k_equiv_sources<<<(unsigned)std::min<int64_t>(nvec, 65535), 128, sizeof(c64d) * L.T, s>>>(
-            h->q64[l].as<c64d>(), h->Vup[l].as<c64d>(), L.T, L.n_eq, nvec, phi.as<c64d>() + phi_off[l]);
+        k_equiv_sources<F><<<(unsigned)std::min<int64_t>(nvec, 65535), 128, sizeof(cx<F>) * L.T, s>>>(
+            h->q64[l].as<c64d>(), h->Vup[l].as<c64d>(), L.T, L.n_eq, nvec, phi.as<cx<F>>() + phi_off[l]);
         FDA_CHECK_LAUNCH();
     }
-    const size_t dyn = sizeof(c64d) * (size_t)std::max(1, t.max_chk);
+    const size_t dyn = sizeof(cx<F>) * (size_t)std::max(1, t.max_chk);
     if (dyn > 96 * 1024) fda_fail(FDA_ERR_STATE, "fast field: more than 6,144 equivalent points at a level");
-    FDA_CUDA(cudaFuncSetAttribute(k_field_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    FDA_CUDA(cudaFuncSetAttribute(k_field_fast<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     for (int64_t t0 = 0; t0 < ntgt; t0 += (1ll << 30)) {
         const int64_t nb = std::min<int64_t>(1ll << 30, ntgt - t0);
-        k_field_fast<<<(unsigned)nb, FF, dyn, s>>>(t, h->qpt.as<double>(), h->qw.as<double>(), h->nrm.as<double>(),
-                                                   us, qs, tgt_dev + 3 * t0, nb, h->k, derr.as<int>(), out + t0);
+        k_field_fast<F><<<(unsigned)nb, FF, dyn, s>>>(t, h->qpt.as<double>(), h->qw.as<double>(),
+                                                      h->nrm.as<double>(), us, qs, tgt_dev + 3 * t0, nb, h->k,
+                                                      derr.as<int>(), out + t0);
         FDA_CHECK_LAUNCH();
     }
     int herr = 0;
     FDA_CUDA(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     FDA_CUDA(cudaStreamSynchronize(s));
     if (herr) fda_fail(FDA_ERR_STATE, "fast field: more than 2,048 boxes of one level near a point");
+}
+
+}  // namespace
+
+// Scattered field at points through the fast algorithm (see k_field_fast):
+// the outgoing densities of -D[u] + S[q] by S2M and M2M, the local densities
+// by M2L and L2L (in FP64, or as in the chosen form's apply when the handle
+// is in the chosen precision), the equivalent sources of every box, then one
+// CTA per point (FP64 arithmetic; FP32 in the chosen precision, the
+// differences x - y in FP64 and each CTA's partial sums added in FP64).  u, q: caller order (device, q may be null); tgt:
+// device [ntgt][3]; out: device [ntgt], overwritten.
+void fda_field_fast(fda_handle *h, const c64d *u, const c64d *q, const double *tgt_dev, int64_t ntgt, c64d *out)
+{
+    cudaStream_t s = h->stream;
+    if (ntgt == 0 || h->N == 0) {
+        FDA_CUDA(cudaMemsetAsync(out, 0, sizeof(c64d) * ntgt, s));
+        return;
+    }
+    // no level with interaction lists: every pair is near and the direct sum is the method
+    if (h->lev_lo < 0) {
+        fda_field(h, u, q, tgt_dev, ntgt, 0, out);
+        return;
+    }
+    c64d *us = h->xs.as<c64d>(), *qs = q ? h->ys.as<c64d>() : nullptr;
+    fda_gather_cols(h, u, h->N, us, 1, s);
+    if (q) fda_gather_cols(h, q, h->N, qs, 1, s);
+    k_negate<<<fda_blocks(h->N, 256), 256, 0, s>>>(us, h->N);
+    FDA_CHECK_LAUNCH();
+    if (q) fda_rhs_layers_prepare(h);
+    const bool chosen = h->cfg.precision == FDA_CHOSEN_FP32 && h->have32;
+    if (chosen) {
+        // the translations as in the chosen form's apply, densities then in FP64
+        fda_translate_chosen(h, us, qs);
+    } else {
+        fda_upward_fp64(h, us, 0, 0);
+        if (q) fda_upward_fp64(h, qs, 1, 1);
+        fda_m2m_fp64(h);
+        fda_downward_fp64(h);
+    }
+    // point evaluation in FP32 in the chosen precision, else in FP64
+    if (chosen) field_points<float>(h, us, qs, tgt_dev, ntgt, out);
+    else field_points<double>(h, us, qs, tgt_dev, ntgt, out);
 }

@@ -137,9 +137,11 @@ def test_fast_field_matches_direct_and_oracle(mesh, k, with_q, precision):
     the downward pass, equivalent sources of the boxes the point is not
     near, six-point sums of the near leaves) agrees with the direct
     six-point sums and the oracle's field, group by group of points, with
-    the translations in FP64 (plain) and as in the chosen form's apply (FP32
-    S2M, tensor-core M2M / M2L / L2L).  Bound 1e-3 relative per group: the
-    translations are truncated at eps = 1e-4 relative to each box's field."""
+    the translations and the point arithmetic in FP64 (plain) and in the
+    chosen precision (translations as in its apply: FP32 S2M, tensor-core
+    M2M / M2L / L2L; point arithmetic in FP32).  Bound 1e-3 relative per
+    group: the translations are truncated at eps = 1e-4 relative to each
+    box's field."""
     from paper_1403_4747_gb300 import FDAProblem
     level = int(mesh[-1])
     v, f = icosphere(level) if mesh.startswith("sphere") else ellipsoid_from_icosphere(level)
