@@ -46,7 +46,8 @@ def reference_tree(v, f, k, leaf_max=64, rho_min=2.2):
             if leaf[cc]:
                 active[el] = False
         rho = max(rho_min, w / lam) if hf else 0.0
-        levels.append({"boxes": {cc: sorted(el) for cc, el in boxes.items()}, "leaf": leaf, "hf": hf, "rho": rho})
+        levels.append({"boxes": {cc: sorted(el) for cc, el in boxes.items()}, "leaf": leaf, "hf": hf, "rho": rho,
+                       "w": w, "root": root})
     return levels
 
 
