@@ -322,6 +322,31 @@ __global__ void __launch_bounds__(32 * LPB) k_l2t_w(lvl_ptrs<R> P, int nleaf, co
     const cx<R> *src = P.p[l] + (int64_t)(B - P.box0[l]) * T;
     const bool r0 = lane < nB, r1 = lane + 32 < nB;
     cx<R> a0, a1;
+    if (nB <= 32) {
+        // one row per lane: sixteen operator loads in flight per step
+        constexpr int UV = 16;
+        for (int tb = 0; tb < T; tb += 32) {
+            const cx<R> pv = tb + lane < T ? src[tb + lane] : cx<R>();
+            const int nt = min(32, T - tb);
+            for (int ub = 0; ub < nt; ub += UV) {
+                cx<R> c0[UV];
+#pragma unroll
+                for (int u = 0; u < UV; ++u)
+                    c0[u] = ub + u < nt && r0 ? Tm[(int64_t)(tb + ub + u) * ld + lane] : cx<R>();
+#pragma unroll
+                for (int u = 0; u < UV; ++u) {
+                    const cx<R> pt(__shfl_sync(0xffffffffu, pv.re, (ub + u) & 31),
+                                   __shfl_sync(0xffffffffu, pv.im, (ub + u) & 31));
+                    cfma(a0, c0[u], pt);
+                }
+            }
+        }
+        if (r0) {
+            c64d v = y[i0 + lane];
+            y[i0 + lane] = c64d(v.re + (double)a0.re, v.im + (double)a0.im);
+        }
+        return;
+    }
     constexpr int UU = 8;  // densities per step: their operator loads are issued before the products
     for (int tb = 0; tb < T; tb += 32) {
         const cx<R> pv = tb + lane < T ? src[tb + lane] : cx<R>();
