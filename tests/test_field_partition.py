@@ -110,3 +110,11 @@ def test_partition_sphere():
 def test_partition_ellipsoid():
     v, f = ellipsoid_from_icosphere(3)
     _check(v, f, 16.0)
+
+
+def test_partition_two_high_frequency_levels():
+    """Level-4 sphere at k = 40: levels 2 and 3 are high-frequency (rho 3.2
+    and 2.2 widths), level 4 low-frequency, so the walk opens boxes through
+    two directional levels before it reaches the leaves."""
+    v, f = icosphere(4)
+    _check(v, f, 40.0)
